@@ -1,0 +1,167 @@
+/*
+ * stag.h -- C ABI of libstag, a staggered Dirac operator and even-odd CG
+ * library for one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Operator (Sec. 4.2, Eq. (staggered) of "Portable Lattice QCD implementation
+ * based on OpenCL"):
+ *
+ *   (D phi)_x = sum_{mu=0..3} [ eta_mu(x) U_{x,mu} phi_{x+mu}
+ *                              - eta_mu(x-mu) U^dagger_{x-mu,mu} phi_{x-mu} ]
+ *
+ * with eta_0 = 1, eta_1 = (-1)^x, eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z),
+ * periodic boundaries in x, y, z and antiperiodic in t (a hop that crosses the
+ * time boundary takes a factor -1).  No factor 1/2, no mass term.  The solvers
+ * work on the even-odd normal matrix M = m^2 - D_eo D_oe acting on even sites,
+ * which is Hermitian positive definite because D_eo^dagger = -D_oe.
+ *
+ * Canonical layouts (all complex numbers interleaved re, im as doubles):
+ *   site index   i = x + Lx*(y + Ly*(z + Lz*t));  mu = 0,1,2,3 = x,y,z,t
+ *   gauge field  U[V][4][3][3] complex, U[i][mu][a][b] = (U_{x,mu})_{ab}
+ *   half field   psi[V/2][3] complex over the sites of one parity
+ *                ((x+y+z+t) mod 2), indexed h = i/2 (Lx even)
+ *   multi field  psi[n][V/2][3] complex, n half fields back to back
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are CUDA device pointers (for instance a torch
+ *     tensor's data_ptr()); the caller owns them and they are only borrowed for
+ *     the call.  Buffers must be 16-byte aligned and must not overlap unless a
+ *     function says so.
+ *   - The library owns everything it allocates inside a context (compressed
+ *     links, work vectors, CUDA graphs); stag_destroy frees it.
+ *   - Work is enqueued on the context's stream and is asynchronous with respect
+ *     to the host, except where a function says it blocks.
+ *   - A context is not thread safe: one host thread at a time.
+ *   - Return value: 0 = success; negative = error, nothing was written to the
+ *     outputs; positive = numerical outcome (outputs and stats are written).
+ *     stag_strerror() names a code; stag_last_error() gives the message of the
+ *     last failure on the calling thread.
+ */
+#ifndef STAG_H
+#define STAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STAG_ABI_VERSION 1
+
+typedef struct stag_ctx_s *stag_ctx;
+
+enum stag_status {
+    STAG_OK = 0,
+    STAG_NOT_CONVERGED = 1, /* solver reached maxiter; stats hold the residual reached */
+    STAG_BREAKDOWN = 2,     /* <p, Mp> <= 0 or not finite: operator not HPD or data not finite */
+    STAG_EINVAL = -1,       /* bad argument: NULL or misaligned pointer, bad enum, bad size */
+    STAG_EGEOM = -2,        /* lattice extents not even or < 2, or volume too large */
+    STAG_ENOMEM = -3,       /* a device or host allocation failed */
+    STAG_ECUDA = -4,        /* a CUDA call failed (see stag_last_error) */
+    STAG_ENOGAUGE = -5,     /* no gauge field uploaded to this context yet */
+    STAG_EUNSUPPORTED = -6  /* combination of precision / compression not provided */
+};
+
+/* Storage precision of an operator application. */
+enum stag_prec {
+    STAG_F64 = 0, /* double links and spinors, double arithmetic */
+    STAG_F32 = 1, /* float links and spinors, float arithmetic */
+    STAG_F16 = 2  /* half links, half spinors with a float norm per site, float arithmetic */
+};
+
+/* Link compression (Sec. 4.3): 18 reals per link, or 12 (rows 0 and 1; row 2
+ * rebuilt as the complex conjugate of row0 x row1, exact for SU(3) links). */
+enum stag_recon { STAG_RECON_18 = 18, STAG_RECON_12 = 12 };
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context for an Lx x Ly x Lz x Lt lattice on the current CUDA
+ * device.  dims: host array {Lx, Ly, Lz, Lt}, each even and >= 2, volume
+ * < 2^31.  stream: a cudaStream_t (NULL = the legacy default stream) on which
+ * every later call of this context is enqueued.  On success *out holds the new
+ * context.  Errors: STAG_EINVAL (out or dims NULL), STAG_EGEOM, STAG_ENOMEM,
+ * STAG_ECUDA. */
+int stag_create(stag_ctx *out, const int dims[4], void *stream);
+
+/* Free every device and host resource of the context (after synchronising its
+ * stream).  NULL is accepted and ignored. */
+int stag_destroy(stag_ctx ctx);
+
+/* Change the stream later calls are enqueued on. */
+int stag_set_stream(stag_ctx ctx, void *stream);
+
+/* Lattice extents and volume of a context (host outputs, any may be NULL). */
+int stag_get_dims(stag_ctx ctx, int dims[4], long long *volume);
+
+/* Upload the gauge field U (canonical [V][4][3][3] complex128) into the
+ * context's internal layout.  on_device = 1: U is a device pointer; 0: a host
+ * pointer (copied through a device staging buffer).  The field is copied, so U
+ * may be freed or changed after the call returns (on_device = 0) or after the
+ * stream reaches this point (on_device = 1).  Compressed and reduced-precision
+ * copies are derived from it on first use.  Links may be any complex 3x3
+ * matrices for the 18-real forms; the 12-real forms assume SU(3). */
+int stag_upload_gauge(stag_ctx ctx, const double *U, int on_device);
+
+/* ------------------------------------------------------- operator (Eq. staggered) */
+
+/* out_even = D_eo in_odd: the operator restricted to even output sites acting
+ * on a field living on odd sites (both canonical half fields, device).
+ * prec/recon select the storage the kernel streams (input and output stay
+ * complex128 at the boundary; for STAG_F32/STAG_F16 the input is rounded to
+ * that storage first).  Asynchronous.  Errors: STAG_EINVAL, STAG_ENOGAUGE,
+ * STAG_EUNSUPPORTED, STAG_ECUDA. */
+int stag_dslash_eo(stag_ctx ctx, double *out_even, const double *in_odd, int prec, int recon);
+
+/* out_odd = D_oe in_even, as stag_dslash_eo with the parities exchanged. */
+int stag_dslash_oe(stag_ctx ctx, double *out_odd, const double *in_even, int prec, int recon);
+
+/* out_even = M in_even = m^2 in_even - D_eo (D_oe in_even), complex128 double
+ * precision, 18-real links.  Uses a context-owned odd temporary. */
+int stag_apply_M(stag_ctx ctx, double *out_even, const double *in_even, double mass);
+
+/* ---------------------------------------------------------------- solvers */
+
+typedef struct {
+    double tol;            /* stop when ||b - M x|| <= tol ||b||, recomputed in double */
+    int maxiter;           /* total iteration limit (all restarts together); <= 0: 100000 */
+    int use_graph;         /* 1: iterate inside one CUDA graph with a device-side loop;
+                              0: host-driven loop (one stream sync per check_every iterations) */
+    int check_every;       /* host-driven loop only: iterations between convergence reads */
+    double delta;          /* mixed precision: reliable update when ||r|| < delta * max ||r||; <= 0: 0.1 */
+    int inner_prec;        /* mixed precision: STAG_F32 or STAG_F16 */
+    int inner_recon;       /* mixed precision: STAG_RECON_18 or STAG_RECON_12 */
+    int rhs_block;         /* batched solves: right-hand sides per operator pass; 0: autotune */
+} stag_solver_params;
+
+typedef struct {
+    int status;               /* same code the call returned */
+    int iters;                /* operator applications of the (inner) iteration */
+    int restarts;             /* times the iteration restarted from the true residual */
+    int reliable_updates;     /* mixed precision: double-precision residual recomputations */
+    double true_rel_residual; /* ||b - M x|| / ||b|| recomputed in double at the end */
+    double iter_rel_residual; /* the iterated (recursive) residual at the end */
+    double seconds;           /* host wall time of the call, including the final sync */
+} stag_solver_stats;
+
+/* Fill *p with defaults: tol 1e-10, maxiter 100000, use_graph 1, check_every 25,
+ * delta 0.1, inner_prec STAG_F32, inner_recon STAG_RECON_12, rhs_block 0. */
+void stag_solver_params_default(stag_solver_params *p);
+
+/* Solve M x = b by conjugate gradient in double precision (Sec. 1 and
+ * Sec. 4.2: inversion of the staggered operator by CG, here on the even-odd
+ * normal matrix).  x_even, b_even: device canonical half fields.  x starts at
+ * zero.  The iterated residual drives the loop; at the end the true residual
+ * is recomputed in double and the iteration restarts from it while it is above
+ * tol and iterations remain.  Blocks until the solution and *stats (may be
+ * NULL) are final.  Returns STAG_OK, STAG_NOT_CONVERGED, STAG_BREAKDOWN or a
+ * negative error. */
+int stag_cg_solve(stag_ctx ctx, double *x_even, const double *b_even, double mass,
+                  const stag_solver_params *params, stag_solver_stats *stats);
+
+/* ------------------------------------------------------------- utilities */
+
+const char *stag_strerror(int code);
+const char *stag_last_error(void);
+int stag_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAG_H */

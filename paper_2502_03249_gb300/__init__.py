@@ -1,0 +1,231 @@
+"""Python binding of libstag (staggered Dslash and even-odd CG on one GB300).
+
+Argument marshalling only: every operation runs in the CUDA kernels of
+``libstag.so`` (built from ``csrc/`` by ``_build.build()``).  There is no CPU
+fallback; if the library or a CUDA device is missing, the calls raise.
+
+Fields are torch complex128 tensors on the CUDA device, in the canonical
+layout of ``include/stag.h``:
+
+* gauge field: shape (V, 4, 3, 3), site index x + Lx*(y + Ly*(z + Lz*t));
+* half field of one parity: shape (V//2, 3); several: (n, V//2, 3).
+
+Method names follow the C entry points (``stag_dslash_eo`` ->
+``Context.dslash_eo``).  Work is enqueued on torch's current CUDA stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "F64", "F32", "F16", "RECON_18", "RECON_12", "StagError", "NotConverged",
+    "load", "build", "Context", "SolverParams", "SolverStats",
+]
+
+F64, F32, F16 = 0, 1, 2
+RECON_18, RECON_12 = 18, 12
+OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libstag.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class StagError(RuntimeError):
+    """A libstag call returned a negative status."""
+
+    def __init__(self, code, msg):
+        super().__init__(f"libstag error {code}: {msg}")
+        self.code = code
+
+
+class NotConverged(RuntimeError):
+    """A solver returned STAG_NOT_CONVERGED or STAG_BREAKDOWN (stats attached)."""
+
+    def __init__(self, code, stats):
+        super().__init__(f"solver status {code}: {stats}")
+        self.code = code
+        self.stats = stats
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("delta", ctypes.c_double), ("inner_prec", ctypes.c_int),
+                ("inner_recon", ctypes.c_int), ("rhs_block", ctypes.c_int)]
+
+
+class SolverStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
+                ("iter_rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile libstag.so for sm_103a in-tree (needs nvcc)."""
+    from . import _build
+    return _build.build(force=force)
+
+
+def _declare(lib):
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "stag_create": ([ctypes.POINTER(P), ctypes.POINTER(I), P], I),
+        "stag_destroy": ([P], I),
+        "stag_set_stream": ([P, P], I),
+        "stag_get_dims": ([P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)], I),
+        "stag_upload_gauge": ([P, P, I], I),
+        "stag_dslash_eo": ([P, P, P, I, I], I),
+        "stag_dslash_oe": ([P, P, P, I, I], I),
+        "stag_apply_M": ([P, P, P, D], I),
+        "stag_solver_params_default": ([ctypes.POINTER(SolverParams)], None),
+        "stag_cg_solve": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
+        "stag_strerror": ([I], ctypes.c_char_p),
+        "stag_last_error": ([], ctypes.c_char_p),
+        "stag_abi_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def load(path: str | None = None):
+    """Load libstag.so (building it first if it is missing); raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _LIB_PATH
+            if not os.path.exists(p):
+                build()
+            if not os.path.exists(p):
+                raise ImportError(f"libstag.so not found at {p}; run paper_2502_03249_gb300.build()")
+            _lib = _declare(ctypes.CDLL(p))
+    return _lib
+
+
+def _check(rc):
+    if rc < 0:
+        lib = load()
+        raise StagError(rc, f"{lib.stag_strerror(rc).decode()}: {lib.stag_last_error().decode()}")
+    return rc
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libstag needs a CUDA device; none is available")
+    return torch
+
+
+class Context:
+    """One lattice geometry on the current CUDA device (wraps stag_ctx)."""
+
+    def __init__(self, dims, stream=None):
+        torch = _torch()
+        self._lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        d = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(self._lib.stag_create(ctypes.byref(h), d, ctypes.c_void_p(s)))
+        self._h = h
+        self.V = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        self.Vh = self.V // 2
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stag_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers -----------------------------------------------------------
+    def _sync_stream(self):
+        torch = _torch()
+        _check(self._lib.stag_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def _field(self, t, name, n=None):
+        torch = _torch()
+        shape = (self.Vh, 3) if n is None else (n, self.Vh, 3)
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+            raise TypeError(f"{name} must be a complex128 CUDA tensor")
+        if tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {shape}, got {tuple(t.shape)}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def new_half(self, n=None):
+        torch = _torch()
+        shape = (self.Vh, 3) if n is None else (n, self.Vh, 3)
+        return torch.empty(shape, dtype=torch.complex128, device=self.device)
+
+    # -- API -----------------------------------------------------------------
+    def upload_gauge(self, U):
+        """stag_upload_gauge: U complex128 (V,4,3,3), CUDA or CPU tensor."""
+        torch = _torch()
+        if U.dtype != torch.complex128 or tuple(U.shape) != (self.V, 4, 3, 3):
+            raise ValueError("U must be complex128 with shape (V, 4, 3, 3)")
+        U = U.contiguous()
+        self._sync_stream()
+        if U.is_cuda:
+            _check(self._lib.stag_upload_gauge(self._h, ctypes.c_void_p(U.data_ptr()), 1))
+        else:
+            _check(self._lib.stag_upload_gauge(self._h, ctypes.c_void_p(U.data_ptr()), 0))
+        self._U_keepalive = U if U.is_cuda else None
+
+    def dslash_eo(self, out, inp, prec=F64, recon=RECON_18):
+        """stag_dslash_eo: out (even) = D_eo inp (odd)."""
+        self._sync_stream()
+        _check(self._lib.stag_dslash_eo(self._h, self._field(out, "out"), self._field(inp, "in"), prec, recon))
+        return out
+
+    def dslash_oe(self, out, inp, prec=F64, recon=RECON_18):
+        """stag_dslash_oe: out (odd) = D_oe inp (even)."""
+        self._sync_stream()
+        _check(self._lib.stag_dslash_oe(self._h, self._field(out, "out"), self._field(inp, "in"), prec, recon))
+        return out
+
+    def apply_M(self, out, inp, mass):
+        """stag_apply_M: out = (m^2 - D_eo D_oe) inp on even sites."""
+        self._sync_stream()
+        _check(self._lib.stag_apply_M(self._h, self._field(out, "out"), self._field(inp, "in"), float(mass)))
+        return out
+
+    @staticmethod
+    def solver_params(**kw) -> SolverParams:
+        p = SolverParams()
+        load().stag_solver_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        return p
+
+    def cg_solve(self, x, b, mass, raise_on_fail=True, **params):
+        """stag_cg_solve: x = M^{-1} b (double precision CG); returns the stats dict."""
+        self._sync_stream()
+        prm = self.solver_params(**params)
+        st = SolverStats()
+        rc = _check(self._lib.stag_cg_solve(self._h, self._field(x, "x"), self._field(b, "b"), float(mass),
+                                            ctypes.byref(prm), ctypes.byref(st)))
+        if rc != OK and raise_on_fail:
+            raise NotConverged(rc, st.as_dict())
+        return st.as_dict()

@@ -1,0 +1,150 @@
+// cg_kernels.cuh -- the kernels of one conjugate-gradient iteration on
+// M = m^2 - D_eo D_oe (+ sigma), for any spinor storage S and link field LF.
+//
+// One iteration is four launches:
+//   hop     t  = D_oe p                                   (odd sites)
+//   Mp_dot  Ap = (m^2 + sigma) p - D_eo t, pAp = Re<p,Ap>,  alpha = rr / pAp
+//   update  x += alpha p, r -= alpha Ap, rr' = |r|^2,      beta = rr'/rr
+//   p       p  = r + beta p
+// Scalars live in a CgScalars record in device memory; each reduction ends in
+// the last block to arrive, which sums the per-block partials in a fixed order
+// (deterministic) and updates the record.  Once the record says done, every
+// kernel of the iteration returns at once, and the update kernel clears the
+// condition of the enclosing CUDA-graph loop.
+#pragma once
+
+#include "ctx.h"
+#include "dslash.cuh"
+
+namespace stag {
+
+template <class T> struct Real2Double { static __device__ __forceinline__ double f(T v) { return (double)v; } };
+
+// Site contribution to a real inner product; float sites are summed in float
+// first (six terms) and enter the block sum in double.
+template <typename T>
+__device__ __forceinline__ double site_dot(const Vec3<T>& a, const Vec3<T>& b)
+{
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s = fma(a.c[c].re, b.c[c].re, s);
+        s = fma(a.c[c].im, b.c[c].im, s);
+    }
+    return (double)s;
+}
+
+template <class LF, class S, int BS>
+__global__ void __launch_bounds__(BS) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
+{
+    if (sc->done) return;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    if (h >= g.Vh) return;
+    out.store(h, dslash_site(g, p, h, U, in));
+}
+
+template <class LF, class S, int BS>
+__global__ void __launch_bounds__(BS) k_Mp_dot(Geom g, LF U, S t, S p, S Ap, CgScalars* sc,
+                                               double* part, unsigned* cnt)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    if (sc->done) return;
+    typedef typename S::real real;
+    const real m2s = (real)(sc->m2 + sc->sigma);
+    const int h = blockIdx.x * BS + threadIdx.x;
+    double d = 0.0;
+    if (h < g.Vh) {
+        const Vec3<real> Dt = dslash_site(g, 0, h, U, t);
+        const Vec3<real> pv = p.load(h);
+        Vec3<real> a;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.c[c].re = fma(m2s, pv.c[c].re, -Dt.c[c].re);
+            a.c[c].im = fma(m2s, pv.c[c].im, -Dt.c[c].im);
+        }
+        Ap.store(h, a);
+        d = site_dot(pv, a);
+    }
+    const double bs = block_sum<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!arrive_last(cnt, &last)) return;
+    const double pAp = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        sc->pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            sc->status = STAG_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rr / pAp;
+        }
+    }
+}
+
+template <class S, int BS>
+__global__ void __launch_bounds__(BS) k_cg_update(int Vh, S x, S r, S p, S Ap, CgScalars* sc, double* part,
+                                                  unsigned* cnt, cudaGraphConditionalHandle cond, int use_cond)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    if (sc->done) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        return;
+    }
+    typedef typename S::real real;
+    const real alpha = (real)sc->alpha;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    double d = 0.0;
+    if (h < Vh) {
+        Vec3<real> xv = x.load_rw(h), rv = r.load_rw(h);
+        const Vec3<real> pv = p.load(h), av = Ap.load(h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xv.c[c].re = fma(alpha, pv.c[c].re, xv.c[c].re);
+            xv.c[c].im = fma(alpha, pv.c[c].im, xv.c[c].im);
+            rv.c[c].re = fma(-alpha, av.c[c].re, rv.c[c].re);
+            rv.c[c].im = fma(-alpha, av.c[c].im, rv.c[c].im);
+        }
+        x.store(h, xv);
+        r.store(h, rv);
+        d = site_dot(rv, rv);
+    }
+    const double bs = block_sum<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!arrive_last(cnt, &last)) return;
+    const double rr_new = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        sc->beta = rr_new / sc->rr;
+        sc->rr = rr_new;
+        sc->iter += 1;
+        if (!isfinite(rr_new)) {
+            sc->status = STAG_BREAKDOWN;
+            sc->done = 1;
+        } else if (rr_new <= sc->tol2 || sc->iter >= sc->maxiter) {
+            sc->done = 1;
+        }
+        if (use_cond) cudaGraphSetConditional(cond, sc->done ? 0 : 1);
+    }
+}
+
+template <class S, int BS>
+__global__ void __launch_bounds__(BS) k_cg_p(int Vh, S r, S p, const CgScalars* sc)
+{
+    if (sc->done) return;
+    typedef typename S::real real;
+    const real beta = (real)sc->beta;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    if (h >= Vh) return;
+    const Vec3<real> rv = r.load(h);
+    Vec3<real> pv = p.load_rw(h);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pv.c[c].re = fma(beta, pv.c[c].re, rv.c[c].re);
+        pv.c[c].im = fma(beta, pv.c[c].im, rv.c[c].im);
+    }
+    p.store(h, pv);
+}
+
+}  // namespace stag

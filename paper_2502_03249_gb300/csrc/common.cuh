@@ -1,0 +1,364 @@
+// common.cuh -- device-side building blocks shared by the libstag kernels:
+// lattice geometry of one parity, complex 3-vectors and 3x3 matrices, the
+// internal storage layouts of links and spinors, and block reductions.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stag {
+
+// ---------------------------------------------------------------- geometry
+//
+// A half field of parity p holds the V/2 sites with (x+y+z+t) mod 2 == p,
+// indexed h = i/2 with i = x + Lx*(y + Ly*(z + Lz*t)).  Writing h = xh + Lxh*r
+// (Lxh = Lx/2, r the row index of (y,z,t)), the site's x is 2*xh + ((p+y+z+t)&1).
+struct Geom {
+    int L[4];     // Lx, Ly, Lz, Lt
+    int Lxh;      // Lx / 2
+    int Vh;       // V / 2
+};
+
+struct SiteNbrs {
+    int h;             // own half index
+    int fwd[4];        // half index of x + mu (other parity)
+    int bwd[4];        // half index of x - mu (other parity)
+    uint32_t sf[4];    // sign bit (0 or 0x80000000) of eta_mu(x) * boundary, forward hop
+    uint32_t sb[4];    // sign bit of -eta_mu(x-mu) * boundary, backward hop
+};
+
+// Neighbours and hop signs of output site h of parity p.  eta_mu(x-mu) equals
+// eta_mu(x) because eta_mu does not depend on x_mu (even extents keep this
+// true across the periodic wrap).  The backward term of Eq. (staggered) carries
+// an explicit minus, folded into sb.
+__device__ __forceinline__ void site_nbrs(const Geom& g, int p, int h, SiteNbrs& s)
+{
+    const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
+    const int r = h / g.Lxh;
+    const int xh = h - r * g.Lxh;
+    const int y = r % Ly;
+    const int zt = r / Ly;
+    const int z = zt % Lz;
+    const int t = zt / Lz;
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    s.h = h;
+    const int rowh = g.Lxh * r;
+    s.fwd[0] = ((x + 1 == Lx) ? 0 : x + 1) / 2 + rowh;
+    s.bwd[0] = ((x == 0) ? Lx - 1 : x - 1) / 2 + rowh;
+    const int sy = g.Lxh, sz = g.Lxh * Ly, st = g.Lxh * Ly * Lz;
+    s.fwd[1] = h + ((y + 1 == Ly) ? -(Ly - 1) * sy : sy);
+    s.bwd[1] = h + ((y == 0) ? (Ly - 1) * sy : -sy);
+    s.fwd[2] = h + ((z + 1 == Lz) ? -(Lz - 1) * sz : sz);
+    s.bwd[2] = h + ((z == 0) ? (Lz - 1) * sz : -sz);
+    s.fwd[3] = h + ((t + 1 == Lt) ? -(Lt - 1) * st : st);
+    s.bwd[3] = h + ((t == 0) ? (Lt - 1) * st : -st);
+    const uint32_t SB = 0x80000000u;
+    const uint32_t e1 = (x & 1) ? SB : 0u;
+    const uint32_t e2 = ((x + y) & 1) ? SB : 0u;
+    const uint32_t e3 = ((x + y + z) & 1) ? SB : 0u;
+    const uint32_t bf3 = (t == Lt - 1) ? SB : 0u;   // forward hop crosses the time boundary
+    const uint32_t bb3 = (t == 0) ? SB : 0u;        // backward hop crosses it
+    s.sf[0] = 0u;
+    s.sf[1] = e1;
+    s.sf[2] = e2;
+    s.sf[3] = e3 ^ bf3;
+    s.sb[0] = SB;
+    s.sb[1] = e1 ^ SB;
+    s.sb[2] = e2 ^ SB;
+    s.sb[3] = e3 ^ bb3 ^ SB;
+}
+
+// ------------------------------------------------------- complex arithmetic
+
+template <typename T> struct Cplx { T re, im; };
+
+template <typename T> struct Vec3 { Cplx<T> c[3]; };
+template <typename T> struct Mat3 { Cplx<T> m[9]; };   // row major
+
+__device__ __forceinline__ double flip(double v, uint32_t sbit)
+{
+    // v with its sign bit xor-ed with sbit (an exact negation when sbit is set)
+    long long b = __double_as_longlong(v);
+    b ^= ((long long)sbit) << 32;
+    return __longlong_as_double(b);
+}
+__device__ __forceinline__ float flip(float v, uint32_t sbit)
+{
+    return __uint_as_float(__float_as_uint(v) ^ sbit);
+}
+
+template <typename T>
+__device__ __forceinline__ Vec3<T> vflip(const Vec3<T>& v, uint32_t s)
+{
+    Vec3<T> o;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o.c[a].re = flip(v.c[a].re, s);
+        o.c[a].im = flip(v.c[a].im, s);
+    }
+    return o;
+}
+
+// acc += U v
+template <typename T>
+__device__ __forceinline__ void mv_acc(Vec3<T>& acc, const Mat3<T>& U, const Vec3<T>& v)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T re = acc.c[a].re, im = acc.c[a].im;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const Cplx<T> u = U.m[a * 3 + b];
+            re = fma(u.re, v.c[b].re, re);
+            re = fma(-u.im, v.c[b].im, re);
+            im = fma(u.re, v.c[b].im, im);
+            im = fma(u.im, v.c[b].re, im);
+        }
+        acc.c[a].re = re;
+        acc.c[a].im = im;
+    }
+}
+
+// acc += U^dagger v
+template <typename T>
+__device__ __forceinline__ void mdv_acc(Vec3<T>& acc, const Mat3<T>& U, const Vec3<T>& v)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T re = acc.c[a].re, im = acc.c[a].im;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const Cplx<T> u = U.m[b * 3 + a];
+            re = fma(u.re, v.c[b].re, re);
+            re = fma(u.im, v.c[b].im, re);
+            im = fma(u.re, v.c[b].im, im);
+            im = fma(-u.im, v.c[b].re, im);
+        }
+        acc.c[a].re = re;
+        acc.c[a].im = im;
+    }
+}
+
+// Third row of an SU(3) matrix from its first two: conj(row0 x row1) (Sec. 4.3).
+template <typename T>
+__device__ __forceinline__ void reconstruct_row2(Mat3<T>& U)
+{
+    const Cplx<T>* a = &U.m[0];
+    const Cplx<T>* b = &U.m[3];
+    // c_k = conj(a_i b_j - a_j b_i) for (k,i,j) cyclic
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+        T re = a[i].re * b[j].re - a[i].im * b[j].im - (a[j].re * b[i].re - a[j].im * b[i].im);
+        T im = a[i].re * b[j].im + a[i].im * b[j].re - (a[j].re * b[i].im + a[j].im * b[i].re);
+        U.m[6 + k].re = re;
+        U.m[6 + k].im = -im;
+    }
+}
+
+// ------------------------------------------------------------ link storage
+//
+// Links are stored per parity, direction and matrix element, structure of
+// arrays over half sites, so that a warp reading element k of 32 consecutive
+// sites touches one contiguous run:
+//     base[((par*4 + mu)*NE + k)*Vh + h],   NE = 9 (18-real) or 6 (12-real)
+// with element type double2 (F64), float2 (F32) or __half2 (F16).
+
+template <typename S> struct StoreTraits;
+template <> struct StoreTraits<double2> { typedef double real; };
+template <> struct StoreTraits<float2> { typedef float real; };
+template <> struct StoreTraits<__half2> { typedef float real; };
+
+__device__ __forceinline__ Cplx<double> to_cplx(double2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ Cplx<float> to_cplx(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ Cplx<float> to_cplx(__half2 v)
+{
+    float2 f = __half22float2(v);
+    return {f.x, f.y};
+}
+
+template <typename S>
+__device__ __forceinline__ S ldg_nc(const S* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ __half2 ldg_nc<__half2>(const __half2* p)
+{
+    unsigned int u = __ldg(reinterpret_cast<const unsigned int*>(p));
+    return *reinterpret_cast<__half2*>(&u);
+}
+
+template <typename S, int RECON>
+struct LinkField {
+    typedef typename StoreTraits<S>::real real;
+    static constexpr int NE = (RECON == 12) ? 6 : 9;
+    const S* base;
+    int Vh;
+    __device__ __forceinline__ Mat3<real> load(int par, int mu, int h) const
+    {
+        Mat3<real> U;
+        const S* p = base + ((size_t)(par * 4 + mu) * NE) * Vh + h;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) U.m[k] = to_cplx(ldg_nc(p + (size_t)k * Vh));
+        if (RECON == 12) reconstruct_row2(U);
+        return U;
+    }
+};
+
+// ---------------------------------------------------------- spinor storage
+//
+// F64: the canonical layout, complex128 [h][3] (double2 per colour).
+// F32: structure of arrays, float2 [c][Vh] per colour.
+// F16: structure of arrays, __half2 [c][Vh] codes plus a float norm [Vh]; the
+//      value is code * norm, the norm being the largest magnitude of the six
+//      real components of the site.
+// A multi field is n such fields back to back (stride = one field).
+
+struct SpinorF64 {
+    typedef double real;
+    static constexpr bool has_norm = false;
+    double2* p;
+    __device__ __forceinline__ Vec3<double> load(int h) const
+    {
+        Vec3<double> v;
+        const double2* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v.c[c] = to_cplx(__ldg(q + c));
+        return v;
+    }
+    __device__ __forceinline__ Vec3<double> load_rw(int h) const
+    {
+        Vec3<double> v;
+        const double2* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v.c[c] = to_cplx(q[c]);
+        return v;
+    }
+    __device__ __forceinline__ void store(int h, const Vec3<double>& v) const
+    {
+        double2* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] = make_double2(v.c[c].re, v.c[c].im);
+    }
+};
+
+struct SpinorF32 {
+    typedef float real;
+    static constexpr bool has_norm = false;
+    float2* p;
+    int Vh;
+    __device__ __forceinline__ Vec3<float> load(int h) const
+    {
+        Vec3<float> v;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v.c[c] = to_cplx(__ldg(p + (size_t)c * Vh + h));
+        return v;
+    }
+    __device__ __forceinline__ Vec3<float> load_rw(int h) const
+    {
+        Vec3<float> v;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v.c[c] = to_cplx(p[(size_t)c * Vh + h]);
+        return v;
+    }
+    __device__ __forceinline__ void store(int h, const Vec3<float>& v) const
+    {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[(size_t)c * Vh + h] = make_float2(v.c[c].re, v.c[c].im);
+    }
+};
+
+struct SpinorF16 {
+    typedef float real;
+    static constexpr bool has_norm = true;
+    __half2* p;
+    float* norm;
+    int Vh;
+    __device__ __forceinline__ Vec3<float> load(int h) const
+    {
+        Vec3<float> v;
+        const float n = __ldg(norm + h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Cplx<float> q = to_cplx(ldg_nc(p + (size_t)c * Vh + h));
+            v.c[c].re = q.re * n;
+            v.c[c].im = q.im * n;
+        }
+        return v;
+    }
+    __device__ __forceinline__ Vec3<float> load_rw(int h) const
+    {
+        Vec3<float> v;
+        const float n = norm[h];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Cplx<float> q = to_cplx(p[(size_t)c * Vh + h]);
+            v.c[c].re = q.re * n;
+            v.c[c].im = q.im * n;
+        }
+        return v;
+    }
+    // Encode: norm = max |component| (float), code = RN_half(component / norm)
+    // with an IEEE float division; a zero site stores zeros.
+    __device__ __forceinline__ void store(int h, const Vec3<float>& v) const
+    {
+        float n = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) n = fmaxf(n, fmaxf(fabsf(v.c[c].re), fabsf(v.c[c].im)));
+        norm[h] = n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float re = 0.f, im = 0.f;
+            if (n > 0.f) {
+                re = __fdiv_rn(v.c[c].re, n);
+                im = __fdiv_rn(v.c[c].im, n);
+            }
+            p[(size_t)c * Vh + h] = __floats2half2_rn(re, im);
+        }
+    }
+};
+
+// ------------------------------------------------------------ reductions
+
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double* smem)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) smem[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (l < BS / 32) ? smem[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;   // valid in thread 0 (warp 0)
+}
+
+// Each block stores its partial sum; the last block to arrive (counted with an
+// atomic after a fence) sees every partial.  Nobody waits, so the pattern is
+// safe for any grid size.  Returns true in all threads of the last block.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* smem_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int prev = atomicAdd(counter, 1u);
+        *smem_flag = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    return *smem_flag;
+}
+
+// Deterministic sum of n partials by one block (fixed order for fixed n).
+template <int BS>
+__device__ __forceinline__ double sum_partials(const double* part, int n, double* smem)
+{
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += BS) s += __ldcg(part + k);
+    return block_sum<BS>(s, smem);
+}
+
+}  // namespace stag

@@ -1,0 +1,99 @@
+// ctx.h -- host-side internals of libstag: the context object, error
+// reporting helpers and the launchers each translation unit exports to the
+// others.  Not part of the public ABI (include/stag.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "common.cuh"
+#include "stag.h"
+
+namespace stag {
+
+void set_error(const char* fmt, ...);
+
+#define STAG_CUDA_TRY(call)                                                        \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ::stag::set_error("%s failed at %s:%d: %s", #call, __FILE__, __LINE__, \
+                              cudaGetErrorString(e_));                             \
+            return STAG_ECUDA;                                                     \
+        }                                                                          \
+    } while (0)
+
+#define STAG_TRY(call)              \
+    do {                            \
+        int rc_ = (call);           \
+        if (rc_ < 0) return rc_;    \
+    } while (0)
+
+// Index of a (precision, compression) link copy.
+inline int link_slot(int prec, int recon) { return prec * 2 + (recon == 12 ? 1 : 0); }
+
+// Scalars of one CG-type iteration, resident in device memory so the loop
+// runs without host round trips.  One record per right-hand side.
+struct CgScalars {
+    double rr;        // current iterated |r|^2
+    double rr0;       // |b|^2
+    double pAp;
+    double alpha;
+    double beta;
+    double tol2;      // tol^2 * |b|^2 threshold on |r|^2
+    double rr_true;   // last recomputed |b - M x|^2
+    double rmax2;     // mixed precision: max |r|^2 since the last reliable update
+    double delta2;    // mixed precision: delta^2
+    double m2;        // mass^2 of M = m^2 - D_eo D_oe
+    double sigma;     // shift added to M (multi-shift base system)
+    int iter;         // M applications so far
+    int maxiter;
+    int status;       // 0 running/converged, STAG_NOT_CONVERGED, STAG_BREAKDOWN
+    int done;         // 1 once the loop must stop
+    int reliable;     // mixed precision: a reliable update is due
+    int n_reliable;
+    int pad[2];
+};
+
+struct Workspace;   // solver vectors and graphs (cg.cu)
+
+}  // namespace stag
+
+struct stag_ctx_s {
+    stag::Geom g;
+    long long V;
+    int device;
+    int sm_count;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;   // private stream used only to capture graphs
+    bool have_gauge;
+    void* links[6];            // link copies, index link_slot(prec, recon)
+    size_t link_bytes[6];
+    // reduction scratch: partial sums (one double per block) and arrival counters
+    double* partials;
+    unsigned int* counters;    // 64 counters, each used by one reduction site
+    int max_blocks;
+    // temporaries of the operator entry points
+    double2* tmp_odd;          // V/2 x 3 complex
+    void* tmp_lo_in;           // reduced-precision conversions of an API input/output
+    void* tmp_lo_out;
+    size_t tmp_lo_bytes;
+    stag::Workspace* ws;
+};
+
+namespace stag {
+
+// pack.cu
+int upload_gauge(stag_ctx ctx, const double* U, int on_device);
+int ensure_links(stag_ctx ctx, int prec, int recon, const void** out);
+int convert_f64_to_lo(stag_ctx ctx, int prec, const double2* in, void* out, int nvec, cudaStream_t s);
+int convert_lo_to_f64(stag_ctx ctx, int prec, const void* in, double2* out, int nvec, cudaStream_t s);
+size_t lo_spinor_bytes(const Geom& g, int prec);
+
+// dslash.cu: out = D_{par_out, 1-par_out} in, storage chosen by prec/recon.
+// in/out are in the internal storage of prec (F64: canonical AoS).
+int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
+                  cudaStream_t s);
+
+}  // namespace stag

@@ -1,0 +1,54 @@
+// dslash.cu -- the half-lattice staggered operator D_eo / D_oe (Sec. 4.2,
+// Eq. (staggered)) for every supported storage, one output site per thread.
+#include "ctx.h"
+#include "dslash.cuh"
+
+namespace stag {
+
+template <class LF, class SIn, class SOut, int BS>
+__global__ void __launch_bounds__(BS) k_dslash(Geom g, int p, LF U, SIn in, SOut out)
+{
+    const int h = blockIdx.x * BS + threadIdx.x;
+    if (h >= g.Vh) return;
+    out.store(h, dslash_site(g, p, h, U, in));
+}
+
+template <class LF, class SIn, class SOut>
+static int run_dslash(stag_ctx ctx, const LF& U, const SIn& in, const SOut& out, int p,
+                      cudaStream_t s)
+{
+    constexpr int BS = 128;
+    const int grid = (ctx->g.Vh + BS - 1) / BS;
+    k_dslash<LF, SIn, SOut, BS><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
+                  cudaStream_t s)
+{
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    const int Vh = ctx->g.Vh;
+    if (prec == STAG_F64) {
+        SpinorF64 si{(double2*)in}, so{(double2*)out};
+        if (recon == 18) return run_dslash(ctx, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, par_out, s);
+        return run_dslash(ctx, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, par_out, s);
+    }
+    if (prec == STAG_F32) {
+        SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
+        if (recon == 18) return run_dslash(ctx, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, par_out, s);
+        return run_dslash(ctx, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, par_out, s);
+    }
+    if (prec == STAG_F16) {
+        const size_t codes = (size_t)3 * Vh;
+        SpinorF16 si{(__half2*)in, (float*)((__half2*)in + codes), Vh};
+        SpinorF16 so{(__half2*)out, (float*)((__half2*)out + codes), Vh};
+        if (recon == 18) return run_dslash(ctx, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, par_out, s);
+        return run_dslash(ctx, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, par_out, s);
+    }
+    set_error("unsupported precision %d", prec);
+    return STAG_EUNSUPPORTED;
+}
+
+}  // namespace stag

@@ -1,0 +1,35 @@
+// dslash.cuh -- the per-site staggered hop sum of Sec. 4.2, Eq. (staggered),
+// restricted to one output parity, for any link / spinor storage.
+#pragma once
+
+#include "common.cuh"
+
+namespace stag {
+
+// D_{p,1-p} psi at output half site h of parity p:
+//   sum_mu [ eta_mu(x) U_{x,mu} psi_{x+mu} - eta_mu(x-mu) U^dagger_{x-mu,mu} psi_{x-mu} ]
+// Forward links live at x (parity p), backward links at x-mu (parity 1-p).
+// Eight hops, 570 flop per site in the paper's count (Sec. 4.3).
+template <class LF, class SIn>
+__device__ __forceinline__ Vec3<typename LF::real> dslash_site(const Geom& g, int p, int h,
+                                                               const LF& U, const SIn& in)
+{
+    typedef typename LF::real real;
+    SiteNbrs s;
+    site_nbrs(g, p, h, s);
+    Vec3<real> acc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = real(0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const Mat3<real> Uf = U.load(p, mu, h);
+        const Vec3<real> vf = vflip(in.load(s.fwd[mu]), s.sf[mu]);
+        mv_acc(acc, Uf, vf);
+        const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
+        const Vec3<real> vb = vflip(in.load(s.bwd[mu]), s.sb[mu]);
+        mdv_acc(acc, Ub, vb);
+    }
+    return acc;
+}
+
+}  // namespace stag

@@ -1,0 +1,204 @@
+// pack.cu -- conversions between the canonical host-facing layouts and the
+// internal device layouts: the gauge field upload, its 12-real / float / half
+// copies (Sec. 4.3 link compression) and reduced-precision spinor codes.
+#include "ctx.h"
+
+namespace stag {
+
+// canonical U[i][mu][a][b] (complex128) -> internal F64/18:
+//   out[((par*4 + mu)*9 + k)*Vh + i/2],  par = parity of site i
+__global__ void k_pack_gauge(Geom g, const double2* __restrict__ U, double2* __restrict__ out)
+{
+    const long long V = 2LL * g.Vh;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, mu)
+    if (idx >= 4 * V) return;
+    const long long i = idx >> 2;
+    const int mu = (int)(idx & 3);
+    const int x = (int)(i % g.L[0]);
+    long long r = i / g.L[0];
+    const int y = (int)(r % g.L[1]);
+    r /= g.L[1];
+    const int z = (int)(r % g.L[2]);
+    const int t = (int)(r / g.L[2]);
+    const int par = (x + y + z + t) & 1;
+    const long long h = i >> 1;
+    const double2* src = U + idx * 9;
+    double2* dst = out + ((size_t)(par * 4 + mu) * 9) * g.Vh + h;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dst[(size_t)k * g.Vh] = src[k];
+}
+
+// internal F64/18 -> another (precision, compression); element k of NE kept.
+template <typename S, int NE>
+__global__ void k_derive_links(int Vh, const double2* __restrict__ in, S* __restrict__ out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (par, mu, h)
+    if (idx >= 8LL * Vh) return;
+    const long long pm = idx / Vh, h = idx - pm * Vh;
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+        const double2 v = in[(pm * 9 + k) * Vh + h];
+        S o;
+        if constexpr (sizeof(S) == 16) {
+            o = *reinterpret_cast<const S*>(&v);
+        } else if constexpr (sizeof(S) == 8) {
+            float2 f = make_float2((float)v.x, (float)v.y);   // double -> float, RN
+            o = *reinterpret_cast<S*>(&f);
+        } else {
+            __half2 q = __floats2half2_rn((float)v.x, (float)v.y);  // via float, both RN
+            o = *reinterpret_cast<S*>(&q);
+        }
+        out[(pm * NE + k) * Vh + h] = o;
+    }
+}
+
+int upload_gauge(stag_ctx ctx, const double* U, int on_device)
+{
+    const size_t n = (size_t)ctx->V * 4 * 9;
+    const double2* src = (const double2*)U;
+    double2* staging = nullptr;
+    if (!on_device) {
+        STAG_CUDA_TRY(cudaMallocAsync(&staging, n * sizeof(double2), ctx->stream));
+        STAG_CUDA_TRY(cudaMemcpyAsync(staging, U, n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        src = staging;
+    }
+    // drop every derived copy; the F64/18 copy is rebuilt in place
+    for (int s = 1; s < 6; ++s) {
+        if (ctx->links[s]) {
+            cudaFreeAsync(ctx->links[s], ctx->stream);
+            ctx->links[s] = nullptr;
+            ctx->link_bytes[s] = 0;
+        }
+    }
+    if (!ctx->links[0]) {
+        STAG_CUDA_TRY(cudaMalloc(&ctx->links[0], n * sizeof(double2)));
+        ctx->link_bytes[0] = n * sizeof(double2);
+    }
+    const long long work = 4 * ctx->V;
+    const int BS = 256;
+    k_pack_gauge<<<(unsigned)((work + BS - 1) / BS), BS, 0, ctx->stream>>>(ctx->g, src, (double2*)ctx->links[0]);
+    STAG_CUDA_TRY(cudaGetLastError());
+    if (staging) STAG_CUDA_TRY(cudaFreeAsync(staging, ctx->stream));
+    if (!on_device) STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));   // host buffer may be reused
+    ctx->have_gauge = true;
+    return STAG_OK;
+}
+
+int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
+{
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    if (prec < STAG_F64 || prec > STAG_F16 || (recon != 18 && recon != 12)) {
+        set_error("unsupported links: prec %d recon %d", prec, recon);
+        return STAG_EUNSUPPORTED;
+    }
+    const int slot = link_slot(prec, recon);
+    if (!ctx->links[slot]) {
+        const int NE = recon == 12 ? 6 : 9;
+        const size_t esz = prec == STAG_F64 ? 16 : (prec == STAG_F32 ? 8 : 4);
+        const size_t bytes = (size_t)8 * ctx->g.Vh * NE * esz;
+        void* p = nullptr;
+        STAG_CUDA_TRY(cudaMalloc(&p, bytes));
+        const long long work = 8LL * ctx->g.Vh;
+        const int BS = 256;
+        const unsigned grid = (unsigned)((work + BS - 1) / BS);
+        const double2* src = (const double2*)ctx->links[0];
+        if (prec == STAG_F64) k_derive_links<double2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (double2*)p);
+        else if (prec == STAG_F32 && NE == 9) k_derive_links<float2, 9><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float2*)p);
+        else if (prec == STAG_F32) k_derive_links<float2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float2*)p);
+        else if (NE == 9) k_derive_links<__half2, 9><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (__half2*)p);
+        else k_derive_links<__half2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (__half2*)p);
+        STAG_CUDA_TRY(cudaGetLastError());
+        ctx->links[slot] = p;
+        ctx->link_bytes[slot] = bytes;
+    }
+    *out = ctx->links[slot];
+    return STAG_OK;
+}
+
+// ----------------------------------------------------------- spinor codes
+
+size_t lo_spinor_bytes(const Geom& g, int prec)
+{
+    if (prec == STAG_F32) return (size_t)g.Vh * 3 * sizeof(float2);
+    if (prec == STAG_F16) return (size_t)g.Vh * 3 * sizeof(__half2) + (size_t)g.Vh * sizeof(float);
+    return (size_t)g.Vh * 3 * sizeof(double2);
+}
+
+template <class SOut>
+__global__ void k_to_lo(int Vh, int nvec, const double2* __restrict__ in, SOut out, size_t out_stride_bytes)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nvec * Vh) return;
+    const int v = (int)(idx / Vh), h = (int)(idx - (long long)v * Vh);
+    Vec3<float> f;
+    const double2* q = in + ((size_t)v * Vh + h) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        f.c[c].re = (float)q[c].x;
+        f.c[c].im = (float)q[c].y;
+    }
+    SOut o = out;
+    o.p = (decltype(o.p))((char*)out.p + v * out_stride_bytes);
+    if constexpr (SOut::has_norm) o.norm = (float*)((char*)out.norm + v * out_stride_bytes);
+    o.store(h, f);
+}
+
+template <class SIn>
+__global__ void k_from_lo(int Vh, int nvec, SIn in, size_t in_stride_bytes, double2* __restrict__ out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nvec * Vh) return;
+    const int v = (int)(idx / Vh), h = (int)(idx - (long long)v * Vh);
+    SIn s = in;
+    s.p = (decltype(s.p))((char*)in.p + v * in_stride_bytes);
+    if constexpr (SIn::has_norm) s.norm = (float*)((char*)in.norm + v * in_stride_bytes);
+    const Vec3<float> f = s.load_rw(h);
+    double2* q = out + ((size_t)v * Vh + h) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q[c] = make_double2((double)f.c[c].re, (double)f.c[c].im);
+}
+
+int convert_f64_to_lo(stag_ctx ctx, int prec, const double2* in, void* out, int nvec, cudaStream_t s)
+{
+    const int Vh = ctx->g.Vh;
+    const long long work = (long long)nvec * Vh;
+    const int BS = 256;
+    const unsigned grid = (unsigned)((work + BS - 1) / BS);
+    const size_t stride = lo_spinor_bytes(ctx->g, prec);
+    if (prec == STAG_F32) {
+        k_to_lo<SpinorF32><<<grid, BS, 0, s>>>(Vh, nvec, in, SpinorF32{(float2*)out, Vh}, stride);
+    } else if (prec == STAG_F16) {
+        SpinorF16 o{(__half2*)out, (float*)((__half2*)out + (size_t)3 * Vh), Vh};
+        k_to_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, in, o, stride);
+    } else {
+        set_error("convert_f64_to_lo: bad precision %d", prec);
+        return STAG_EUNSUPPORTED;
+    }
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+int convert_lo_to_f64(stag_ctx ctx, int prec, const void* in, double2* out, int nvec, cudaStream_t s)
+{
+    const int Vh = ctx->g.Vh;
+    const long long work = (long long)nvec * Vh;
+    const int BS = 256;
+    const unsigned grid = (unsigned)((work + BS - 1) / BS);
+    const size_t stride = lo_spinor_bytes(ctx->g, prec);
+    if (prec == STAG_F32) {
+        k_from_lo<SpinorF32><<<grid, BS, 0, s>>>(Vh, nvec, SpinorF32{(float2*)in, Vh}, stride, out);
+    } else if (prec == STAG_F16) {
+        SpinorF16 i{(__half2*)in, (float*)((__half2*)in + (size_t)3 * Vh), Vh};
+        k_from_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, i, stride, out);
+    } else {
+        set_error("convert_lo_to_f64: bad precision %d", prec);
+        return STAG_EUNSUPPORTED;
+    }
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+}  // namespace stag

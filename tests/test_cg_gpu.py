@@ -1,0 +1,121 @@
+"""Parity of the double-precision M apply and CG solver against the CPU oracle.
+
+Bars: M applied to a vector within 1e-12 relative (L2); a solve to tol must
+have an oracle-recomputed true residual <= tol; two solves to 1e-14 agree to
+1e-12 relative (the solution error is bounded by cond(M) * residual).
+"""
+
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def setup(stag, dims, recipe="haar", eps=None, seed=301):
+    U = li.random_links(dims, recipe, eps=eps, seed=seed)
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(dev(U))
+    return ctx, U
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4), (10, 6, 4, 6)])
+def test_apply_M_matches_oracle(stag, dims):
+    ctx, U = setup(stag, dims)
+    psi = li.gaussian_half(dims, seed=302)
+    out = ctx.new_half()
+    ctx.apply_M(out, dev(psi), 0.1)
+    assert rel(host(out), orc.apply_M(dims, U, 0.1, psi)) <= 1e-12
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_cg_4x4_workload(stag, use_graph):
+    """4^4, Haar links, m = 0.1, stop at true residual 1e-10."""
+    dims, mass = (4, 4, 4, 4), 0.1
+    ctx, U = setup(stag, dims, seed=li.workload_seed(0, 0))
+    b = li.gaussian_half(dims, seed=li.workload_seed(0, 1))
+    x = ctx.new_half()
+    st = ctx.cg_solve(x, dev(b), mass, tol=1e-10, use_graph=use_graph)
+    xr = host(x)
+    assert st["status"] == 0
+    res = orc.true_residual(dims, U, mass, xr, b)
+    assert res <= 1e-10
+    assert abs(res - st["true_rel_residual"]) <= 1e-3 * res + 1e-16
+    x_cpu, it_cpu, _, _ = orc.cg(dims, U, mass, b, tol=1e-10)
+    assert abs(st["iters"] - it_cpu) <= max(3, it_cpu // 20)
+
+
+def test_graph_and_host_loop_identical(stag):
+    dims, mass = (6, 4, 2, 10), 0.05
+    ctx, U = setup(stag, dims, seed=311)
+    b = dev(li.gaussian_half(dims, seed=312))
+    x1, x2 = ctx.new_half(), ctx.new_half()
+    s1 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1)
+    s2 = ctx.cg_solve(x2, b, mass, tol=1e-11, use_graph=0, check_every=7)
+    assert s1["iters"] == s2["iters"]
+    assert bool((x1 == x2).all())      # deterministic reductions: bit for bit
+    s3 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1)   # graph reused
+    assert s3["iters"] == s1["iters"] and bool((x1 == x2).all())
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 8)])
+def test_cg_tight_solution_matches_oracle(stag, dims):
+    mass = 0.1
+    ctx, U = setup(stag, dims, seed=321)
+    b = li.gaussian_half(dims, seed=322)
+    x = ctx.new_half()
+    ctx.cg_solve(x, dev(b), mass, tol=1e-14)
+    x_cpu, _, rel_cpu, st = orc.cg(dims, U, mass, b, tol=1e-14)
+    assert st == 0
+    assert rel(host(x), x_cpu) <= 1e-12
+
+
+def test_cg_32c8_workload(stag):
+    """32^3 x 8, smooth links eps = 0.3, m = 0.01, true residual 1e-10."""
+    dims, mass = (32, 32, 32, 8), 0.01
+    ctx, U = setup(stag, dims, "smooth", eps=0.3, seed=li.workload_seed(1, 0))
+    b = li.gaussian_half(dims, seed=li.workload_seed(1, 1))
+    x = ctx.new_half()
+    st = ctx.cg_solve(x, dev(b), mass, tol=1e-10)
+    assert st["status"] == 0 and st["iters"] > 10
+    assert orc.true_residual(dims, U, mass, host(x), b) <= 1e-10
+
+
+def test_cg_edge_cases(stag):
+    import torch
+    dims = (4, 4, 4, 4)
+    ctx, U = setup(stag, dims, seed=331)
+    x = ctx.new_half()
+    # zero source: x = 0 exactly, no iterations
+    st = ctx.cg_solve(x, torch.zeros_like(x), 0.1)
+    assert st["status"] == 0 and st["iters"] == 0 and bool((x == 0).all())
+    # iteration limit
+    b = dev(li.gaussian_half(dims, seed=332))
+    with pytest.raises(stag.NotConverged) as e:
+        ctx.cg_solve(x, b, 0.01, tol=1e-14, maxiter=5)
+    assert e.value.code == 1 and e.value.stats["iters"] == 5
+    st = ctx.cg_solve(x, b, 0.01, tol=1e-14, maxiter=5, raise_on_fail=False)
+    assert st["status"] == 1 and st["true_rel_residual"] > 1e-10
+    # non-finite data ends in a breakdown status, not a fault
+    bn = b.clone()
+    bn[3, 1] = float("nan")
+    st = ctx.cg_solve(x, bn, 0.1, raise_on_fail=False)
+    assert st["status"] == 2
+    # the context still solves afterwards
+    st = ctx.cg_solve(x, b, 0.1)
+    assert st["status"] == 0

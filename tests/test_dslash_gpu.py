@@ -1,0 +1,172 @@
+"""Parity of the CUDA half-lattice operators against the CPU oracle.
+
+Tolerances (derived from the arithmetic, see the module docstrings of the
+oracle encodings):
+  * F64 storage, double arithmetic: relative L2 error <= 1e-12 (spec bar)
+    and every element within 1e-13 of the output scale;
+  * F32 / F16 storage, float arithmetic: compared with the double-precision
+    operator applied to the *stored* values (rounded links, F16 codes); each
+    output component is a sum of 48 products of magnitude <= max|U||psi|, so
+    float accumulation bounds the error by about 48 * 2^-24 ~ 3e-6 of that
+    scale: relative L2 <= 1e-5.
+Sizes span several 128-thread blocks with a ragged tail (V/2 not a multiple of
+128), the extent-2 case where x+mu = x-mu, and the 32^3 x 8 workload.
+"""
+
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+import oracle as orc
+from oracle import encodings as enc
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 2, 2), (10, 6, 4, 6), (8, 8, 8, 8), (4, 6, 10, 14)]
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make_ctx(stag, dims, U):
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(dev(U))
+    return ctx
+
+
+@pytest.mark.parametrize("dims", SIZES)
+@pytest.mark.parametrize("parity", [0, 1])
+def test_f64_18_matches_oracle(stag, dims, parity):
+    U = li.random_links(dims, "haar", seed=201)
+    psi = li.gaussian_half(dims, seed=202)
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    (ctx.dslash_eo if parity == 0 else ctx.dslash_oe)(out, dev(psi))
+    got = host(out)
+    ref = orc.dslash_half(dims, U, psi, parity)
+    assert rel(got, ref) <= 1e-12
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 6)])
+def test_f64_18_gl3_links_and_host_upload(stag, dims):
+    """Any complex links (not only SU(3)) for 18-real storage; upload from host memory."""
+    U = li.random_links(dims, "gl3", seed=211)
+    psi = li.gaussian_half(dims, seed=212)
+    ctx = stag.Context(dims)
+    import torch
+    ctx.upload_gauge(torch.from_numpy(U))
+    out = ctx.new_half()
+    ctx.dslash_oe(out, dev(psi))
+    assert rel(host(out), orc.dslash_oe(dims, U, psi)) <= 1e-12
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 6)])
+def test_f64_12_matches_oracle(stag, dims):
+    U = li.random_links(dims, "haar", seed=221)
+    psi = li.gaussian_half(dims, seed=222)
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    ctx.dslash_eo(out, dev(psi), stag.F64, stag.RECON_12)
+    ref = orc.dslash_eo(dims, enc.recon12(U), psi)
+    assert rel(host(out), ref) <= 1e-12
+    assert rel(host(out), orc.dslash_eo(dims, U, psi)) <= 1e-12
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 6), (8, 8, 8, 8)])
+@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_f32_matches_oracle_on_stored_values(stag, dims, recon, parity):
+    U = li.random_links(dims, "smooth", eps=0.3, seed=231)
+    psi = li.gaussian_half(dims, seed=232)
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    (ctx.dslash_eo if parity == 0 else ctx.dslash_oe)(out, dev(psi), stag.F32, recon)
+    Us = enc.round_f32(U) if recon == 18 else enc.recon12(U, enc.round_f32)
+    ref = orc.dslash_half(dims, Us, enc.round_f32(psi), parity)
+    got = host(out)
+    assert rel(got, ref) <= 1e-5
+    assert rel(got, orc.dslash_half(dims, U, psi, parity)) <= 1e-5
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 6), (8, 8, 8, 8)])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_f16_matches_oracle_on_stored_values(stag, dims, recon):
+    U = li.random_links(dims, "smooth", eps=0.3, seed=241)
+    psi = li.gaussian_half(dims, seed=242) * np.exp(np.random.default_rng(243).uniform(-3, 3, (dims[0] * dims[1] * dims[2] * dims[3] // 2, 1)))
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    ctx.dslash_oe(out, dev(psi), stag.F16, recon)
+    Us = enc.round_f16(U) if recon == 18 else enc.recon12(U, enc.round_f16)
+    ref = orc.dslash_oe(dims, Us, enc.half_spinor(psi))
+    got = host(out)
+    # output is re-encoded to F16 on the way out: one more code rounding
+    ref_out = enc.half_spinor(ref)
+    assert rel(got, ref_out) <= 1e-3
+    assert rel(got, ref) <= 1e-3
+    assert rel(got, orc.dslash_oe(dims, U, psi)) <= 3e-3
+
+
+def test_full_size_32c8_f64(stag):
+    """The 32^3 x 8 workload (smooth links eps = 0.3): every output element."""
+    dims = (32, 32, 32, 8)
+    U = li.random_links(dims, "smooth", eps=0.3, seed=li.workload_seed(1, 0))
+    psi = li.gaussian_half(dims, seed=li.workload_seed(1, 1))
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    ctx.dslash_eo(out, dev(psi))
+    ref = orc.dslash_eo(dims, U, psi)
+    assert rel(host(out), ref) <= 1e-12
+    ctx.dslash_oe(out, dev(psi))
+    assert rel(host(out), orc.dslash_oe(dims, U, psi)) <= 1e-12
+
+
+def test_deterministic_repeat(stag):
+    dims = (8, 8, 8, 8)
+    U = li.random_links(dims, "haar", seed=251)
+    psi = dev(li.gaussian_half(dims, seed=252))
+    ctx = make_ctx(stag, dims, U)
+    a, b = ctx.new_half(), ctx.new_half()
+    ctx.dslash_eo(a, psi)
+    ctx.dslash_eo(b, psi)
+    assert bool((a == b).all())
+
+
+def test_errors_are_reported_not_faulted(stag):
+    import torch
+    dims = (4, 4, 4, 4)
+    ctx = stag.Context(dims)
+    psi = dev(li.gaussian_half(dims, seed=261))
+    out = ctx.new_half()
+    with pytest.raises(stag.StagError) as e:
+        ctx.dslash_eo(out, psi)          # no gauge field yet
+    assert e.value.code == -5
+    ctx.upload_gauge(dev(li.random_links(dims, "haar", seed=262)))
+    with pytest.raises(stag.StagError) as e:
+        ctx.dslash_eo(out, psi, 7, 18)   # unknown precision
+    assert e.value.code == -6
+    with pytest.raises(stag.StagError) as e:
+        ctx.dslash_eo(out, psi, 0, 10)   # unknown compression
+    assert e.value.code == -6
+    lib = stag.load()
+    import ctypes
+    raw = torch.zeros(2 * psi.numel() + 1, dtype=torch.float64, device="cuda")
+    mis = ctypes.c_void_p(raw.data_ptr() + 8)   # 8-byte aligned only
+    assert lib.stag_dslash_eo(ctx._h, mis, ctypes.c_void_p(psi.data_ptr()), 0, 18) == -1
+    assert lib.stag_dslash_eo(ctx._h, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(psi.data_ptr()), 0, 18) == -1
+    host_buf = np.zeros((128, 3), complex)
+    assert lib.stag_dslash_eo(ctx._h, ctypes.c_void_p(host_buf.ctypes.data), ctypes.c_void_p(psi.data_ptr()), 0, 18) == -1
+    # the context is still usable afterwards
+    ctx.dslash_eo(out, psi)
+    torch.cuda.synchronize()
