@@ -194,13 +194,39 @@ def cpu_baseline_sample(dims, U, b, mass, Vh, budget_s=12.0):
 
 # ---------------------------------------------------------------- ours
 
+def profile_kernel(args, stag, torch):
+    """A few launches of one operator on the workload, nothing timed (an ncu target)."""
+    name = args.profile_kernel
+    kern, _, dtxt = name.partition("@")
+    parts = kern.split("_")
+    prec = {"f64": stag.F64, "f32": stag.F32, "f16": stag.F16}[parts[1]]
+    recon = int(parts[2])
+    w = li.WORKLOADS[WORKLOAD_INDEX]
+    dims = tuple(int(v) for v in dtxt.split("x")) if dtxt else w["dims"]
+    U = li.random_links(dims, "smooth", eps=w["eps"], seed=li.workload_seed(WORKLOAD_INDEX, 0))
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(torch.from_numpy(U).cuda())
+    psi = torch.from_numpy(li.gaussian_half(dims, seed=99)).cuda()
+    out = ctx.new_half()
+    for _ in range(args.warmup + args.steps):
+        ctx.dslash_eo(out, psi, prec, recon)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_kernel": name, "workload": w["name"], "launches": args.warmup + args.steps}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--use-graph", type=int, default=1,
+                    help="1: device-side loop in one CUDA graph; 0: host-driven loop (per-kernel profiling)")
+    ap.add_argument("--profile-kernel", default=None,
+                    help="only run a few launches of one kernel on the workload (for ncu): "
+                         "dslash_f64_18, dslash_f32_12, dslash_f16_12, ...; optional @LXxLYxLZxLT lattice")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -214,6 +240,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2502_03249_gb300 as stag
     stag.load()
+    if args.profile_kernel:
+        return profile_kernel(args, stag, torch)
 
     w = li.WORKLOADS[WORKLOAD_INDEX]
     dims, mass = w["dims"], w["mass"]
@@ -232,8 +260,9 @@ def main():
         if ws > 1:
             dist.barrier()
 
+    ug = args.use_graph
     for _ in range(args.warmup):
-        st = ctx.cg_solve(x, b, mass, tol=TOL)
+        st = ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug)
     torch.cuda.synchronize()
 
     # ---- timed region: K complete solves, L2 flushed between them
@@ -246,7 +275,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = ctx.cg_solve(x, b, mass, tol=TOL)
+            st = ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -307,6 +336,26 @@ def main():
         e2e_half.append(2 * (st["iters"] + st["restarts"] + 1))
     e2e_val = FLOP_PER_SITE * Vh * statistics.mean(e2e_half) / statistics.mean(e2e_t) * 1e-9
 
+    # ---- mixed precision on the same workload: time-to-solution at the same true residual
+    mixed = {}
+    for name, prec, recon in (("f32_12", stag.F32, 12), ("f16_12", stag.F16, 12)):
+        xm = ctx.new_half()
+        for _ in range(2):
+            ctx.cg_solve_mixed(xm, b, mass, tol=TOL, inner_prec=prec, inner_recon=recon, use_graph=ug)
+        tm = []
+        for _ in range(3):
+            flush.fill_(4.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sm = ctx.cg_solve_mixed(xm, b, mass, tol=TOL, inner_prec=prec, inner_recon=recon, use_graph=ug)
+            e1.record(stream)
+            e1.synchronize()
+            tm.append(e0.elapsed_time(e1))
+        mixed[name] = {"time_to_solution_ms": statistics.median(tm), "iters": sm["iters"],
+                       "reliable_updates": sm["reliable_updates"], "true_rel_residual": sm["true_rel_residual"],
+                       "speedup_vs_f64": ms_per_step / statistics.median(tm)}
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -349,6 +398,7 @@ def main():
         },
         "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": int(b_host.numel() * 16),
                 "d2h_bytes_per_step": int(x_host.numel() * 16), "seconds_per_step": statistics.mean(e2e_t)},
+        "mixed": mixed,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,

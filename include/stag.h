@@ -44,6 +44,7 @@ extern "C" {
 #endif
 
 #define STAG_ABI_VERSION 1
+#define STAG_MAX_RHS 64   /* largest batch of right-hand sides or shifts */
 
 typedef struct stag_ctx_s *stag_ctx;
 
@@ -112,6 +113,16 @@ int stag_dslash_eo(stag_ctx ctx, double *out_even, const double *in_odd, int pre
 /* out_odd = D_oe in_even, as stag_dslash_eo with the parities exchanged. */
 int stag_dslash_oe(stag_ctx ctx, double *out_odd, const double *in_even, int prec, int recon);
 
+/* Multi-vector operator (Sec. 4.3, NMULTI): out_k = D_{p,1-p} in_k for
+ * k = 0..nrhs-1, with each link loaded once per site for a block of
+ * rhs_block vectors (1, 2, 4, 8 or 16; 0 = autotuned, cached per context).
+ * in/out: device multi fields [nrhs][V/2][3] complex128; out_parity 0 gives
+ * D_eo (in on odd sites), 1 gives D_oe.  prec/recon as stag_dslash_eo.
+ * nrhs in [1, STAG_MAX_RHS].  Asynchronous (the first autotuned call times
+ * the candidates and waits for them). */
+int stag_dslash_multi(stag_ctx ctx, double *out, const double *in, int nrhs, int out_parity, int prec, int recon,
+                      int rhs_block);
+
 /* out_even = M in_even = m^2 in_even - D_eo (D_oe in_even), complex128 double
  * precision, 18-real links.  Uses a context-owned odd temporary. */
 int stag_apply_M(stag_ctx ctx, double *out_even, const double *in_even, double mass);
@@ -154,6 +165,54 @@ void stag_solver_params_default(stag_solver_params *p);
  * negative error. */
 int stag_cg_solve(stag_ctx ctx, double *x_even, const double *b_even, double mass,
                   const stag_solver_params *params, stag_solver_stats *stats);
+
+/* Mixed-precision CG with reliable updates on M x = b.  The inner iteration
+ * stores links and vectors in params->inner_prec (STAG_F32, or STAG_F16 with a
+ * float norm per site) with params->inner_recon links, in float arithmetic; the
+ * solution is accumulated in double precision and the residual recomputed in
+ * double precision (18-real double links) whenever the inner residual has
+ * dropped by params->delta below its maximum since the previous recomputation,
+ * and when the inner iteration reaches tol.  Converged means the double
+ * precision true residual is <= tol.  Arguments, blocking and return codes as
+ * stag_cg_solve; stats->reliable_updates counts the recomputations.  (The paper
+ * cites mixed-precision GPU solvers in its bibliography but has no such
+ * solver itself.) */
+int stag_cg_solve_mixed(stag_ctx ctx, double *x_even, const double *b_even, double mass,
+                        const stag_solver_params *params, stag_solver_stats *stats);
+
+/* Batched CG: solve M X_k = B_k for nrhs right-hand sides in one CUDA graph
+ * launch, every operator pass applying each loaded link to params->rhs_block
+ * systems (0 = autotuned).  X, B: device multi fields [nrhs][V/2][3]
+ * complex128, nrhs in [1, STAG_MAX_RHS].  params->inner_prec selects the
+ * iteration's storage: STAG_F64 (plain double-precision CG), or STAG_F32 /
+ * STAG_F16 with params->inner_recon links and double-precision reliable
+ * updates as in stag_cg_solve_mixed, per system.  Converged systems drop out
+ * of the passes.  stats: NULL or an array of nrhs records.  Blocks until done;
+ * returns the worst status over the systems (STAG_OK, STAG_NOT_CONVERGED,
+ * STAG_BREAKDOWN) or a negative error.  (The paper applies the operator to
+ * several vectors at once, Sec. 4.3; the batched solver around it is not in
+ * the paper.) */
+int stag_cg_solve_multi(stag_ctx ctx, double *X, const double *B, int nrhs, double mass,
+                        const stag_solver_params *params, stag_solver_stats *stats);
+
+/* Multi-shift CG: solve (M + shifts[i]) X_i = b for i = 0..nshift-1 from one
+ * Krylov space (one operator application per iteration serves every shift),
+ * then bring each X_i to a double-precision true residual <= tol with a
+ * batched reliable-update solve seeded by X_i.  shifts: host array of nshift
+ * values >= 0 (added to M, any order; the smallest drives the iteration),
+ * nshift in [1, STAG_MAX_RHS].  b: device half field [V/2][3]; X: device multi
+ * field [nshift][V/2][3].  params->inner_prec STAG_F32 (default) or STAG_F64
+ * selects the Krylov phase's storage, params->inner_recon its links; the
+ * refinement uses params->inner_prec / inner_recon with reliable updates.
+ * stats: NULL or nshift records (iters counts both phases, restarts holds the
+ * shared Krylov iterations).  Blocks until done.  (Not in the paper; it is
+ * the solver a rational hybrid Monte Carlo force needs.) */
+int stag_cg_solve_multishift(stag_ctx ctx, double *X, const double *b, const double *shifts, int nshift,
+                             double mass, const stag_solver_params *params, stag_solver_stats *stats);
+
+/* Right-hand sides per operator pass used by the last batched solve of this
+ * context (the autotuner's choice when rhs_block was 0). */
+int stag_last_rhs_block(stag_ctx ctx);
 
 /* ------------------------------------------------------------- utilities */
 

@@ -86,6 +86,11 @@ def _declare(lib):
         "stag_apply_M": ([P, P, P, D], I),
         "stag_solver_params_default": ([ctypes.POINTER(SolverParams)], None),
         "stag_cg_solve": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
+        "stag_cg_solve_mixed": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
+        "stag_cg_solve_multi": ([P, P, P, I, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
+        "stag_dslash_multi": ([P, P, P, I, I, I, I, I], I),
+        "stag_last_rhs_block": ([P], I),
+        "stag_cg_solve_multishift": ([P, P, P, P, I, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_strerror": ([I], ctypes.c_char_p),
         "stag_last_error": ([], ctypes.c_char_p),
         "stag_abi_version": ([], I),
@@ -219,13 +224,60 @@ class Context:
             setattr(p, k, v)
         return p
 
-    def cg_solve(self, x, b, mass, raise_on_fail=True, **params):
-        """stag_cg_solve: x = M^{-1} b (double precision CG); returns the stats dict."""
+    def _solve(self, fn, x, b, mass, raise_on_fail, params):
         self._sync_stream()
         prm = self.solver_params(**params)
         st = SolverStats()
-        rc = _check(self._lib.stag_cg_solve(self._h, self._field(x, "x"), self._field(b, "b"), float(mass),
-                                            ctypes.byref(prm), ctypes.byref(st)))
+        rc = _check(fn(self._h, self._field(x, "x"), self._field(b, "b"), float(mass), ctypes.byref(prm),
+                       ctypes.byref(st)))
         if rc != OK and raise_on_fail:
             raise NotConverged(rc, st.as_dict())
         return st.as_dict()
+
+    def cg_solve(self, x, b, mass, raise_on_fail=True, **params):
+        """stag_cg_solve: x = M^{-1} b (double precision CG); returns the stats dict."""
+        return self._solve(self._lib.stag_cg_solve, x, b, mass, raise_on_fail, params)
+
+    def dslash_multi(self, out, inp, out_parity, prec=F64, recon=RECON_18, rhs_block=0):
+        """stag_dslash_multi: out[k] = D_{p,1-p} inp[k] for every k (links loaded once per rhs block)."""
+        n = int(inp.shape[0])
+        self._sync_stream()
+        _check(self._lib.stag_dslash_multi(self._h, self._field(out, "out", n), self._field(inp, "in", n), n,
+                                           int(out_parity), prec, recon, int(rhs_block)))
+        return out
+
+    def cg_solve_multi(self, X, B, mass, raise_on_fail=True, **params):
+        """stag_cg_solve_multi: X[k] = M^{-1} B[k] for all k in one graph launch; returns a list of stats."""
+        n = int(B.shape[0])
+        self._sync_stream()
+        prm = self.solver_params(**params)
+        st = (SolverStats * n)()
+        rc = _check(self._lib.stag_cg_solve_multi(self._h, self._field(X, "X", n), self._field(B, "B", n), n,
+                                                  float(mass), ctypes.byref(prm), st))
+        out = [s.as_dict() for s in st]
+        if rc != OK and raise_on_fail:
+            raise NotConverged(rc, out)
+        return out
+
+    def cg_solve_multishift(self, X, b, shifts, mass, raise_on_fail=True, **params):
+        """stag_cg_solve_multishift: X[i] = (M + shifts[i])^{-1} b; returns a list of stats."""
+        sh = [float(v) for v in shifts]
+        n = len(sh)
+        arr = (ctypes.c_double * n)(*sh)
+        self._sync_stream()
+        prm = self.solver_params(**params)
+        st = (SolverStats * n)()
+        rc = _check(self._lib.stag_cg_solve_multishift(self._h, self._field(X, "X", n), self._field(b, "b"), arr, n,
+                                                       float(mass), ctypes.byref(prm), st))
+        out = [s.as_dict() for s in st]
+        if rc != OK and raise_on_fail:
+            raise NotConverged(rc, out)
+        return out
+
+    def last_rhs_block(self):
+        """stag_last_rhs_block: rhs block of the last batched solve."""
+        return int(self._lib.stag_last_rhs_block(self._h))
+
+    def cg_solve_mixed(self, x, b, mass, raise_on_fail=True, **params):
+        """stag_cg_solve_mixed: reliable-update CG, inner precision params inner_prec / inner_recon."""
+        return self._solve(self._lib.stag_cg_solve_mixed, x, b, mass, raise_on_fail, params)

@@ -23,6 +23,7 @@ void set_error(const char* fmt, ...)
 }
 
 void free_workspace(stag_ctx ctx);   // cg.cu
+void free_tune_cache(stag_ctx ctx);  // tune.cu
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -74,6 +75,8 @@ static int ensure_lo_tmp(stag_ctx ctx, size_t bytes)
     ctx->tmp_lo_bytes = bytes;
     return STAG_OK;
 }
+
+int ensure_lo_tmp_public(stag_ctx ctx, size_t bytes) { return ensure_lo_tmp(ctx, bytes); }
 
 // out (parity par_out) = D in, boundary fields complex128.
 static int dslash_entry(stag_ctx ctx, double* out, const double* in, int prec, int recon, int par_out)
@@ -185,6 +188,7 @@ int stag_destroy(stag_ctx ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream || ctx->cap_stream) cudaStreamSynchronize(ctx->stream);
     free_workspace(ctx);
+    free_tune_cache(ctx);
     for (int s = 0; s < 6; ++s)
         if (ctx->links[s]) cudaFree(ctx->links[s]);
     if (ctx->partials) cudaFree(ctx->partials);

@@ -1,0 +1,793 @@
+// batched.cu -- batched reliable-update CG: n independent systems
+// (M + sigma_k) x_k = b_k, M = m^2 - D_eo D_oe, advanced together so that each
+// operator pass loads every link once for NB right-hand sides (NB chosen by
+// the autotuner).  Inner storage F64, F32 or F16 (with 18- or 12-real links);
+// the solution of each system is accumulated in double precision and its true
+// residual recomputed in double precision when its inner residual has dropped
+// by delta below the maximum since its last update, or has reached tol.  With
+// F64 inner storage and delta = 0 this is plain batched CG with a final true
+// residual check.  Systems that have converged are masked out of every pass.
+//
+// Serves stag_cg_solve_multi (shared shift 0) and the double-precision
+// refinement of stag_cg_solve_multishift (one shift per system, the shifted
+// solutions as initial guesses).
+//
+// Graph: while (W) { hop; Mp_dot; update; if (I) { accum_x; hop64; resid64; finish } p }
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "batched.cuh"
+#include "cg_kernels.cuh"
+#include "graph.h"
+#include "tune.h"
+#include "workspace.h"
+
+namespace stag {
+
+constexpr int BBS = 128;      // threads (sites) per block of every batched kernel
+constexpr int NB64 = 4;       // right-hand sides per thread of the double-precision passes
+
+struct BatchScal {
+    CgScalars* sc;      // [nrhs]
+    int nrhs;
+    double* part;       // [nrhs][gx]
+    unsigned* cnt;
+    int gx;             // blocks along the sites
+};
+
+__device__ __forceinline__ bool active(const CgScalars& s) { return !s.done; }
+__device__ __forceinline__ bool updating(const CgScalars& s) { return !s.done && s.reliable; }
+
+// Masks of the NB systems starting at k0 that a pass works on.
+template <int NB>
+__device__ __forceinline__ unsigned mask_active(const BatchScal& b, int k0)
+{
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+        if (k0 + k < b.nrhs && active(b.sc[k0 + k])) m |= 1u << k;
+    return m;
+}
+template <int NB>
+__device__ __forceinline__ unsigned mask_updating(const BatchScal& b, int k0)
+{
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+        if (k0 + k < b.nrhs && updating(b.sc[k0 + k])) m |= 1u << k;
+    return m;
+}
+
+// ------------------------------------------------------------- start
+
+// x_hi = x0 (or 0), xlo = 0, rr0 = |b|^2 per system; every system marked for a
+// residual recomputation.  grid (gx, nrhs).
+template <class SX>
+__global__ void __launch_bounds__(BBS) k_b_init(int Vh, const double2* b, const double2* x0, double2* x_hi, SX xlo,
+                                                size_t sx_stride, BatchScal bs, double tol, int maxiter, double m2,
+                                                const double* shifts, double delta)
+{
+    __shared__ double red[BBS / 32];
+    __shared__ bool last;
+    const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
+    double d = 0.0;
+    if (h < Vh) {
+        const size_t o = ((size_t)k * Vh + h) * 3;
+        Vec3<typename SX::real> z;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 bv = b[o + c];
+            d = fma(bv.x, bv.x, d);
+            d = fma(bv.y, bv.y, d);
+            x_hi[o + c] = x0 ? x0[o + c] : make_double2(0.0, 0.0);
+            z.c[c].re = z.c[c].im = 0;
+        }
+        xlo.at(k, sx_stride).store(h, z);
+    }
+    const double s = block_sum<BBS>(d, red);
+    if (threadIdx.x == 0) bs.part[(size_t)k * bs.gx + blockIdx.x] = s;
+    if (!arrive_last(bs.cnt, &last)) return;
+    for (int kk = 0; kk < bs.nrhs; ++kk) {
+        const double bb = sum_partials<BBS>(bs.part + (size_t)kk * bs.gx, bs.gx, red);
+        if (threadIdx.x == 0) {
+            CgScalars c = {};
+            c.rr0 = c.rr = c.rmax2 = c.rr_true = bb;
+            c.tol2 = tol * tol * bb;
+            c.delta2 = delta * delta;
+            c.maxiter = maxiter;
+            c.m2 = m2;
+            c.sigma = shifts ? shifts[kk] : 0.0;
+            c.rr_prev = bb;
+            c.done = (bb == 0.0) ? 1 : 0;
+            c.reliable = 1;
+            bs.sc[kk] = c;
+        }
+    }
+    if (threadIdx.x == 0) *bs.cnt = 0;
+}
+
+// ------------------------------------------------------- operator passes
+
+// t_k = D_oe p_k for the systems selected by MODE (0: active, 1: updating).
+template <class LF, class S, int NB, int MODE>
+__global__ void __launch_bounds__(BBS) k_b_hop(Geom g, LF U, S in, S out, size_t stride, BatchScal bs)
+{
+    const int k0 = blockIdx.y * NB;
+    const unsigned mask = MODE == 0 ? mask_active<NB>(bs, k0) : mask_updating<NB>(bs, k0);
+    if (!mask) return;
+    const int h = blockIdx.x * BBS + threadIdx.x;
+    if (h >= g.Vh) return;
+    Vec3<typename LF::real> acc[NB];
+    dslash_site_multi<LF, S, NB>(g, 1, h, U, in, stride, k0, mask, acc);
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+        if (mask & (1u << k)) out.at(k0 + k, stride).store(h, acc[k]);
+}
+
+// Ap_k = (m^2 + sigma_k) p_k - D_eo t_k, pAp_k, alpha_k = rr_k / pAp_k.
+template <class LF, class S, int NB>
+__global__ void __launch_bounds__(BBS) k_b_Mp_dot(Geom g, LF U, S t, S p, S Ap, size_t stride, BatchScal bs)
+{
+    __shared__ double red[BBS / 32];
+    __shared__ bool last;
+    typedef typename S::real real;
+    const int k0 = blockIdx.y * NB;
+    const unsigned mask = mask_active<NB>(bs, k0);
+    const int h = blockIdx.x * BBS + threadIdx.x;
+    double d[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) d[k] = 0.0;
+    if (mask && h < g.Vh) {
+        Vec3<real> acc[NB];
+        dslash_site_multi<LF, S, NB>(g, 0, h, U, t, stride, k0, mask, acc);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (!(mask & (1u << k))) continue;
+            const real m2s = (real)(bs.sc[k0 + k].m2 + bs.sc[k0 + k].sigma);
+            const Vec3<real> pv = p.at(k0 + k, stride).load(h);
+            Vec3<real> a;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a.c[c].re = fma(m2s, pv.c[c].re, -acc[k].c[c].re);
+                a.c[c].im = fma(m2s, pv.c[c].im, -acc[k].c[c].im);
+            }
+            Ap.at(k0 + k, stride).store(h, a);
+            d[k] = site_dot(pv, a);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (!(mask & (1u << k))) continue;   // uniform over the block
+        const double s = block_sum<BBS>(d[k], red);
+        if (threadIdx.x == 0) bs.part[(size_t)(k0 + k) * bs.gx + blockIdx.x] = s;
+    }
+    if (!arrive_last(bs.cnt, &last)) return;
+    for (int kk = 0; kk < bs.nrhs; ++kk) {
+        if (!active(bs.sc[kk])) continue;
+        const double pAp = sum_partials<BBS>(bs.part + (size_t)kk * bs.gx, bs.gx, red);
+        if (threadIdx.x == 0) {
+            CgScalars& c = bs.sc[kk];
+            c.pAp = pAp;
+            if (!(pAp > 0.0) || !isfinite(pAp)) {
+                c.status = STAG_BREAKDOWN;
+                c.done = 1;
+                c.reliable = 0;
+            } else {
+                c.alpha = c.rr / pAp;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *bs.cnt = 0;
+}
+
+// x_k += alpha_k p_k, r_k -= alpha_k Ap_k, rr_k; flag reliable updates.  grid (gx, nrhs).
+template <class S, class SX>
+__global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride, S r, S p, S Ap, size_t stride,
+                                                  BatchScal bs, cudaGraphConditionalHandle wh,
+                                                  cudaGraphConditionalHandle ih, int use_cond)
+{
+    __shared__ double red[BBS / 32];
+    __shared__ bool last;
+    typedef typename S::real real;
+    const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
+    const bool on = active(bs.sc[k]);
+    double d = 0.0;
+    if (on && h < Vh) {
+        const real alpha = (real)bs.sc[k].alpha;
+        const SX xk = x.at(k, sx_stride);
+        const S rk = r.at(k, stride);
+        Vec3<typename SX::real> xv = xk.load_rw(h);
+        Vec3<real> rv = rk.load_rw(h);
+        const Vec3<real> pv = p.at(k, stride).load(h), av = Ap.at(k, stride).load(h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xv.c[c].re = fma(alpha, pv.c[c].re, xv.c[c].re);
+            xv.c[c].im = fma(alpha, pv.c[c].im, xv.c[c].im);
+            rv.c[c].re = fma(-alpha, av.c[c].re, rv.c[c].re);
+            rv.c[c].im = fma(-alpha, av.c[c].im, rv.c[c].im);
+        }
+        xk.store(h, xv);
+        rk.store(h, rv);
+        d = site_dot(rv, rv);
+    }
+    if (on) {
+        const double s = block_sum<BBS>(d, red);
+        if (threadIdx.x == 0) bs.part[(size_t)k * bs.gx + blockIdx.x] = s;
+    }
+    if (!arrive_last(bs.cnt, &last)) return;
+    int any_rel = 0, any_on = 0;
+    for (int kk = 0; kk < bs.nrhs; ++kk) {
+        if (!active(bs.sc[kk])) {
+            if (threadIdx.x == 0) bs.sc[kk].reliable = 0;
+            continue;
+        }
+        const double rr_new = sum_partials<BBS>(bs.part + (size_t)kk * bs.gx, bs.gx, red);
+        if (threadIdx.x == 0) {
+            CgScalars& c = bs.sc[kk];
+            c.rr_prev = c.rr;
+            c.beta = rr_new / c.rr;
+            c.rr = rr_new;
+            c.iter += 1;
+            if (rr_new > c.rmax2) c.rmax2 = rr_new;
+            c.reliable = !isfinite(rr_new) || rr_new < c.delta2 * c.rmax2 || rr_new <= c.tol2 || c.iter >= c.maxiter;
+            any_rel |= c.reliable;
+            any_on = 1;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *bs.cnt = 0;
+        if (use_cond) {
+            cudaGraphSetConditional(ih, any_rel ? 1 : 0);
+            cudaGraphSetConditional(wh, any_on ? 1 : 0);
+        }
+    }
+}
+
+// x_hi_k += xlo_k, xlo_k = 0 for systems due a reliable update.  grid (gx, nrhs).
+template <class SX>
+__global__ void __launch_bounds__(BBS) k_b_accum_x(int Vh, double2* x_hi, SX xlo, size_t sx_stride, BatchScal bs)
+{
+    const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
+    if (!updating(bs.sc[k]) || h >= Vh) return;
+    const SX xk = xlo.at(k, sx_stride);
+    const Vec3<typename SX::real> v = xk.load_rw(h);
+    Vec3<typename SX::real> z;
+    const size_t o = ((size_t)k * Vh + h) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double2 xv = x_hi[o + c];
+        xv.x += (double)v.c[c].re;
+        xv.y += (double)v.c[c].im;
+        x_hi[o + c] = xv;
+        z.c[c].re = z.c[c].im = 0;
+    }
+    xk.store(h, z);
+}
+
+// r_hi_k = b_k - (m^2 + sigma_k) x_hi_k + D_eo t_k, rr_true_k (double) for updating systems.
+template <class LF, int NB>
+__global__ void __launch_bounds__(BBS) k_b_resid64(Geom g, LF U, const double2* t, const double2* x_hi,
+                                                   const double2* b, double2* r_hi, BatchScal bs)
+{
+    __shared__ double red[BBS / 32];
+    __shared__ bool last;
+    const int k0 = blockIdx.y * NB;
+    const unsigned mask = mask_updating<NB>(bs, k0);
+    const int h = blockIdx.x * BBS + threadIdx.x;
+    const size_t stride = (size_t)g.Vh * 3 * sizeof(double2);
+    double d[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) d[k] = 0.0;
+    if (mask && h < g.Vh) {
+        Vec3<double> acc[NB];
+        dslash_site_multi<LF, SpinorF64, NB>(g, 0, h, U, SpinorF64{(double2*)t}, stride, k0, mask, acc);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (!(mask & (1u << k))) continue;
+            const double m2s = bs.sc[k0 + k].m2 + bs.sc[k0 + k].sigma;
+            const size_t o = ((size_t)(k0 + k) * g.Vh + h) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double2 xv = x_hi[o + c], bv = b[o + c];
+                const double re = bv.x - fma(m2s, xv.x, -acc[k].c[c].re);
+                const double im = bv.y - fma(m2s, xv.y, -acc[k].c[c].im);
+                r_hi[o + c] = make_double2(re, im);
+                d[k] = fma(re, re, d[k]);
+                d[k] = fma(im, im, d[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (!(mask & (1u << k))) continue;
+        const double s = block_sum<BBS>(d[k], red);
+        if (threadIdx.x == 0) bs.part[(size_t)(k0 + k) * bs.gx + blockIdx.x] = s;
+    }
+    if (!arrive_last(bs.cnt, &last)) return;
+    for (int kk = 0; kk < bs.nrhs; ++kk) {
+        if (!updating(bs.sc[kk])) continue;
+        const double rr = sum_partials<BBS>(bs.part + (size_t)kk * bs.gx, bs.gx, red);
+        if (threadIdx.x == 0) bs.sc[kk].rr_true = rr;
+    }
+    if (threadIdx.x == 0) *bs.cnt = 0;
+}
+
+// r_k = lo(r_hi_k) (and p_k = r_k at the start); then, in the last block,
+// restart each updated system's recurrence from its true residual and decide
+// convergence.  grid (gx, nrhs).
+template <class S>
+__global__ void __launch_bounds__(BBS) k_b_finish(int Vh, const double2* r_hi, S r, S p, size_t stride, BatchScal bs,
+                                                  int start, cudaGraphConditionalHandle wh, int use_cond)
+{
+    __shared__ bool last;
+    typedef typename S::real real;
+    const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
+    if (updating(bs.sc[k]) && h < Vh) {
+        Vec3<real> v;
+        const size_t o = ((size_t)k * Vh + h) * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 q = r_hi[o + c];
+            v.c[c].re = (real)q.x;
+            v.c[c].im = (real)q.y;
+        }
+        r.at(k, stride).store(h, v);
+        if (start) p.at(k, stride).store(h, v);
+    }
+    if (!arrive_last(bs.cnt, &last)) return;
+    if (threadIdx.x == 0) {
+        int any_on = 0;
+        for (int kk = 0; kk < bs.nrhs; ++kk) {
+            CgScalars& c = bs.sc[kk];
+            if (updating(c)) {
+                const double rt = c.rr_true;
+                if (!start) c.n_reliable += 1;
+                if (!isfinite(rt)) {
+                    c.status = STAG_BREAKDOWN;
+                    c.done = 1;
+                } else if (rt <= c.tol2) {
+                    c.done = 1;
+                } else if (c.iter >= c.maxiter) {
+                    c.status = STAG_NOT_CONVERGED;
+                    c.done = 1;
+                }
+                c.beta = start ? 0.0 : rt / c.rr_prev;
+                c.rr = rt;
+                c.rmax2 = rt;
+            }
+            c.reliable = 0;
+            any_on |= !c.done;
+        }
+        *bs.cnt = 0;
+        if (use_cond) cudaGraphSetConditional(wh, any_on ? 1 : 0);
+    }
+}
+
+// p_k = r_k + beta_k p_k.  grid (gx, nrhs).
+template <class S>
+__global__ void __launch_bounds__(BBS) k_b_p(int Vh, S r, S p, size_t stride, BatchScal bs)
+{
+    typedef typename S::real real;
+    const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
+    if (!active(bs.sc[k]) || h >= Vh) return;
+    const real beta = (real)bs.sc[k].beta;
+    const S pk = p.at(k, stride);
+    const Vec3<real> rv = r.at(k, stride).load(h);
+    Vec3<real> pv = pk.load_rw(h);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pv.c[c].re = fma(beta, pv.c[c].re, rv.c[c].re);
+        pv.c[c].im = fma(beta, pv.c[c].im, rv.c[c].im);
+    }
+    pk.store(h, pv);
+}
+
+// ------------------------------------------------------------- driver
+
+typedef LinkField<double2, 18> LF64B;
+
+template <class S, class SX, class LF, int NB>
+struct BatchPlan {
+    static S spin(const BatchSlot& m, void* buf) { return m.template spinor<S>(buf); }
+    static SX spinx(const BatchSlot& m, void* buf) { return m.template spinor<SX>(buf); }
+
+    static int enqueue_start(stag_ctx ctx, BatchSlot& m, const LF64B& U64, cudaStream_t s, const double2* x0,
+                             double tol, int maxiter, double mass, const double* shifts_dev, double delta)
+    {
+        const Geom g = ctx->g;
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        const dim3 gb(m.gx, m.nrhs), g64(m.gx, (m.nrhs + NB64 - 1) / NB64);
+        k_b_init<SX><<<gb, BBS, 0, s>>>(g.Vh, m.b, x0, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs, tol, maxiter,
+                                        mass * mass, shifts_dev, delta);
+        k_b_hop<LF64B, SpinorF64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SpinorF64{m.x_hi}, SpinorF64{m.t64},
+                                                                m.f64_stride, bs);
+        k_b_resid64<LF64B, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+        k_b_finish<S><<<gb, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 1, 0, 0);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+    static int enqueue_main(stag_ctx ctx, BatchSlot& m, const LF& U, cudaStream_t s, LoopGraph* lg, int use_cond)
+    {
+        const Geom g = ctx->g;
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        const dim3 gb(m.gx, m.nrhs), gn(m.gx, (m.nrhs + NB - 1) / NB);
+        k_b_hop<LF, S, NB, 0><<<gn, BBS, 0, s>>>(g, U, spin(m, m.p), spin(m, m.t), m.s_stride, bs);
+        k_b_Mp_dot<LF, S, NB><<<gn, BBS, 0, s>>>(g, U, spin(m, m.t), spin(m, m.p), spin(m, m.Ap), m.s_stride, bs);
+        k_b_update<S, SX><<<gb, BBS, 0, s>>>(g.Vh, spinx(m, m.xlo), m.sx_stride, spin(m, m.r), spin(m, m.p),
+                                             spin(m, m.Ap), m.s_stride, bs, lg ? lg->w : 0, lg ? lg->i : 0, use_cond);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+    static int enqueue_reliable(stag_ctx ctx, BatchSlot& m, const LF64B& U64, cudaStream_t s, LoopGraph* lg,
+                                int use_cond)
+    {
+        const Geom g = ctx->g;
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        const dim3 gb(m.gx, m.nrhs), g64(m.gx, (m.nrhs + NB64 - 1) / NB64);
+        k_b_accum_x<SX><<<gb, BBS, 0, s>>>(g.Vh, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs);
+        k_b_hop<LF64B, SpinorF64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SpinorF64{m.x_hi}, SpinorF64{m.t64},
+                                                                m.f64_stride, bs);
+        k_b_resid64<LF64B, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+        k_b_finish<S><<<gb, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 0,
+                                         lg ? lg->w : 0, use_cond);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+    static int enqueue_p(stag_ctx ctx, BatchSlot& m, cudaStream_t s)
+    {
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        k_b_p<S><<<dim3(m.gx, m.nrhs), BBS, 0, s>>>(ctx->g.Vh, spin(m, m.r), spin(m, m.p), m.s_stride, bs);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+
+    static int run(stag_ctx ctx, BatchSlot& m, const void* lk, const double2* x0, double mass,
+                   const double* shifts_dev, const stag_solver_params& prm, double delta)
+    {
+        const void* lk64 = nullptr;
+        STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk64));
+        const LF U{(const typename LF::store*)lk, ctx->g.Vh};
+        const LF64B U64{(const double2*)lk64, ctx->g.Vh};
+        const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
+        STAG_TRY(enqueue_start(ctx, m, U64, ctx->stream, x0, prm.tol, maxiter, mass, shifts_dev, delta));
+        if (prm.use_graph) {
+            if (!m.lg.exec || m.graph_nb != NB) {
+                LoopGraph& lg = m.lg;
+                STAG_TRY(build_loop_graph(
+                    ctx->cap_stream, lg, true, [&](cudaStream_t s) { return enqueue_main(ctx, m, U, s, &lg, 1); },
+                    [&](cudaStream_t s) { return enqueue_reliable(ctx, m, U64, s, &lg, 1); },
+                    [&](cudaStream_t s) { return enqueue_p(ctx, m, s); }));
+                m.graph_nb = NB;
+            }
+            STAG_CUDA_TRY(cudaGraphLaunch(m.lg.exec, ctx->stream));
+        } else {
+            const int every = prm.check_every > 0 ? prm.check_every : 25;
+            std::vector<CgScalars> hs(m.nrhs);
+            for (;;) {
+                for (int k = 0; k < every; ++k) {
+                    STAG_TRY(enqueue_main(ctx, m, U, ctx->stream, nullptr, 0));
+                    STAG_TRY(enqueue_reliable(ctx, m, U64, ctx->stream, nullptr, 0));
+                    STAG_TRY(enqueue_p(ctx, m, ctx->stream));
+                }
+                STAG_CUDA_TRY(cudaMemcpyAsync(hs.data(), m.sc, sizeof(CgScalars) * m.nrhs, cudaMemcpyDeviceToHost,
+                                              ctx->stream));
+                STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+                bool any = false;
+                for (auto& c : hs) any |= !c.done;
+                if (!any) break;
+            }
+        }
+        return STAG_OK;
+    }
+};
+
+// Multi operator pass for the autotuner and the public multi Dslash.
+template <class LF, class S, int NB>
+__global__ void __launch_bounds__(BBS) k_multi_dslash(Geom g, int p, LF U, S in, S out, size_t stride, int nrhs)
+{
+    const int k0 = blockIdx.y * NB;
+    unsigned mask = 0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+        if (k0 + k < nrhs) mask |= 1u << k;
+    const int h = blockIdx.x * BBS + threadIdx.x;
+    if (h >= g.Vh) return;
+    Vec3<typename LF::real> acc[NB];
+    dslash_site_multi<LF, S, NB>(g, p, h, U, in, stride, k0, mask, acc);
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+        if (mask & (1u << k)) out.at(k0 + k, stride).store(h, acc[k]);
+}
+
+template <class LF, class S>
+int launch_multi_dslash_nb(stag_ctx ctx, int nb, const LF& U, const S& in, const S& out, size_t stride, int nrhs,
+                           int p, cudaStream_t s)
+{
+    const int gx = (ctx->g.Vh + BBS - 1) / BBS;
+    const dim3 grid(gx, (nrhs + nb - 1) / nb);
+    switch (nb) {
+    case 1: k_multi_dslash<LF, S, 1><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 2: k_multi_dslash<LF, S, 2><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 4: k_multi_dslash<LF, S, 4><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 8: k_multi_dslash<LF, S, 8><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 16: k_multi_dslash<LF, S, 16><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    default: set_error("unsupported rhs block %d", nb); return STAG_EINVAL;
+    }
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+// Apply the multi Dslash on internal-storage multi fields; nb = 0 asks the
+// autotuner (timed on these buffers, cached per context and shape).
+template <class LF, class S>
+static int multi_dslash_tuned(stag_ctx ctx, const char* tag, const LF& U, const S& in, const S& out, size_t stride,
+                              int nrhs, int p, int nb, int* nb_used)
+{
+    if (nb == 0) {
+        char key[128];
+        snprintf(key, sizeof(key), "multi_dslash/%s/nrhs%d", tag, nrhs);
+        STAG_TRY(tune_choice(ctx, key, {1, 2, 4, 8, 16}, nrhs, &nb, [&](int c) {
+            return launch_multi_dslash_nb(ctx, c, U, in, out, stride, nrhs, p, ctx->stream);
+        }));
+    }
+    if (nb_used) *nb_used = nb;
+    return launch_multi_dslash_nb(ctx, nb, U, in, out, stride, nrhs, p, ctx->stream);
+}
+
+int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs, int nb,
+                 int* nb_used)
+{
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    const int Vh = ctx->g.Vh;
+    const size_t stride = lo_spinor_bytes(ctx->g, prec);
+    char tag[32];
+    snprintf(tag, sizeof(tag), "p%d_r%d", prec, recon);
+    if (prec == STAG_F64) {
+        SpinorF64 si{(double2*)in}, so{(double2*)out};
+        if (recon == 18)
+            return multi_dslash_tuned(ctx, tag, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+                                      par_out, nb, nb_used);
+        return multi_dslash_tuned(ctx, tag, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+                                  par_out, nb, nb_used);
+    }
+    if (prec == STAG_F32) {
+        SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
+        if (recon == 18)
+            return multi_dslash_tuned(ctx, tag, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+                                      par_out, nb, nb_used);
+        return multi_dslash_tuned(ctx, tag, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+                                  par_out, nb, nb_used);
+    }
+    const size_t codes = (size_t)3 * Vh;
+    SpinorF16 si{(__half2*)in, (float*)((__half2*)in + codes), Vh};
+    SpinorF16 so{(__half2*)out, (float*)((__half2*)out + codes), Vh};
+    if (recon == 18)
+        return multi_dslash_tuned(ctx, tag, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, stride, nrhs,
+                                  par_out, nb, nb_used);
+    return multi_dslash_tuned(ctx, tag, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, stride, nrhs, par_out,
+                              nb, nb_used);
+}
+
+// ------------------------------------------------------------- slots
+
+int ensure_cg_f64(stag_ctx ctx);
+
+static int ensure_batch(stag_ctx ctx, int prec, int recon, int nrhs, BatchSlot** out)
+{
+    if (!ctx->ws) {
+        ctx->ws = new (std::nothrow) Workspace();
+        if (!ctx->ws) return STAG_ENOMEM;
+    }
+    BatchSlot& m = ctx->ws->batch[prec][recon == 12 ? 1 : 0];
+    if (m.ready && m.cap < nrhs) m.release();
+    if (!m.ready) {
+        const Geom& g = ctx->g;
+        m.Vh = g.Vh;
+        m.cap = nrhs;
+        m.s_stride = lo_spinor_bytes(g, prec);
+        m.sx_stride = lo_spinor_bytes(g, prec == STAG_F64 ? STAG_F64 : STAG_F32);
+        m.f64_stride = (size_t)g.Vh * 3 * sizeof(double2);
+        m.prec = prec;
+        m.gx = (g.Vh + BBS - 1) / BBS;
+        const size_t n = (size_t)nrhs;
+        STAG_CUDA_TRY(cudaMalloc(&m.r, n * m.s_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.p, n * m.s_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.Ap, n * m.s_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.t, n * m.s_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.xlo, n * m.sx_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.x_hi, n * m.f64_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.r_hi, n * m.f64_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.b, n * m.f64_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.t64, n * m.f64_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.sc, n * sizeof(CgScalars)));
+        STAG_CUDA_TRY(cudaMalloc(&m.part, n * m.gx * sizeof(double)));
+        STAG_CUDA_TRY(cudaMalloc(&m.shifts, n * sizeof(double)));
+        m.ready = true;
+    }
+    if (m.nrhs != nrhs) m.lg.destroy();   // the graph bakes the batch size into its grids
+    m.nrhs = nrhs;
+    *out = &m;
+    return STAG_OK;
+}
+
+template <class S, class SX, class LF>
+static int run_with_nb(stag_ctx ctx, BatchSlot& m, const void* lk, const double2* x0, double mass,
+                       const double* shifts_dev, const stag_solver_params& prm, double delta, int nb)
+{
+    switch (nb) {
+    case 1: return BatchPlan<S, SX, LF, 1>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
+    case 2: return BatchPlan<S, SX, LF, 2>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
+    case 4: return BatchPlan<S, SX, LF, 4>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
+    case 8: return BatchPlan<S, SX, LF, 8>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
+    case 16: return BatchPlan<S, SX, LF, 16>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
+    default: set_error("unsupported rhs block %d", nb); return STAG_EINVAL;
+    }
+}
+
+// X (device, [nrhs][Vh][3] complex128) = solutions of (M + shifts_k) X_k = B_k.
+// shifts_host: NULL (all zero) or nrhs host values; X0: NULL or initial guesses.
+int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double mass, const double* shifts_host,
+                  const double2* X0, const stag_solver_params& prm, stag_solver_stats* stats)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const int prec = prm.inner_prec, recon = prm.inner_recon;
+    if (prec < STAG_F64 || prec > STAG_F16 || (recon != 18 && recon != 12)) {
+        set_error("batched solver: unsupported inner precision %d / compression %d", prec, recon);
+        return STAG_EUNSUPPORTED;
+    }
+    BatchSlot* mp = nullptr;
+    STAG_TRY(ensure_batch(ctx, prec, recon, nrhs, &mp));
+    BatchSlot& m = *mp;
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    const double delta = prec == STAG_F64 ? 0.0 : (prm.delta > 0 ? prm.delta : 0.1);
+    const size_t vbytes = (size_t)nrhs * m.f64_stride;
+    STAG_CUDA_TRY(cudaMemcpyAsync(m.b, B, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    const double* shifts_dev = nullptr;
+    if (shifts_host) {
+        STAG_CUDA_TRY(cudaMemcpyAsync(m.shifts, shifts_host, nrhs * sizeof(double), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        shifts_dev = m.shifts;
+    }
+    // right-hand sides per operator pass: given, or tuned on the inner operator
+    int nb = prm.rhs_block;
+    if (nb != 0 && nb != 1 && nb != 2 && nb != 4 && nb != 8 && nb != 16) {
+        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
+        return STAG_EINVAL;
+    }
+    if (nb == 0) STAG_TRY(multi_dslash(ctx, prec, recon, 1, m.t, m.p, nrhs, 0, &nb));
+    int rc;
+    if (prec == STAG_F64) {
+        rc = recon == 18 ? run_with_nb<SpinorF64, SpinorF64, LinkField<double2, 18>>(ctx, m, lk, X0, mass, shifts_dev, prm, delta, nb)
+                         : run_with_nb<SpinorF64, SpinorF64, LinkField<double2, 12>>(ctx, m, lk, X0, mass, shifts_dev, prm, delta, nb);
+    } else if (prec == STAG_F32) {
+        rc = recon == 18 ? run_with_nb<SpinorF32, SpinorF32, LinkField<float2, 18>>(ctx, m, lk, X0, mass, shifts_dev, prm, delta, nb)
+                         : run_with_nb<SpinorF32, SpinorF32, LinkField<float2, 12>>(ctx, m, lk, X0, mass, shifts_dev, prm, delta, nb);
+    } else {
+        rc = recon == 18 ? run_with_nb<SpinorF16, SpinorF32, LinkField<__half2, 18>>(ctx, m, lk, X0, mass, shifts_dev, prm, delta, nb)
+                         : run_with_nb<SpinorF16, SpinorF32, LinkField<__half2, 12>>(ctx, m, lk, X0, mass, shifts_dev, prm, delta, nb);
+    }
+    STAG_TRY(rc);
+    std::vector<CgScalars> hs(nrhs);
+    STAG_CUDA_TRY(cudaMemcpyAsync(hs.data(), m.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    STAG_CUDA_TRY(cudaMemcpyAsync(X, m.x_hi, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    int status = STAG_OK;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < nrhs; ++k) {
+        const CgScalars& c = hs[k];
+        int sk = STAG_OK;
+        if (c.rr0 == 0.0) {
+            STAG_CUDA_TRY(cudaMemsetAsync(X + (size_t)k * 3 * ctx->g.Vh, 0, m.f64_stride, ctx->stream));
+        } else if (c.status == STAG_BREAKDOWN) {
+            sk = STAG_BREAKDOWN;
+        } else if (!(c.rr_true <= c.tol2)) {
+            sk = STAG_NOT_CONVERGED;
+        }
+        if (sk > status) status = sk;
+        if (stats) {
+            stats[k].status = sk;
+            stats[k].iters = c.iter;
+            stats[k].restarts = 0;
+            stats[k].reliable_updates = c.n_reliable;
+            stats[k].true_rel_residual = c.rr0 > 0 ? sqrt(c.rr_true / c.rr0) : 0.0;
+            stats[k].iter_rel_residual = c.rr0 > 0 ? sqrt(c.rr / c.rr0) : 0.0;
+            stats[k].seconds = secs;
+        }
+    }
+    STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->last_rhs_block = nb;
+    return status;
+}
+
+void BatchSlot::release()
+{
+    lg.destroy();
+    void* bufs[] = {r, p, Ap, t, xlo, x_hi, r_hi, b, t64, sc, part, shifts};
+    for (void* q : bufs)
+        if (q) cudaFree(q);
+    *this = BatchSlot();
+}
+
+void free_batches(Workspace* ws)
+{
+    for (auto& row : ws->batch)
+        for (auto& m : row) m.release();
+}
+
+int check_ctx(stag_ctx ctx);
+int check_half_field(const void* p, const char* what);
+
+}  // namespace stag
+
+using namespace stag;
+
+extern "C" {
+
+int stag_cg_solve_multi(stag_ctx ctx, double* X, const double* B, int nrhs, double mass,
+                        const stag_solver_params* params, stag_solver_stats* stats)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(X, "X"));
+    STAG_TRY(check_half_field(B, "B"));
+    if (nrhs < 1 || nrhs > STAG_MAX_RHS) {
+        set_error("nrhs must be in [1, %d]", STAG_MAX_RHS);
+        return STAG_EINVAL;
+    }
+    stag_solver_params prm;
+    stag_solver_params_default(&prm);
+    if (params) prm = *params;
+    if (!(prm.tol > 0.0)) {
+        set_error("tol must be positive");
+        return STAG_EINVAL;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    return batched_solve(ctx, (double2*)X, (const double2*)B, nrhs, mass, nullptr, nullptr, prm, stats);
+}
+
+int stag_dslash_multi(stag_ctx ctx, double* out, const double* in, int nrhs, int out_parity, int prec, int recon,
+                      int rhs_block)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(out, "out"));
+    STAG_TRY(check_half_field(in, "in"));
+    if (out == in) {
+        set_error("out and in must not alias");
+        return STAG_EINVAL;
+    }
+    if (nrhs < 1 || nrhs > STAG_MAX_RHS || (out_parity != 0 && out_parity != 1)) {
+        set_error("nrhs must be in [1, %d] and out_parity 0 or 1", STAG_MAX_RHS);
+        return STAG_EINVAL;
+    }
+    if (rhs_block != 0 && rhs_block != 1 && rhs_block != 2 && rhs_block != 4 && rhs_block != 8 && rhs_block != 16) {
+        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
+        return STAG_EINVAL;
+    }
+    if (prec < STAG_F64 || prec > STAG_F16 || (recon != 18 && recon != 12)) {
+        set_error("unsupported prec %d / recon %d", prec, recon);
+        return STAG_EUNSUPPORTED;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    if (prec == STAG_F64) return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr);
+    const size_t lo = lo_spinor_bytes(ctx->g, prec) * nrhs;
+    STAG_TRY(ensure_lo_tmp_public(ctx, lo));
+    STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, nrhs, ctx->stream));
+    STAG_TRY(multi_dslash(ctx, prec, recon, out_parity, ctx->tmp_lo_out, ctx->tmp_lo_in, nrhs, rhs_block, nullptr));
+    return convert_lo_to_f64(ctx, prec, ctx->tmp_lo_out, (double2*)out, nrhs, ctx->stream);
+}
+
+int stag_last_rhs_block(stag_ctx ctx)
+{
+    if (!ctx) return STAG_EINVAL;
+    return ctx->last_rhs_block;
+}
+
+}  // extern "C"

@@ -1,0 +1,38 @@
+// batched.cuh -- the staggered operator applied to NB right-hand sides per
+// thread: every link is loaded once per site and used for all NB vectors
+// (the paper's multi-vector Dslash, Sec. 4.3, NMULTI), plus the per-system
+// masks the batched solvers use.
+#pragma once
+
+#include "dslash.cuh"
+
+namespace stag {
+
+// acc[k] = (D_{p,1-p} in_{k0+k})_h for the k with bit k of mask set.
+// in.at(j, stride) is field j of the multi field.
+template <class LF, class S, int NB>
+__device__ __forceinline__ void dslash_site_multi(const Geom& g, int p, int h, const LF& U, const S& in,
+                                                  size_t stride, int k0, unsigned mask,
+                                                  Vec3<typename LF::real>* acc)
+{
+    typedef typename LF::real real;
+    SiteNbrs s;
+    site_nbrs(g, p, h, s);
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[k].c[a].re = acc[k].c[a].im = real(0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const Mat3<real> Uf = U.load(p, mu, h);
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if (mask & (1u << k)) mv_acc(acc[k], Uf, vflip(in.at(k0 + k, stride).load(s.fwd[mu]), s.sf[mu]));
+        const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if (mask & (1u << k)) mdv_acc(acc[k], Ub, vflip(in.at(k0 + k, stride).load(s.bwd[mu]), s.sb[mu]));
+    }
+}
+
+}  // namespace stag

@@ -12,6 +12,7 @@ namespace stag {
 
 constexpr int HOP_BS = 128;
 constexpr int BLAS_BS = 256;
+constexpr int MAX_RESTARTS = 100;
 
 typedef LinkField<double2, 18> LF64;
 
@@ -19,39 +20,14 @@ static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 
 // -------------------------------------------------------------- M apply
 
-template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS) k_xpay_hop(Geom g, LF U, S t, S x, S out, double a)
-{
-    // out = a x - D_eo t  on even sites
-    typedef typename S::real real;
-    const int h = blockIdx.x * BS + threadIdx.x;
-    if (h >= g.Vh) return;
-    const Vec3<real> Dt = dslash_site(g, 0, h, U, t);
-    const Vec3<real> xv = x.load(h);
-    Vec3<real> o;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        o.c[c].re = fma((real)a, xv.c[c].re, -Dt.c[c].re);
-        o.c[c].im = fma((real)a, xv.c[c].im, -Dt.c[c].im);
-    }
-    out.store(h, o);
-}
-
-template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS) k_hop(Geom g, int p, LF U, S in, S out)
-{
-    const int h = blockIdx.x * BS + threadIdx.x;
-    if (h >= g.Vh) return;
-    out.store(h, dslash_site(g, p, h, U, in));
-}
-
 int apply_M_f64(stag_ctx ctx, double2* out, const double2* in, double mass, double2* tmp_odd, cudaStream_t s)
 {
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
     LF64 U{(const double2*)lk, ctx->g.Vh};
     const int grid = nblk(ctx->g.Vh, HOP_BS);
-    k_hop<LF64, SpinorF64, HOP_BS><<<grid, HOP_BS, 0, s>>>(ctx->g, 1, U, SpinorF64{(double2*)in}, SpinorF64{tmp_odd});
+    k_hop<LF64, SpinorF64, HOP_BS><<<grid, HOP_BS, 0, s>>>(ctx->g, 1, U, SpinorF64{(double2*)in}, SpinorF64{tmp_odd},
+                                                           nullptr, 0);
     k_xpay_hop<LF64, SpinorF64, HOP_BS><<<grid, HOP_BS, 0, s>>>(ctx->g, U, SpinorF64{tmp_odd}, SpinorF64{(double2*)in},
                                                                  SpinorF64{out}, mass * mass);
     STAG_CUDA_TRY(cudaGetLastError());
@@ -95,39 +71,6 @@ __global__ void __launch_bounds__(BS) k_cg_start_f64(int Vh, const double2* b, d
         s.sigma = sigma;
         s.done = (bb == 0.0) ? 1 : 0;
         *sc = s;
-    }
-}
-
-// r = b - (m^2 + sigma) x + D_eo t  (t = D_oe x), rr_true = |r|^2
-template <class LF, int BS>
-__global__ void __launch_bounds__(BS) k_true_resid_f64(Geom g, LF U, const double2* t, const double2* x,
-                                                       const double2* b, double2* r, CgScalars* sc, double* part,
-                                                       unsigned* cnt)
-{
-    __shared__ double red[BS / 32];
-    __shared__ bool last;
-    const int h = blockIdx.x * BS + threadIdx.x;
-    double d = 0.0;
-    const double m2s = sc->m2 + sc->sigma;
-    if (h < g.Vh) {
-        const Vec3<double> Dt = dslash_site(g, 0, h, U, SpinorF64{(double2*)t});
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double2 xv = x[(size_t)h * 3 + c], bv = b[(size_t)h * 3 + c];
-            const double re = bv.x - fma(m2s, xv.x, -Dt.c[c].re);
-            const double im = bv.y - fma(m2s, xv.y, -Dt.c[c].im);
-            r[(size_t)h * 3 + c] = make_double2(re, im);
-            d = fma(re, re, d);
-            d = fma(im, im, d);
-        }
-    }
-    const double bs = block_sum<BS>(d, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
-    if (!arrive_last(cnt, &last)) return;
-    const double rr = sum_partials<BS>(part, gridDim.x, red);
-    if (threadIdx.x == 0) {
-        *cnt = 0;
-        sc->rr_true = rr;
     }
 }
 
@@ -267,18 +210,23 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
     STAG_CUDA_TRY(cudaGetLastError());
     int restarts = 0;
     CgScalars* hs = ws->sc_host;
+    double prev_true = INFINITY;
     for (;;) {
         STAG_TRY(run_loop_f64(ctx, U, prm));
         // true residual r = b - M x, recomputed in double
         k_hop<LF64, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(g, 1, U, SpinorF64{ws->x},
-                                                                                      SpinorF64{ws->t});
+                                                                                      SpinorF64{ws->t}, nullptr, 0);
         k_true_resid_f64<LF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(
-            g, U, ws->t, ws->x, ws->b, ws->r, ws->sc, ctx->partials, ctx->counters);
+            g, U, ws->t, ws->x, ws->b, ws->r, ws->sc, ctx->partials, ctx->counters, 0);
         STAG_CUDA_TRY(cudaGetLastError());
         STAG_CUDA_TRY(cudaMemcpyAsync(hs, ws->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
         STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         if (hs->rr0 == 0.0 || hs->rr_true <= hs->tol2 || hs->status == STAG_BREAKDOWN || hs->iter >= hs->maxiter)
             break;
+        // A restart that did not halve the true residual norm means the
+        // iteration sits at its rounding floor: stop (NOT_CONVERGED).
+        if (!(hs->rr_true < 0.25 * prev_true) || restarts >= MAX_RESTARTS) break;
+        prev_true = hs->rr_true;
         ++restarts;
         k_cg_restart_f64<BLAS_BS><<<nblk(3 * g.Vh, BLAS_BS), BLAS_BS, 0, ctx->stream>>>(g.Vh, ws->r, ws->p, ws->sc);
         STAG_CUDA_TRY(cudaGetLastError());
@@ -305,6 +253,9 @@ void free_workspace(stag_ctx ctx)
     Workspace* ws = ctx->ws;
     if (!ws) return;
     free_graph_pair(ws->f64_graph, ws->f64_exec);
+    free_mixed(ws);
+    free_batches(ws);
+    for (auto& m : ws->ms) m.release();
     double2* bufs[] = {ws->x, ws->r, ws->p, ws->Ap, ws->b, ws->t};
     for (auto b : bufs)
         if (b) cudaFree(b);

@@ -18,8 +18,6 @@
 
 namespace stag {
 
-template <class T> struct Real2Double { static __device__ __forceinline__ double f(T v) { return (double)v; } };
-
 // Site contribution to a real inner product; float sites are summed in float
 // first (six terms) and enter the block sum in double.
 template <typename T>
@@ -145,6 +143,69 @@ __global__ void __launch_bounds__(BS) k_cg_p(int Vh, S r, S p, const CgScalars* 
         pv.c[c].im = fma(beta, pv.c[c].im, rv.c[c].im);
     }
     p.store(h, pv);
+}
+
+template <class LF, class S, int BS>
+__global__ void __launch_bounds__(BS) k_xpay_hop(Geom g, LF U, S t, S x, S out, double a)
+{
+    // out = a x - D_eo t  on even sites
+    typedef typename S::real real;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    if (h >= g.Vh) return;
+    const Vec3<real> Dt = dslash_site(g, 0, h, U, t);
+    const Vec3<real> xv = x.load(h);
+    Vec3<real> o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        o.c[c].re = fma((real)a, xv.c[c].re, -Dt.c[c].re);
+        o.c[c].im = fma((real)a, xv.c[c].im, -Dt.c[c].im);
+    }
+    out.store(h, o);
+}
+
+// out = D_{p,1-p} in; with guard set, only when a reliable update is due.
+template <class LF, class S, int BS>
+__global__ void __launch_bounds__(BS) k_hop(Geom g, int p, LF U, S in, S out, const CgScalars* sc, int guard)
+{
+    if (guard && !sc->reliable) return;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    if (h >= g.Vh) return;
+    out.store(h, dslash_site(g, p, h, U, in));
+}
+
+// r = b - (m^2 + sigma) x + D_eo t  (t = D_oe x), rr_true = |r|^2, double precision.
+// With guard set, only when a reliable update is due.
+template <class LF, int BS>
+__global__ void __launch_bounds__(BS) k_true_resid_f64(Geom g, LF U, const double2* t, const double2* x,
+                                                       const double2* b, double2* r, CgScalars* sc, double* part,
+                                                       unsigned* cnt, int guard)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    if (guard && !sc->reliable) return;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    double d = 0.0;
+    const double m2s = sc->m2 + sc->sigma;
+    if (h < g.Vh) {
+        const Vec3<double> Dt = dslash_site(g, 0, h, U, SpinorF64{(double2*)t});
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 xv = x[(size_t)h * 3 + c], bv = b[(size_t)h * 3 + c];
+            const double re = bv.x - fma(m2s, xv.x, -Dt.c[c].re);
+            const double im = bv.y - fma(m2s, xv.y, -Dt.c[c].im);
+            r[(size_t)h * 3 + c] = make_double2(re, im);
+            d = fma(re, re, d);
+            d = fma(im, im, d);
+        }
+    }
+    const double bs = block_sum<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!arrive_last(cnt, &last)) return;
+    const double rr = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        sc->rr_true = rr;
+    }
 }
 
 }  // namespace stag

@@ -190,6 +190,7 @@ __device__ __forceinline__ __half2 ldg_nc<__half2>(const __half2* p)
 template <typename S, int RECON>
 struct LinkField {
     typedef typename StoreTraits<S>::real real;
+    typedef S store;
     static constexpr int NE = (RECON == 12) ? 6 : 9;
     const S* base;
     int Vh;
@@ -217,6 +218,11 @@ struct SpinorF64 {
     typedef double real;
     static constexpr bool has_norm = false;
     double2* p;
+    // field k of a multi field whose fields are stride bytes apart
+    __host__ __device__ __forceinline__ SpinorF64 at(int k, size_t stride) const
+    {
+        return SpinorF64{(double2*)((char*)p + (size_t)k * stride)};
+    }
     __device__ __forceinline__ Vec3<double> load(int h) const
     {
         Vec3<double> v;
@@ -246,6 +252,10 @@ struct SpinorF32 {
     static constexpr bool has_norm = false;
     float2* p;
     int Vh;
+    __host__ __device__ __forceinline__ SpinorF32 at(int k, size_t stride) const
+    {
+        return SpinorF32{(float2*)((char*)p + (size_t)k * stride), Vh};
+    }
     __device__ __forceinline__ Vec3<float> load(int h) const
     {
         Vec3<float> v;
@@ -273,6 +283,10 @@ struct SpinorF16 {
     __half2* p;
     float* norm;
     int Vh;
+    __host__ __device__ __forceinline__ SpinorF16 at(int k, size_t stride) const
+    {
+        return SpinorF16{(__half2*)((char*)p + (size_t)k * stride), (float*)((char*)norm + (size_t)k * stride), Vh};
+    }
     __device__ __forceinline__ Vec3<float> load(int h) const
     {
         Vec3<float> v;

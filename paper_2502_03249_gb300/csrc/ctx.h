@@ -47,6 +47,7 @@ struct CgScalars {
     double delta2;    // mixed precision: delta^2
     double m2;        // mass^2 of M = m^2 - D_eo D_oe
     double sigma;     // shift added to M (multi-shift base system)
+    double rr_prev;   // mixed precision: |r|^2 before the last step (beta after a reliable update)
     int iter;         // M applications so far
     int maxiter;
     int status;       // 0 running/converged, STAG_NOT_CONVERGED, STAG_BREAKDOWN
@@ -80,6 +81,8 @@ struct stag_ctx_s {
     void* tmp_lo_out;
     size_t tmp_lo_bytes;
     stag::Workspace* ws;
+    void* tune;                // autotuner cache (tune.cu)
+    int last_rhs_block;        // right-hand sides per pass chosen by the last batched solve
 };
 
 namespace stag {
@@ -90,6 +93,10 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out);
 int convert_f64_to_lo(stag_ctx ctx, int prec, const double2* in, void* out, int nvec, cudaStream_t s);
 int convert_lo_to_f64(stag_ctx ctx, int prec, const void* in, double2* out, int nvec, cudaStream_t s);
 size_t lo_spinor_bytes(const Geom& g, int prec);
+
+int ensure_lo_tmp_public(stag_ctx ctx, size_t bytes);
+int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs, int nb,
+                 int* nb_used);
 
 // dslash.cu: out = D_{par_out, 1-par_out} in, storage chosen by prec/recon.
 // in/out are in the internal storage of prec (F64: canonical AoS).

@@ -3,19 +3,84 @@
 #pragma once
 
 #include "ctx.h"
+#include "graph.h"
 
 namespace stag {
 
+// Buffers of one mixed-precision configuration (inner precision x compression).
+struct MixedSlot {
+    void *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr;   // inner precision
+    void* xlo = nullptr;                                             // float accumulator of x
+    CgScalars* sc = nullptr;
+    LoopGraph lg;
+    int Vh = 0;
+    bool ready = false;
+    template <class S> S spinor(void* buf) const;
+};
+template <> inline SpinorF32 MixedSlot::spinor<SpinorF32>(void* buf) const { return SpinorF32{(float2*)buf, Vh}; }
+template <> inline SpinorF16 MixedSlot::spinor<SpinorF16>(void* buf) const
+{
+    return SpinorF16{(__half2*)buf, (float*)((__half2*)buf + (size_t)3 * Vh), Vh};
+}
+
+// Buffers of one batched configuration (inner precision x compression), for
+// up to cap systems: inner r p Ap t (S), xlo (F32 or F64), and the double
+// vectors x_hi r_hi b t64, all n fields back to back.
+struct BatchSlot {
+    void *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr, *xlo = nullptr;
+    double2 *x_hi = nullptr, *r_hi = nullptr, *b = nullptr, *t64 = nullptr;
+    CgScalars* sc = nullptr;
+    double* part = nullptr;
+    double* shifts = nullptr;
+    size_t s_stride = 0, sx_stride = 0, f64_stride = 0;
+    int Vh = 0, cap = 0, nrhs = 0, gx = 0, prec = 0, graph_nb = 0;
+    bool ready = false;
+    LoopGraph lg;
+    template <class S> S spinor(void* buf) const;
+    void release();
+};
+template <> inline SpinorF64 BatchSlot::spinor<SpinorF64>(void* buf) const { return SpinorF64{(double2*)buf}; }
+template <> inline SpinorF32 BatchSlot::spinor<SpinorF32>(void* buf) const { return SpinorF32{(float2*)buf, Vh}; }
+template <> inline SpinorF16 BatchSlot::spinor<SpinorF16>(void* buf) const
+{
+    return SpinorF16{(__half2*)buf, (float*)((__half2*)buf + (size_t)3 * Vh), Vh};
+}
+
+// Buffers of the multi-shift Krylov phase (inner precision): p_i and x_i of
+// every shift, r, Ap, t, the scalar records and the replicated source for the
+// refinement.
+struct MsSlot {
+    void *P = nullptr, *X = nullptr, *r = nullptr, *Ap = nullptr, *t = nullptr;
+    CgScalars* sc = nullptr;
+    struct MsState* ms = nullptr;
+    double* shifts = nullptr;
+    double2* brep = nullptr;
+    size_t stride = 0;
+    int Vh = 0, cap = 0, nshift = 0, base = 0, graph_n = 0, graph_base = -1;
+    bool ready = false;
+    LoopGraph lg;
+    template <class S> S spinor(void* buf) const;
+    void release();
+};
+template <> inline SpinorF64 MsSlot::spinor<SpinorF64>(void* buf) const { return SpinorF64{(double2*)buf}; }
+template <> inline SpinorF32 MsSlot::spinor<SpinorF32>(void* buf) const { return SpinorF32{(float2*)buf, Vh}; }
+
 struct Workspace {
-    // double-precision CG (even: x r p Ap b, odd: t), canonical layout
+    // double-precision CG (even: x r p Ap b, odd: t), canonical layout; the
+    // mixed solver uses x, r, b, t as its double-precision vectors
     double2 *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *b = nullptr, *t = nullptr;
     CgScalars* sc = nullptr;        // device scalar records
     CgScalars* sc_host = nullptr;   // pinned host mirror for the final read
     bool f64_ready = false;
     cudaGraph_t f64_graph = nullptr;
     cudaGraphExec_t f64_exec = nullptr;
+    MixedSlot mixed[2][2];          // [F32, F16][18, 12]
+    BatchSlot batch[3][2];          // [F64, F32, F16][18, 12]
+    MsSlot ms[2];                   // multi-shift [F64, F32]
 };
 
 int free_graph_pair(cudaGraph_t& g, cudaGraphExec_t& e);
+void free_mixed(Workspace* ws);
+void free_batches(Workspace* ws);
 
 }  // namespace stag

@@ -1,8 +1,9 @@
 """Parity of the double-precision M apply and CG solver against the CPU oracle.
 
 Bars: M applied to a vector within 1e-12 relative (L2); a solve to tol must
-have an oracle-recomputed true residual <= tol; two solves to 1e-14 agree to
-1e-12 relative (the solution error is bounded by cond(M) * residual).
+have an oracle-recomputed true residual <= tol; two solves near the rounding
+floor agree to 2 tol cond(M) (the solution error is bounded by cond(M) times
+the relative residual).
 """
 
 import numpy as np
@@ -73,16 +74,38 @@ def test_graph_and_host_loop_identical(stag):
     assert s3["iters"] == s1["iters"] and bool((x1 == x2).all())
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 8)])
-def test_cg_tight_solution_matches_oracle(stag, dims):
-    mass = 0.1
+@pytest.mark.parametrize("dims,mass,tol", [((4, 4, 4, 4), 0.1, 1e-13), ((8, 8, 8, 8), 0.5, 3e-14)])
+def test_cg_tight_solution_matches_oracle(stag, dims, mass, tol):
+    """Both solves to a residual near the double-precision floor.  Each solution
+    is within tol ||b|| / lambda_min of the exact one and ||x|| >= ||b|| / lambda_max,
+    so the two agree to 2 tol cond(M) relative.  cond(M) is computed from the dense
+    M at 4^4; at 8^4 it is bounded by (m^2 + 64) / m^2 (||D_eo|| <= 8 for unitary
+    links)."""
     ctx, U = setup(stag, dims, seed=321)
     b = li.gaussian_half(dims, seed=322)
     x = ctx.new_half()
-    ctx.cg_solve(x, dev(b), mass, tol=1e-14)
-    x_cpu, _, rel_cpu, st = orc.cg(dims, U, mass, b, tol=1e-14)
-    assert st == 0
-    assert rel(host(x), x_cpu) <= 1e-12
+    st = ctx.cg_solve(x, dev(b), mass, tol=tol)
+    x_cpu, _, rel_cpu, st_cpu = orc.cg(dims, U, mass, b, tol=tol)
+    assert st_cpu == 0 and st["status"] == 0
+    if dims == (4, 4, 4, 4):
+        Ve = li.volume(dims) // 2
+        M = np.array([orc.apply_M(dims, U, mass, e.reshape(Ve, 3)).ravel() for e in np.eye(3 * Ve)]).T
+        ev = np.linalg.eigvalsh(M)
+        cond = ev.max() / ev.min()
+    else:
+        cond = (mass ** 2 + 64) / mass ** 2
+    assert rel(host(x), x_cpu) <= 2 * tol * cond
+
+
+def test_cg_stagnation_stops(stag):
+    """A tolerance below the rounding floor ends with NOT_CONVERGED after a few
+    restarts instead of spinning until maxiter."""
+    dims = (8, 8, 8, 8)
+    ctx, U = setup(stag, dims, seed=323)
+    b = dev(li.gaussian_half(dims, seed=324))
+    x = ctx.new_half()
+    st = ctx.cg_solve(x, b, 0.1, tol=1e-17, raise_on_fail=False)
+    assert st["status"] == 1 and st["restarts"] < 10 and st["true_rel_residual"] < 1e-12
 
 
 def test_cg_32c8_workload(stag):
