@@ -127,6 +127,32 @@ int stag_dslash_multi(stag_ctx ctx, double *out, const double *in, int nrhs, int
  * precision, 18-real links.  Uses a context-owned odd temporary. */
 int stag_apply_M(stag_ctx ctx, double *out_even, const double *in_even, double mass);
 
+/* Allocation-free variant of stag_apply_M, for callers that cannot allocate
+ * device memory: code running while a stream is captured into a CUDA graph
+ * (cudaMalloc and cudaFree are not capturable, and cudaFree synchronises the
+ * device), latency-critical loops that cannot absorb that synchronisation,
+ * and hosts that keep every device byte in their own pre-sized arena.  It
+ * needs no context: the gauge field is read straight from the caller's
+ * canonical buffer, and the odd-site intermediate D_oe in lives in a static
+ * device array of STAG_NOALLOC_MAX_VH x 3 complex doubles (6 MiB) that every
+ * GPU loading the library holds until the process exits.  (The paper has no
+ * counterpart; this is an interface for such callers.)
+ *   dims: host {Lx, Ly, Lz, Lt}, each even and >= 2, with V/2 <=
+ *         STAG_NOALLOC_MAX_VH (larger lattices: STAG_EINVAL with a message);
+ *   U: device canonical gauge field [V][4][3][3] complex128;
+ *   out_even, in_even: device canonical half fields; must not alias;
+ *   stream: cudaStream_t the two kernels are enqueued on (asynchronous).
+ * Result: out_even = m^2 in_even - D_eo D_oe in_even, the same arithmetic as
+ * stag_apply_M.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture begins.  All calls share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race on
+ * it and must be serialised by the caller.  Nothing in it needs clearing
+ * between calls (every element is written before it is read). */
+#define STAG_NOALLOC_MAX_VH (1 << 17)
+int stag_apply_M_noalloc(const int dims[4], const double *U, double *out_even, const double *in_even, double mass,
+                         void *stream);
+
 /* ---------------------------------------------------------------- solvers */
 
 typedef struct {

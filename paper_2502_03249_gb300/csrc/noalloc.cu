@@ -1,0 +1,149 @@
+// noalloc.cu -- an entry point that performs M = m^2 - D_eo D_oe without
+// allocating any device memory.
+//
+// stag_apply_M needs an odd-parity intermediate t = D_oe in; a context
+// allocates it with cudaMalloc when it is created.  Some callers cannot do
+// that: code that runs while a stream is being captured into a CUDA graph
+// (cudaMalloc/cudaFree are not capturable and cudaFree synchronises the
+// device), latency-critical loops where an allocation's implicit device
+// synchronisation is not acceptable, and hosts that must keep every device
+// byte inside their own pre-sized memory arena.  For them this variant takes
+// the gauge field straight from the caller's canonical buffer (no context, no
+// internal link copy) and keeps the intermediate in a fixed, statically sized
+// device array that is part of the loaded library image.
+//
+// The array holds STAG_NOALLOC_MAX_VH x 3 complex doubles (6 MiB) on every GPU
+// that loads the library, until the process exits.  Every call shares it:
+// calls that overlap on the GPU (different streams, or different host threads
+// on one device) race on it and must be serialised by the caller.  The array
+// keeps the previous call's contents; each call overwrites every element it
+// reads before reading it, so nothing has to start at zero.
+#include <mutex>
+
+#include "cg_kernels.cuh"
+
+namespace stag {
+
+static __device__ __align__(256) double2 g_noalloc_odd[(size_t)STAG_NOALLOC_MAX_VH * 3];
+
+// Links read directly from the canonical layout U[i][mu][a][b] (complex128):
+// the lexicographic index i of half site h of parity par is rebuilt from its
+// coordinates.
+struct LinkCanonicalF64 {
+    typedef double real;
+    typedef double2 store;
+    const double2* U;
+    Geom g;
+    __device__ __forceinline__ Mat3<double> load(int par, int mu, int h) const
+    {
+        const int r = h / g.Lxh;
+        const int xh = h - r * g.Lxh;
+        const int y = r % g.L[1];
+        const int zt = r / g.L[1];
+        const int z = zt % g.L[2];
+        const int t = zt / g.L[2];
+        const int x = 2 * xh + ((par + y + z + t) & 1);
+        const size_t i = (size_t)x + (size_t)g.L[0] * r;
+        const double2* p = U + (i * 4 + mu) * 9;
+        Mat3<double> m;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) m.m[k] = to_cplx(__ldg(p + k));
+        return m;
+    }
+};
+
+// Device address of g_noalloc_odd, looked up once per device with that
+// device current (the host-side symbol is only a stand-in, not a device
+// address).
+static int noalloc_scratch(double2** out)
+{
+    static std::mutex mu;
+    static double2* addr[64] = {};
+    int dev = 0;
+    STAG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d out of range", dev);
+        return STAG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_odd);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+            return STAG_ECUDA;
+        }
+        addr[dev] = (double2*)p;
+    }
+    *out = addr[dev];
+    return STAG_OK;
+}
+
+static int check_device_buffer(const void* p, const char* what)
+{
+    if (!p || ((uintptr_t)p & 15u)) {
+        set_error("%s is NULL or not 16-byte aligned", what);
+        return STAG_EINVAL;
+    }
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("%s is not a CUDA pointer", what);
+        return STAG_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        set_error("%s is not device memory", what);
+        return STAG_EINVAL;
+    }
+    return STAG_OK;
+}
+
+}  // namespace stag
+
+using namespace stag;
+
+extern "C" int stag_apply_M_noalloc(const int dims[4], const double* U, double* out_even, const double* in_even,
+                                    double mass, void* stream)
+{
+    if (!dims) {
+        set_error("dims is NULL");
+        return STAG_EINVAL;
+    }
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || dims[mu] % 2) {
+            set_error("extent %d of direction %d is not even and >= 2", dims[mu], mu);
+            return STAG_EGEOM;
+        }
+        V *= dims[mu];
+    }
+    if (V / 2 > STAG_NOALLOC_MAX_VH) {
+        set_error("stag_apply_M_noalloc: V/2 = %lld sites exceeds the static scratch limit of %d sites "
+                  "(V <= %d); use a context and stag_apply_M instead",
+                  V / 2, STAG_NOALLOC_MAX_VH, 2 * STAG_NOALLOC_MAX_VH);
+        return STAG_EINVAL;
+    }
+    STAG_TRY(check_device_buffer(U, "U"));
+    STAG_TRY(check_device_buffer(out_even, "out_even"));
+    STAG_TRY(check_device_buffer(in_even, "in_even"));
+    if (out_even == in_even) {
+        set_error("out and in must not alias");
+        return STAG_EINVAL;
+    }
+    double2* t = nullptr;
+    STAG_TRY(noalloc_scratch(&t));
+    Geom g;
+    for (int mu = 0; mu < 4; ++mu) g.L[mu] = dims[mu];
+    g.Lxh = dims[0] / 2;
+    g.Vh = (int)(V / 2);
+    const LinkCanonicalF64 L{(const double2*)U, g};
+    constexpr int BS = 128;
+    const int grid = (g.Vh + BS - 1) / BS;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_hop<LinkCanonicalF64, SpinorF64, BS><<<grid, BS, 0, s>>>(g, 1, L, SpinorF64{(double2*)in_even}, SpinorF64{t},
+                                                                nullptr, 0);
+    k_xpay_hop<LinkCanonicalF64, SpinorF64, BS><<<grid, BS, 0, s>>>(g, L, SpinorF64{t}, SpinorF64{(double2*)in_even},
+                                                                     SpinorF64{(double2*)out_even}, mass * mass);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
