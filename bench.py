@@ -1,16 +1,20 @@
 """Benchmark of the staggered Dslash and even-odd CG path on GB300.
 
-Workload (one GPU): the 32^3 x 8 lattice, smooth links exp(0.3 i H), m = 0.01,
-Gaussian source, plain double precision (F64 storage, 18-real links).  One
-step is a complete CG solve of M x = b to a true relative residual of 1e-10:
-every half-Dslash application, the fused BLAS and reductions, and the
-device-side iteration loop, with the inputs resident in HBM.
+Headline step (one GPU): the 32^3 x 8 lattice, smooth links exp(0.3 i H),
+m = 0.01, Gaussian source.  One step is a complete double-precision CG solve
+of M x = b to a true relative residual of 1e-10 -- every half-Dslash
+application, the BLAS and reductions, the device-side iteration loop -- with
+the inputs resident in HBM and L2 flushed before every step.  The operator
+passes use the library's default double-precision arithmetic (double storage,
+double-float arithmetic on the FP32 pipe; IEEE-double passes are timed beside
+it).
 
-Printed value: Dslash GFLOP/s sustained over the solve = 570 flop x V/2 sites x
-(half-Dslash applications in the solve) / solve time (the paper's 570
-flop/site count, Sec. 4.3).  Extra keys report CG time-to-solution, the
-standalone Dslash kernel against its roofline, an end-to-end number through
-the C ABI with host buffers, and the CPU oracle timed on the host cores.
+Printed value: Dslash GFLOP/s sustained over the solve = 570 flop x V/2 sites
+x (half-Dslash applications in the solve) / solve time (the paper's 570
+flop/site count, Sec. 4.3).  Further keys: CG time-to-solution, the Dslash
+kernel against its roofline, an end-to-end number through the C ABI with host
+buffers, mixed-precision, batched multi-RHS, multi-shift and force results on
+the workloads that name them, and the CPU oracle timed on the host cores.
 
 ``--impl reference`` times the CPU oracle on the same workload (bounded
 samples: a few CG iterations per step) and prints the same line with
@@ -31,8 +35,6 @@ import subprocess
 import sys
 import time
 
-import numpy as np
-
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -44,6 +46,9 @@ FLOP_PER_SITE = 570            # Sec. 4.3: per output site of one half-Dslash
 WORKLOAD_INDEX = 1             # 32^3 x 8 smooth eps=0.3, m=0.01
 TOL = 1e-10
 L2_FLUSH_BYTES = 512 << 20     # larger than the 129 MB L2
+SHIFTS12 = [10.0 ** (-5 + 5 * i / 11) for i in range(12)]
+F64_IEEE, F64X = 0, 3
+
 
 # algorithmic bytes per output site of a half-Dslash: 8 links read once,
 # the input spinor once, the output once (links are each used once per half)
@@ -68,6 +73,15 @@ def load_peaks():
             d = json.load(f)
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def load_traffic():
+    """DRAM bytes per launch of the profiled kernels (ncu captures, profiles/traffic.json)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
 
 
 # FP64 FMA rate of GB300 from unit counts and clock: the FP64 pipe issues
@@ -126,6 +140,23 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """Maximum of a per-rank time over all ranks (the timing harness's only collective)."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(ws: int, vh: int, half_dslash_per_step: float, ms_per_step: float) -> float:
+    """Whole-job Dslash GFLOP/s: every rank solves its own system, so the units of
+    work are summed over ranks and divided by the slowest rank's time."""
+    return ws * FLOP_PER_SITE * vh * half_dslash_per_step / (ms_per_step * 1e-3) * 1e-9
 
 
 def dist_setup():
@@ -192,14 +223,48 @@ def cpu_baseline_sample(dims, U, b, mass, Vh, budget_s=12.0):
                       f"{dt:.1f} s)"}
 
 
-# ---------------------------------------------------------------- ours
+# ---------------------------------------------------------------- helpers
+
+class Timer:
+    """CUDA-event timing of a callable on the current stream, L2 flushed before each call."""
+
+    def __init__(self, torch, flush):
+        self.torch = torch
+        self.flush = flush
+
+    def __call__(self, fn, reps=3, warm=1):
+        torch = self.torch
+        for _ in range(warm):
+            fn()
+        out, ts = None, []
+        stream = torch.cuda.current_stream()
+        for _ in range(reps):
+            self.flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), out
+
+
+def dslash_kernel_entry(timer, ctx, psi, out, prec, recon, vh, hbm):
+    ms, _ = timer(lambda: ctx.dslash_eo(out, psi, prec, recon), reps=20, warm=3)
+    pb = {0: 8, 3: 8, 1: 4, 2: 2}[prec]
+    per_site = dslash_bytes_per_site(pb, recon) + (8 if prec == 2 else 0)
+    gbs = per_site * vh / (ms * 1e-3) * 1e-9
+    return {"ms": ms, "gflops": FLOP_PER_SITE * vh / (ms * 1e-3) * 1e-9, "achieved_gbs": gbs,
+            "frac_of_hbm": gbs / hbm, "algorithmic_bytes_per_site": per_site}
+
 
 def profile_kernel(args, stag, torch):
     """A few launches of one operator on the workload, nothing timed (an ncu target)."""
     name = args.profile_kernel
     kern, _, dtxt = name.partition("@")
     parts = kern.split("_")
-    prec = {"f64": stag.F64, "f32": stag.F32, "f16": stag.F16}[parts[1]]
+    prec = {"f64": stag.F64, "f32": stag.F32, "f16": stag.F16, "f64x": stag.F64X}[parts[1]]
     recon = int(parts[2])
     w = li.WORKLOADS[WORKLOAD_INDEX]
     dims = tuple(int(v) for v in dtxt.split("x")) if dtxt else w["dims"]
@@ -215,6 +280,115 @@ def profile_kernel(args, stag, torch):
     return 0
 
 
+def half_dslash(st):
+    # two half-Dslashes per M application, one more M per true-residual check
+    return 2 * (st["iters"] + st["restarts"] + 1)
+
+
+# ---------------------------------------------------------------- sections
+
+def section_48c12(stag, torch, timer, hbm):
+    """48^3 x 12, eps = 0.2, m = 0.002: double CG (both arithmetics) vs mixed F32/F16; Dslash kernels."""
+    w = li.WORKLOADS[2]
+    dims, mass = w["dims"], w["mass"]
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(li.random_links_torch(dims, "smooth", w["eps"], seed=li.workload_seed(2, 0)))
+    b = li.gaussian_half_torch(dims, seed=li.workload_seed(2, 1))
+    x = ctx.new_half()
+    vh = ctx.Vh
+    res = {"workload": w["name"] + " (inputs from the torch generator)"}
+    ms, st = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, f64_arith=F64X), reps=2)
+    res["cg_f64x"] = {"time_to_solution_ms": ms, "iters": st["iters"], "true_rel_residual": st["true_rel_residual"]}
+    ms_i, st = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, f64_arith=F64_IEEE), reps=2)
+    res["cg_ieee_f64"] = {"time_to_solution_ms": ms_i, "iters": st["iters"],
+                          "true_rel_residual": st["true_rel_residual"]}
+    for name, prec in (("mixed_f32_12", stag.F32), ("mixed_f16_12", stag.F16)):
+        m, s = timer(lambda: ctx.cg_solve_mixed(x, b, mass, tol=TOL, inner_prec=prec, inner_recon=12), reps=2)
+        res[name] = {"time_to_solution_ms": m, "iters": s["iters"], "reliable_updates": s["reliable_updates"],
+                     "true_rel_residual": s["true_rel_residual"], "speedup_vs_cg_f64x": ms / m,
+                     "speedup_vs_cg_ieee_f64": ms_i / m}
+    psi = li.gaussian_half_torch(dims, seed=5)
+    out = ctx.new_half()
+    res["dslash"] = {name: dslash_kernel_entry(timer, ctx, psi, out, p, r, vh, hbm)
+                     for name, p, r in (("f64x_18", F64X, 18), ("f64_18", F64_IEEE, 18), ("f32_12", stag.F32, 12),
+                                        ("f16_12", stag.F16, 12))}
+    ctx.close()
+    return res
+
+
+def section_32c16(stag, torch, timer):
+    """32^3 x 16, eps = 0.3, m = 0.005: 16 RHS batched, 12 shifts multi-shift, against sequential solves."""
+    w = li.WORKLOADS[3]
+    dims, mass = w["dims"], w["mass"]
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(li.random_links_torch(dims, "smooth", w["eps"], seed=li.workload_seed(3, 0)))
+    B = li.gaussian_half_torch(dims, seed=li.workload_seed(3, 1), nvec=16)
+    X = ctx.new_half(16)
+    res = {"workload": w["name"] + " (inputs from the torch generator)"}
+    ms_b, st = timer(lambda: ctx.cg_solve_multi(X, B, mass, tol=TOL, inner_prec=stag.F32, inner_recon=12), reps=2)
+    res["batched_16rhs_f32_12"] = {"time_to_solution_ms": ms_b, "rhs_block": ctx.last_rhs_block(),
+                                   "max_iters": max(s["iters"] for s in st),
+                                   "max_true_rel_residual": max(s["true_rel_residual"] for s in st)}
+    xs = ctx.new_half()
+
+    def seq_f64():
+        return [ctx.cg_solve(xs, B[k], mass, tol=TOL) for k in range(16)]
+
+    ms_s, _ = timer(seq_f64, reps=1)
+    res["sequential_16_cg_f64x_ms"] = ms_s
+    res["batched_speedup_vs_sequential_f64x"] = ms_s / ms_b
+    b = B[0].contiguous()
+    Xs = ctx.new_half(12)
+    ms_m, st = timer(lambda: ctx.cg_solve_multishift(Xs, b, SHIFTS12, mass, tol=TOL), reps=2)
+    res["multishift_12"] = {"time_to_solution_ms": ms_m, "krylov_iters": st[0]["restarts"],
+                            "max_true_rel_residual": max(s["true_rel_residual"] for s in st)}
+
+    def seq_shifted():
+        return [ctx.cg_solve_shifted(xs, b, mass, s, tol=TOL) for s in SHIFTS12]
+
+    ms_q, _ = timer(seq_shifted, reps=1)
+    res["sequential_12_shifted_cg_f64x_ms"] = ms_q
+    res["multishift_speedup_vs_sequential_f64x"] = ms_q / ms_m
+    ctx.close()
+    return res
+
+
+def section_force(stag, torch, timer, hbm):
+    """64^3 x 16, eps = 0.3, m = 0.01: force kernel given X, and the autograd forward + backward."""
+    w = li.WORKLOADS[5]
+    dims, mass = w["dims"], w["mass"]
+    ctx = stag.Context(dims)
+    U = li.random_links_torch(dims, "smooth", w["eps"], seed=li.workload_seed(5, 0))
+    ctx.upload_gauge(U)
+    phi = li.gaussian_half_torch(dims, seed=li.workload_seed(5, 1))
+    S, X, st = ctx.fermion_action(phi, mass, tol=TOL, inner_prec=0)
+    P = torch.empty_like(U)
+    ms_f, _ = timer(lambda: ctx.fermion_force(X, P=P), reps=5, warm=2)
+    nlinks = 4 * ctx.V
+    # per link: the link read (144 B) and P written (144 B); X and Y read once per site (96 B per 4 links)
+    bpl = 144 + 144 + 24
+    gbs = bpl * nlinks / (ms_f * 1e-3) * 1e-9
+    res = {"workload": w["name"] + " (inputs from the torch generator)",
+           "force_kernel_ms": ms_f, "links": nlinks, "algorithmic_bytes_per_link": bpl, "achieved_gbs": gbs,
+           "frac_of_hbm": gbs / hbm, "action_solve_iters": st["iters"]}
+    Ug = U.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        S = stag.StaggeredAction(Ug, phi, ctx, mass, tol=TOL)
+        S.backward()
+        return S
+
+    ms_ab, _ = timer(fwd_bwd, reps=1)
+    res["autograd_forward_backward_ms"] = ms_ab
+    res["autograd_note"] = "forward solves X; backward re-solves X (not stored) and applies the force kernel"
+    ctx.close()
+    del Ug, U, P
+    torch.cuda.empty_cache()
+    return res
+
+
+# ---------------------------------------------------------------- ours
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,11 +396,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline step only (no workload sections)")
     ap.add_argument("--use-graph", type=int, default=1,
                     help="1: device-side loop in one CUDA graph; 0: host-driven loop (per-kernel profiling)")
+    ap.add_argument("--f64-arith", type=int, default=F64X, choices=[F64_IEEE, F64X],
+                    help="arithmetic of the headline solve's operator passes (0 IEEE double, 3 double-float)")
     ap.add_argument("--profile-kernel", default=None,
-                    help="only run a few launches of one kernel on the workload (for ncu): "
-                         "dslash_f64_18, dslash_f32_12, dslash_f16_12, ...; optional @LXxLYxLZxLT lattice")
+                    help="only run a few launches of one operator on the workload (for ncu): "
+                         "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ...; optional @LXxLYxLZxLT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -255,14 +432,17 @@ def main():
     x = ctx.new_half()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    timer = Timer(torch, flush)
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    ug, arith = args.use_graph, args.f64_arith
 
     def barrier():
         if ws > 1:
             dist.barrier()
 
-    ug = args.use_graph
     for _ in range(args.warmup):
-        st = ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug)
+        st = ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, f64_arith=arith)
     torch.cuda.synchronize()
 
     # ---- timed region: K complete solves, L2 flushed between them
@@ -275,86 +455,82 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug)
+            st = ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, f64_arith=arith)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
             stats.append(st)
     torch.cuda.synchronize()
     barrier()
-    t_sum = sum(times)
-    if ws > 1:
-        tt = torch.tensor([t_sum], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_sum = float(tt.item())
+    t_sum = max_over_ranks(sum(times), ws, dev)
     ms_per_step = t_sum / args.steps
-    n_half = [2 * (s["iters"] + s["restarts"] + 1) for s in stats]
-    half_per_step = statistics.mean(n_half)
-    value = ws * FLOP_PER_SITE * Vh * half_per_step / (ms_per_step * 1e-3) * 1e-9
+    half_per_step = statistics.mean(half_dslash(s) for s in stats)
+    value = weak_scaling_value(ws, Vh, half_per_step, ms_per_step)
     launches = sum(1 + 4 * s["iters"] + 2 * (s["restarts"] + 1) + s["restarts"] for s in stats)
-
-    # ---- standalone Dslash kernel (F64/18) for the roofline: events per launch, L2 flushed
-    out = ctx.new_half()
-    psi = torch.from_numpy(li.gaussian_half(dims, seed=99)).to(dev)
-    for _ in range(5):
-        ctx.dslash_eo(out, psi)
-    ks = []
-    for _ in range(30):
-        flush.fill_(2.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.dslash_eo(out, psi)
-        e1.record(stream)
-        e1.synchronize()
-        ks.append(e0.elapsed_time(e1))
-    k_ms = statistics.mean(ks)
-    k_bytes = dslash_bytes_per_site(8, 18) * Vh
-    k_gbs = k_bytes / (k_ms * 1e-3) * 1e-9
-    k_gflops = FLOP_PER_SITE * Vh / (k_ms * 1e-3) * 1e-9
-    peaks, peak_kind = load_peaks()
-    hbm = float(peaks["hbm_gbs"])
     clocks = clk.summary()
+
+    # ---- the same solve with IEEE-double operator passes
+    ms_ieee, st_ieee = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, f64_arith=F64_IEEE), reps=3)
+
+    # ---- the dominant kernel, standalone: per-launch CUDA events, L2 flushed before each
+    psi = torch.from_numpy(li.gaussian_half(dims, seed=99)).to(dev)
+    out = ctx.new_half()
+    kern = {"f64x_18": dslash_kernel_entry(timer, ctx, psi, out, F64X, 18, Vh, hbm),
+            "f64_18": dslash_kernel_entry(timer, ctx, psi, out, F64_IEEE, 18, Vh, hbm)}
+    main_k = kern["f64x_18" if arith == F64X else "f64_18"]
+    traffic = load_traffic().get("dslash_f64x_18_32c8" if arith == F64X else "dslash_f64_18_32c8")
     fp64_peak = fp64_peak_gflops()
+    if arith == F64X:
+        roofline = {"kernel": "k_dslash<LinkFieldDF<18>, SpinorF64asDF> (stag_dslash_eo, STAG_F64X)",
+                    "bound": "hbm", "achieved": main_k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": main_k["achieved_gbs"] / hbm, "traffic": traffic,
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind} copy bandwidth)",
+                    "algorithmic_bytes_per_launch": main_k["algorithmic_bytes_per_site"] * Vh,
+                    "kernel_ms": main_k["ms"]}
+    else:
+        roofline = {"kernel": "k_dslash<LinkField<double2,18>, SpinorF64> (stag_dslash_eo, STAG_F64)",
+                    "bound": "alu", "achieved": main_k["gflops"], "peak": fp64_peak, "unit": "GFLOP/s",
+                    "frac": main_k["gflops"] / fp64_peak, "traffic": traffic,
+                    "peak_source": "FP64 FMA rate from unit counts and max clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
+                    "kernel_ms": main_k["ms"]}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     b_host = torch.from_numpy(b_np).pin_memory()
     x_host = torch.empty_like(b_host).pin_memory()
     xd = ctx.new_half()
     bd = torch.empty_like(xd)
-    e2e_t = []
-    e2e_half = []
-    for _ in range(max(2, args.steps // 2)):
+    e2e_t, e2e_half = [], []
+    for _ in range(max(3, args.steps // 4)):
         flush.fill_(3.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         bd.copy_(b_host, non_blocking=True)
-        st = ctx.cg_solve(xd, bd, mass, tol=TOL)
+        st = ctx.cg_solve(xd, bd, mass, tol=TOL, use_graph=ug, f64_arith=arith)
         x_host.copy_(xd, non_blocking=True)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-        e2e_half.append(2 * (st["iters"] + st["restarts"] + 1))
+        e2e_half.append(half_dslash(st))
     e2e_val = FLOP_PER_SITE * Vh * statistics.mean(e2e_half) / statistics.mean(e2e_t) * 1e-9
 
-    # ---- mixed precision on the same workload: time-to-solution at the same true residual
+    # ---- mixed precision on the same workload
     mixed = {}
-    for name, prec, recon in (("f32_12", stag.F32, 12), ("f16_12", stag.F16, 12)):
+    for name, prec in (("f32_12", stag.F32), ("f16_12", stag.F16)):
         xm = ctx.new_half()
-        for _ in range(2):
-            ctx.cg_solve_mixed(xm, b, mass, tol=TOL, inner_prec=prec, inner_recon=recon, use_graph=ug)
-        tm = []
-        for _ in range(3):
-            flush.fill_(4.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sm = ctx.cg_solve_mixed(xm, b, mass, tol=TOL, inner_prec=prec, inner_recon=recon, use_graph=ug)
-            e1.record(stream)
-            e1.synchronize()
-            tm.append(e0.elapsed_time(e1))
-        mixed[name] = {"time_to_solution_ms": statistics.median(tm), "iters": sm["iters"],
-                       "reliable_updates": sm["reliable_updates"], "true_rel_residual": sm["true_rel_residual"],
-                       "speedup_vs_f64": ms_per_step / statistics.median(tm)}
+        m, sm = timer(lambda: ctx.cg_solve_mixed(xm, b, mass, tol=TOL, inner_prec=prec, inner_recon=12,
+                                                 use_graph=ug), reps=3)
+        mixed[name] = {"time_to_solution_ms": m, "iters": sm["iters"], "reliable_updates": sm["reliable_updates"],
+                       "true_rel_residual": sm["true_rel_residual"], "speedup_vs_f64": ms_per_step / m}
+
+    sections = {}
+    if rank == 0 and ws == 1 and not args.quick:
+        ctx.close()
+        for name, fn in (("w48c12", lambda: section_48c12(stag, torch, timer, hbm)),
+                         ("w32c16", lambda: section_32c16(stag, torch, timer)),
+                         ("force_64c16", lambda: section_force(stag, torch, timer, hbm))):
+            try:
+                sections[name] = fn()
+            except Exception as e:   # a failed section is reported, not hidden
+                sections[name] = {"error": repr(e)}
 
     if rank != 0:
         if ws > 1:
@@ -377,28 +553,25 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64 storage; operator in double-float (f32x2)" if arith == F64X else "f64",
         "data": "synthetic",
         "config": {
             "workload": w["name"] + ", double-precision CG to true residual 1e-10 (one solve per step)",
-            "dims": list(dims), "mass": mass, "links": "exp(0.3 i H), 18-real F64", "tol": TOL,
+            "dims": list(dims), "mass": mass, "links": "exp(0.3 i H), 18-real double", "tol": TOL,
+            "f64_arith": "double-float (STAG_F64X)" if arith == F64X else "IEEE double (STAG_F64)",
             "l2": "flushed (512 MB write) before every step; working set 151 MB links + 6 MB per vector",
             "value_definition": "570 flop x V/2 x half-Dslash applications per solve / solve time",
         },
         "cg": {"time_to_solution_ms": ms_per_step, "iters": last["iters"], "restarts": last["restarts"],
                "true_rel_residual": last["true_rel_residual"], "half_dslash_per_solve": half_per_step},
-        "roofline": {
-            "kernel": "k_dslash<F64/18> (stag_dslash_eo)", "bound": "alu",
-            "achieved": k_gflops, "peak": fp64_peak, "unit": "GFLOP/s", "frac": k_gflops / fp64_peak,
-            "traffic": None,
-            "peak_source": "FP64 FMA rate from unit counts and max clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
-            "hbm": {"achieved_gbs": k_gbs, "peak_gbs": hbm, "frac": k_gbs / hbm, "peak_source": peak_kind,
-                    "algorithmic_bytes_per_site": dslash_bytes_per_site(8, 18)},
-            "kernel_ms": k_ms,
-        },
+        "cg_ieee_f64": {"time_to_solution_ms": ms_ieee, "iters": st_ieee["iters"],
+                        "true_rel_residual": st_ieee["true_rel_residual"]},
+        "roofline": roofline,
+        "dslash_kernels_32c8": kern,
         "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": int(b_host.numel() * 16),
                 "d2h_bytes_per_step": int(x_host.numel() * 16), "seconds_per_step": statistics.mean(e2e_t)},
         "mixed": mixed,
+        "sections": sections,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,

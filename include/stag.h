@@ -64,7 +64,12 @@ enum stag_status {
 enum stag_prec {
     STAG_F64 = 0, /* double links and spinors, double arithmetic */
     STAG_F32 = 1, /* float links and spinors, float arithmetic */
-    STAG_F16 = 2  /* half links, half spinors with a float norm per site, float arithmetic */
+    STAG_F16 = 2, /* half links, half spinors with a float norm per site, float arithmetic */
+    STAG_F64X = 3 /* double links and spinors (same bytes as STAG_F64), double-float arithmetic:
+                     each double carried as hi + lo floats (48-bit significand) on the FP32 pipe,
+                     whose rate on GB300 is 64x the FP64 one; 18-real links only.  Results agree
+                     with STAG_F64 to ~1e-14 relative; values below 2^-74 in magnitude keep only
+                     24 significant bits. */
 };
 
 /* Link compression (Sec. 4.3): 18 reals per link, or 12 (rows 0 and 1; row 2
@@ -165,6 +170,9 @@ typedef struct {
     int inner_prec;        /* mixed precision: STAG_F32 or STAG_F16 */
     int inner_recon;       /* mixed precision: STAG_RECON_18 or STAG_RECON_12 */
     int rhs_block;         /* batched solves: right-hand sides per operator pass; 0: autotune */
+    int f64_arith;         /* arithmetic of the double-precision operator passes (stag_cg_solve,
+                              the reliable updates of the mixed solver): STAG_F64 (IEEE double)
+                              or STAG_F64X (double-float) */
 } stag_solver_params;
 
 typedef struct {
@@ -178,7 +186,10 @@ typedef struct {
 } stag_solver_stats;
 
 /* Fill *p with defaults: tol 1e-10, maxiter 100000, use_graph 1, check_every 25,
- * delta 0.1, inner_prec STAG_F32, inner_recon STAG_RECON_12, rhs_block 0. */
+ * delta 0.1, inner_prec STAG_F32, inner_recon STAG_RECON_12, rhs_block 0,
+ * f64_arith STAG_F64X (double-float operator passes: on GB300 about twice as
+ * fast as IEEE double ones, which are FP64-ALU-bound, with results equal to
+ * ~1e-14 relative). */
 void stag_solver_params_default(stag_solver_params *p);
 
 /* Solve M x = b by conjugate gradient in double precision (Sec. 1 and
@@ -191,6 +202,10 @@ void stag_solver_params_default(stag_solver_params *p);
  * negative error. */
 int stag_cg_solve(stag_ctx ctx, double *x_even, const double *b_even, double mass,
                   const stag_solver_params *params, stag_solver_stats *stats);
+
+/* As stag_cg_solve for the shifted system (M + sigma) x = b, sigma >= 0. */
+int stag_cg_solve_shifted(stag_ctx ctx, double *x_even, const double *b_even, double mass, double sigma,
+                          const stag_solver_params *params, stag_solver_stats *stats);
 
 /* Mixed-precision CG with reliable updates on M x = b.  The inner iteration
  * stores links and vectors in params->inner_prec (STAG_F32, or STAG_F16 with a
@@ -235,6 +250,41 @@ int stag_cg_solve_multi(stag_ctx ctx, double *X, const double *B, int nrhs, doub
  * the solver a rational hybrid Monte Carlo force needs.) */
 int stag_cg_solve_multishift(stag_ctx ctx, double *X, const double *b, const double *shifts, int nshift,
                              double mass, const stag_solver_params *params, stag_solver_stats *stats);
+
+/* Full-lattice solve of (m + D) psi = b (D of Eq. (staggered), Sec. 4.2)
+ * through the even-odd Schur complement: M psi_e = m b_e - D_eo b_o, then
+ * psi_o = (b_o - D_oe psi_e) / m.  psi, b: device canonical full fields
+ * [V][3] complex128 (lexicographic sites, both parities); mass > 0.  The even
+ * solve uses params->inner_prec (STAG_F64: stag_cg_solve, else the mixed
+ * solver) and params->tol on M; the full residual is then at most
+ * tol (1 + 8/m) relative (|D_eo| <= 8 for unitary links).  stats describe
+ * the even solve.  Blocks until done. */
+int stag_solve_full(stag_ctx ctx, double *psi, const double *b, double mass, const stag_solver_params *params,
+                    stag_solver_stats *stats);
+
+/* ----------------------------------------------------------- HMC force */
+
+/* Pseudo-fermion action S = phi^dagger M^{-1} phi = Re <phi, X>: solves
+ * M X = phi (params->inner_prec STAG_F64: stag_cg_solve; STAG_F32/F16:
+ * stag_cg_solve_mixed) into X_even and writes S to *S (host).  phi_even,
+ * X_even: device canonical half fields (must not alias).  Blocks; returns the
+ * solver's status.  (The paper runs CG inside HMC, Sec. 1; the action and its
+ * force are the HMC side of that, not in the paper.) */
+int stag_fermion_action(stag_ctx ctx, const double *phi_even, double mass, const stag_solver_params *params,
+                        double *X_even, double *S, stag_solver_stats *stats);
+
+/* Derivative of S with respect to the links, given X = M^{-1} phi (device
+ * canonical half field).  With Y = D_oe X and eta = eta_mu(x) times the
+ * boundary sign of the hop x -> x+mu, the Euclidean gradient of link U_{x,mu}
+ * is G = 2 eta X_x Y_{x+mu}^dagger (x even) or -2 eta Y_x X_{x+mu}^dagger (x
+ * odd), so that dS = Re sum conj(G_ab) dU_ab (the PyTorch convention
+ * dS/dRe U + i dS/dIm U); the projected force is P = TA(U G^dagger)
+ * = (W - W^dagger)/2 - tr(W - W^dagger)/6 with W = U G^dagger, so that
+ * dS/deps = tr(i T P) under U -> exp(i eps T) U.  Outputs (device, canonical
+ * [V][4][3][3] complex128, each may be NULL but not all): P, G, and
+ * phi_grad = dS/dRe phi + i dS/dIm phi = 2 X ([V/2][3]); all multiplied by
+ * scale.  Double-precision arithmetic, 18-real links.  Asynchronous. */
+int stag_fermion_force(stag_ctx ctx, double *P, double *G, const double *X_even, double *phi_grad, double scale);
 
 /* Right-hand sides per operator pass used by the last batched solve of this
  * context (the autotuner's choice when rhs_block was 0). */

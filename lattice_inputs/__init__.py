@@ -39,6 +39,8 @@ __all__ = [
     "random_gauge_transform",
     "unit_links",
     "workload_seed",
+    "random_links_torch",
+    "gaussian_half_torch",
 ]
 
 
@@ -163,3 +165,54 @@ def random_gauge_transform(dims, seed: int = 7) -> np.ndarray:
     """One Haar SU(3) matrix per site, shape (V, 3, 3)."""
     rng = np.random.default_rng(seed)
     return np.ascontiguousarray(haar_su3(rng, volume(dims)), dtype=np.complex128)
+
+
+# ---------------------------------------------------------------------------
+# Device-side generators for large volumes (same recipes, torch's own seeded
+# stream: values differ from the numpy generators above; tests that compare
+# with the oracle copy these arrays to the host and hand them to both sides).
+
+def random_links_torch(dims, recipe: str = "smooth", eps: float | None = None, seed: int = 0, device="cuda"):
+    """Gauge field (V,4,3,3) complex128 generated on `device` with torch.
+
+    "smooth": exp(i*eps*H) with H = (A + A^dagger)/2 - tr/3, A complex Gaussian,
+    the exponential by torch.linalg.matrix_exp; "haar": QR of a complex Gaussian
+    with the phases of R moved into Q, determinant divided out."""
+    import torch
+    v = volume(dims)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    n = 4 * v
+    out = torch.empty((n, 3, 3), dtype=torch.complex128, device=device)
+    chunk = 1 << 21
+    for s0 in range(0, n, chunk):
+        m = min(chunk, n - s0)
+        re = torch.randn((m, 3, 3), generator=gen, dtype=torch.float64, device=device)
+        im = torch.randn((m, 3, 3), generator=gen, dtype=torch.float64, device=device)
+        a = torch.complex(re, im) / np.sqrt(2.0)
+        if recipe == "smooth":
+            h = 0.5 * (a + a.conj().transpose(1, 2))
+            tr = torch.diagonal(h, dim1=1, dim2=2).sum(-1).real / 3.0
+            h = h - tr[:, None, None] * torch.eye(3, dtype=h.dtype, device=device)
+            out[s0:s0 + m] = torch.linalg.matrix_exp(1j * float(eps) * h)
+        elif recipe == "haar":
+            q, r = torch.linalg.qr(a)
+            d = torch.diagonal(r, dim1=1, dim2=2)
+            q = q * (d / d.abs())[:, None, :]
+            det = torch.linalg.det(q)
+            out[s0:s0 + m] = q / (det ** (1.0 / 3.0))[:, None, None]
+        else:
+            raise ValueError(f"unknown link recipe {recipe!r}")
+    return out.reshape(v, 4, 3, 3)
+
+
+def gaussian_half_torch(dims, seed: int = 1, nvec: int | None = None, device="cuda"):
+    """Gaussian half field(s) generated on `device`: (V/2,3) or (nvec,V/2,3) complex128."""
+    import torch
+    v = volume(dims)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    shape = (v // 2, 3) if nvec is None else (int(nvec), v // 2, 3)
+    re = torch.randn(shape, generator=gen, dtype=torch.float64, device=device)
+    im = torch.randn(shape, generator=gen, dtype=torch.float64, device=device)
+    return torch.complex(re, im) / np.sqrt(2.0)

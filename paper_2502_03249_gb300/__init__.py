@@ -21,11 +21,11 @@ import os
 import threading
 
 __all__ = [
-    "F64", "F32", "F16", "RECON_18", "RECON_12", "StagError", "NotConverged",
-    "load", "build", "Context", "SolverParams", "SolverStats",
+    "F64", "F32", "F16", "F64X", "RECON_18", "RECON_12", "StagError", "NotConverged",
+    "load", "build", "Context", "SolverParams", "SolverStats", "StaggeredAction", "fermion_force",
 ]
 
-F64, F32, F16 = 0, 1, 2
+F64, F32, F16, F64X = 0, 1, 2, 3
 RECON_18, RECON_12 = 18, 12
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 
@@ -55,7 +55,7 @@ class NotConverged(RuntimeError):
 class SolverParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("delta", ctypes.c_double), ("inner_prec", ctypes.c_int),
-                ("inner_recon", ctypes.c_int), ("rhs_block", ctypes.c_int)]
+                ("inner_recon", ctypes.c_int), ("rhs_block", ctypes.c_int), ("f64_arith", ctypes.c_int)]
 
 
 class SolverStats(ctypes.Structure):
@@ -87,10 +87,15 @@ def _declare(lib):
         "stag_solver_params_default": ([ctypes.POINTER(SolverParams)], None),
         "stag_cg_solve": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_cg_solve_mixed": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
+        "stag_cg_solve_shifted": ([P, P, P, D, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_cg_solve_multi": ([P, P, P, I, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_dslash_multi": ([P, P, P, I, I, I, I, I], I),
         "stag_last_rhs_block": ([P], I),
         "stag_cg_solve_multishift": ([P, P, P, P, I, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
+        "stag_fermion_action": ([P, P, D, ctypes.POINTER(SolverParams), P, ctypes.POINTER(D),
+                                 ctypes.POINTER(SolverStats)], I),
+        "stag_fermion_force": ([P, P, P, P, P, D], I),
+        "stag_solve_full": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_strerror": ([I], ctypes.c_char_p),
         "stag_last_error": ([], ctypes.c_char_p),
         "stag_abi_version": ([], I),
@@ -274,10 +279,136 @@ class Context:
             raise NotConverged(rc, out)
         return out
 
+    def solve_full(self, psi, b, mass, raise_on_fail=True, **params):
+        """stag_solve_full: psi = (m + D)^{-1} b on the full lattice; psi, b complex128 (V, 3)."""
+        torch = _torch()
+        for t, name in ((psi, "psi"), (b, "b")):
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda or \
+                    tuple(t.shape) != (self.V, 3) or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor of shape (V, 3)")
+        self._sync_stream()
+        prm = self.solver_params(**params)
+        st = SolverStats()
+        rc = _check(self._lib.stag_solve_full(self._h, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                              float(mass), ctypes.byref(prm), ctypes.byref(st)))
+        if rc != OK and raise_on_fail:
+            raise NotConverged(rc, st.as_dict())
+        return st.as_dict()
+
+    def fermion_action(self, phi, mass, X=None, raise_on_fail=True, **params):
+        """stag_fermion_action: S = phi^dagger M^{-1} phi; X (M^{-1} phi) is written too. Returns (S, X, stats)."""
+        X = self.new_half() if X is None else X
+        self._sync_stream()
+        prm = self.solver_params(**params)
+        st = SolverStats()
+        S = ctypes.c_double(0.0)
+        rc = _check(self._lib.stag_fermion_action(self._h, self._field(phi, "phi"), float(mass), ctypes.byref(prm),
+                                                  self._field(X, "X"), ctypes.byref(S), ctypes.byref(st)))
+        if rc != OK and raise_on_fail:
+            raise NotConverged(rc, st.as_dict())
+        return S.value, X, st.as_dict()
+
+    def fermion_force(self, X, P=None, G=None, phi_grad=None, scale=1.0):
+        """stag_fermion_force: projected force P, Euclidean gradient G and dS/dphi = 2 X, times scale."""
+        torch = _torch()
+
+        def link_out(t, name):
+            if t is None:
+                return None
+            if t.dtype != torch.complex128 or not t.is_cuda or tuple(t.shape) != (self.V, 4, 3, 3) or \
+                    not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor of shape (V, 4, 3, 3)")
+            return ctypes.c_void_p(t.data_ptr())
+
+        self._sync_stream()
+        _check(self._lib.stag_fermion_force(self._h, link_out(P, "P"), link_out(G, "G"), self._field(X, "X"),
+                                            None if phi_grad is None else self._field(phi_grad, "phi_grad"),
+                                            float(scale)))
+        return P, G, phi_grad
+
     def last_rhs_block(self):
         """stag_last_rhs_block: rhs block of the last batched solve."""
         return int(self._lib.stag_last_rhs_block(self._h))
 
+    def cg_solve_shifted(self, x, b, mass, sigma, raise_on_fail=True, **params):
+        """stag_cg_solve_shifted: x = (M + sigma)^{-1} b (double precision CG)."""
+        self._sync_stream()
+        prm = self.solver_params(**params)
+        st = SolverStats()
+        rc = _check(self._lib.stag_cg_solve_shifted(self._h, self._field(x, "x"), self._field(b, "b"), float(mass),
+                                                    float(sigma), ctypes.byref(prm), ctypes.byref(st)))
+        if rc != OK and raise_on_fail:
+            raise NotConverged(rc, st.as_dict())
+        return st.as_dict()
+
     def cg_solve_mixed(self, x, b, mass, raise_on_fail=True, **params):
         """stag_cg_solve_mixed: reliable-update CG, inner precision params inner_prec / inner_recon."""
         return self._solve(self._lib.stag_cg_solve_mixed, x, b, mass, raise_on_fail, params)
+
+
+def _autograd_function():
+    import torch
+
+    class _StaggeredAction(torch.autograd.Function):
+        """S(U, phi) = phi^dagger M[U]^{-1} phi, M = m^2 - D_eo D_oe.
+
+        forward: uploads U, solves X = M^{-1} phi (stag_fermion_action), returns S.
+        backward: solves again for X (the solution is recomputed, not stored:
+        only U and phi are saved), then stag_fermion_force gives the Euclidean
+        gradient with respect to U and 2 X with respect to phi, both scaled by
+        the incoming gradient of S.
+        """
+
+        @staticmethod
+        def forward(fctx, U, phi, lattice, mass, params):
+            lattice.upload_gauge(U.detach())
+            S, _, _ = lattice.fermion_action(phi.detach().contiguous(), mass, **params)
+            fctx.save_for_backward(U, phi)
+            fctx.lattice, fctx.mass, fctx.params = lattice, mass, params
+            return torch.tensor(S, dtype=torch.float64, device=U.device)
+
+        @staticmethod
+        def backward(fctx, gS):
+            U, phi = fctx.saved_tensors
+            lat = fctx.lattice
+            lat.upload_gauge(U.detach())
+            _, X, _ = lat.fermion_action(phi.detach().contiguous(), fctx.mass, **fctx.params)
+            G = torch.empty_like(U) if fctx.needs_input_grad[0] else None
+            gphi = torch.empty_like(phi) if fctx.needs_input_grad[1] else None
+            if G is not None or gphi is not None:
+                lat.fermion_force(X, G=G, phi_grad=gphi, scale=float(gS))
+            return G, gphi, None, None, None
+
+    return _StaggeredAction
+
+
+_SA = None
+
+
+def StaggeredAction(U, phi, lattice, mass, **params):
+    """Differentiable S(U, phi) = phi^dagger M[U]^{-1} phi on the given Context.
+
+    U: complex128 (V,4,3,3) CUDA tensor; phi: complex128 (V/2,3) CUDA tensor on
+    even sites.  Solver keyword arguments (tol, inner_prec, ...) are passed to
+    stag_fermion_action.  The gradient with respect to U is the Euclidean one
+    (dS/dRe U + i dS/dIm U)."""
+    global _SA
+    if _SA is None:
+        _SA = _autograd_function()
+    params = dict(params)
+    params.setdefault("tol", 1e-12)
+    params.setdefault("inner_prec", F64)   # exact for any complex links; F32/F16 inner solves assume SU(3)
+    return _SA.apply(U, phi, lattice, float(mass), params)
+
+
+def fermion_force(U, phi, lattice, mass, **params):
+    """The projected HMC force P = TA(U G^dagger) per link, (V,4,3,3), for S = phi^dagger M^{-1} phi."""
+    import torch
+    lattice.upload_gauge(U)
+    params = dict(params)
+    params.setdefault("tol", 1e-12)
+    params.setdefault("inner_prec", F64)
+    _, X, _ = lattice.fermion_action(phi, mass, **params)
+    P = torch.empty_like(U)
+    lattice.fermion_force(X, P=P)
+    return P

@@ -88,7 +88,7 @@ static int dslash_entry(stag_ctx ctx, double* out, const double* in, int prec, i
         set_error("out and in must not alias");
         return STAG_EINVAL;
     }
-    if (prec < STAG_F64 || prec > STAG_F16 || (recon != 18 && recon != 12)) {
+    if (prec < STAG_F64 || prec > STAG_F64X || (recon != 18 && recon != 12) || (prec == STAG_F64X && recon != 18)) {
         set_error("unsupported prec %d / recon %d", prec, recon);
         return STAG_EUNSUPPORTED;
     }
@@ -96,7 +96,7 @@ static int dslash_entry(stag_ctx ctx, double* out, const double* in, int prec, i
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
-    if (prec == STAG_F64) return launch_dslash(ctx, prec, recon, par_out, out, in, ctx->stream);
+    if (prec == STAG_F64 || prec == STAG_F64X) return launch_dslash(ctx, prec, recon, par_out, out, in, ctx->stream);
     STAG_TRY(ensure_lo_tmp(ctx, lo_spinor_bytes(ctx->g, prec)));
     STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, 1, ctx->stream));
     STAG_TRY(launch_dslash(ctx, prec, recon, par_out, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream));
@@ -189,13 +189,14 @@ int stag_destroy(stag_ctx ctx)
     if (ctx->stream || ctx->cap_stream) cudaStreamSynchronize(ctx->stream);
     free_workspace(ctx);
     free_tune_cache(ctx);
-    for (int s = 0; s < 6; ++s)
+    for (int s = 0; s < 8; ++s)
         if (ctx->links[s]) cudaFree(ctx->links[s]);
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->tmp_odd) cudaFree(ctx->tmp_odd);
     if (ctx->tmp_lo_in) cudaFree(ctx->tmp_lo_in);
     if (ctx->tmp_lo_out) cudaFree(ctx->tmp_lo_out);
+    if (ctx->full_tmp) cudaFree(ctx->full_tmp);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return STAG_OK;

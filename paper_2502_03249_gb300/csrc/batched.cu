@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "batched.cuh"
+#include "df64.cuh"
 #include "cg_kernels.cuh"
 #include "graph.h"
 #include "tune.h"
@@ -552,6 +553,11 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
         return multi_dslash_tuned(ctx, tag, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, stride, nrhs,
                                   par_out, nb, nb_used);
     }
+    if (prec == STAG_F64X) {
+        SpinorF64asDF si{(double2*)in}, so{(double2*)out};
+        return multi_dslash_tuned(ctx, tag, LinkFieldDF<18>{(const float4*)lk, Vh}, si, so, stride, nrhs, par_out, nb,
+                                  nb_used);
+    }
     if (prec == STAG_F32) {
         SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
         if (recon == 18)
@@ -768,7 +774,7 @@ int stag_dslash_multi(stag_ctx ctx, double* out, const double* in, int nrhs, int
         set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
         return STAG_EINVAL;
     }
-    if (prec < STAG_F64 || prec > STAG_F16 || (recon != 18 && recon != 12)) {
+    if (prec < STAG_F64 || prec > STAG_F64X || (recon != 18 && recon != 12) || (prec == STAG_F64X && recon != 18)) {
         set_error("unsupported prec %d / recon %d", prec, recon);
         return STAG_EUNSUPPORTED;
     }
@@ -776,7 +782,7 @@ int stag_dslash_multi(stag_ctx ctx, double* out, const double* in, int nrhs, int
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
-    if (prec == STAG_F64) return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr);
+    if (prec == STAG_F64 || prec == STAG_F64X) return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr);
     const size_t lo = lo_spinor_bytes(ctx->g, prec) * nrhs;
     STAG_TRY(ensure_lo_tmp_public(ctx, lo));
     STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, nrhs, ctx->stream));

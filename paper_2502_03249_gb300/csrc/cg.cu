@@ -6,6 +6,7 @@
 #include <new>
 
 #include "cg_kernels.cuh"
+#include "df64.cuh"
 #include "workspace.h"
 
 namespace stag {
@@ -28,7 +29,7 @@ int apply_M_f64(stag_ctx ctx, double2* out, const double2* in, double mass, doub
     const int grid = nblk(ctx->g.Vh, HOP_BS);
     k_hop<LF64, SpinorF64, HOP_BS><<<grid, HOP_BS, 0, s>>>(ctx->g, 1, U, SpinorF64{(double2*)in}, SpinorF64{tmp_odd},
                                                            nullptr, 0);
-    k_xpay_hop<LF64, SpinorF64, HOP_BS><<<grid, HOP_BS, 0, s>>>(ctx->g, U, SpinorF64{tmp_odd}, SpinorF64{(double2*)in},
+    k_xpay_hop<LF64, SpinorF64, SpinorF64, HOP_BS><<<grid, HOP_BS, 0, s>>>(ctx->g, U, SpinorF64{tmp_odd}, SpinorF64{(double2*)in},
                                                                  SpinorF64{out}, mass * mass);
     STAG_CUDA_TRY(cudaGetLastError());
     return STAG_OK;
@@ -108,61 +109,100 @@ int ensure_cg_f64(stag_ctx ctx)
     return STAG_OK;
 }
 
-// Enqueue one CG iteration (four kernels) on stream s.
-static int enqueue_cg_iter_f64(stag_ctx ctx, const LF64& U, cudaStream_t s, cudaGraphConditionalHandle cond,
-                               int use_cond)
-{
-    Workspace* ws = ctx->ws;
-    const Geom g = ctx->g;
-    const int gh = nblk(g.Vh, HOP_BS), gb = nblk(g.Vh, BLAS_BS);
-    SpinorF64 t{ws->t}, p{ws->p}, Ap{ws->Ap}, x{ws->x}, r{ws->r};
-    k_hop_guarded<LF64, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, p, t, ws->sc);
-    k_Mp_dot<LF64, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, t, p, Ap, ws->sc, ctx->partials, ctx->counters);
-    k_cg_update<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, x, r, p, Ap, ws->sc, ctx->partials, ctx->counters,
-                                                          cond, use_cond);
-    k_cg_p<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, r, p, ws->sc);
-    STAG_CUDA_TRY(cudaGetLastError());
-    return STAG_OK;
-}
+// One double-precision CG plan per operator arithmetic: LF / SD are the link
+// field and the spinor view the operator passes use (IEEE double: LinkField +
+// SpinorF64; double-float: LinkFieldDF + SpinorF64asDF over the same double
+// vectors).  The BLAS kernels always work on the double vectors.
+template <class LF, class SD>
+struct F64Plan {
+    // one CG iteration (four kernels) on stream s
+    static int enqueue_iter(stag_ctx ctx, const LF& U, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
+    {
+        Workspace* ws = ctx->ws;
+        const Geom g = ctx->g;
+        const int gh = nblk(g.Vh, HOP_BS), gb = nblk(g.Vh, BLAS_BS);
+        SpinorF64 p{ws->p}, Ap{ws->Ap}, x{ws->x}, r{ws->r};
+        k_hop_guarded<LF, SD, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, SD{ws->p}, SD{ws->t}, ws->sc);
+        k_Mp_dot<LF, SD, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, SD{ws->t}, p, Ap, ws->sc, ctx->partials,
+                                                                  ctx->counters);
+        k_cg_update<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, x, r, p, Ap, ws->sc, ctx->partials,
+                                                              ctx->counters, cond, use_cond);
+        k_cg_p<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, r, p, ws->sc);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
 
-// Build (once per context) the graph: while (cond) { one CG iteration }.
-static int ensure_cg_graph_f64(stag_ctx ctx, const LF64& U)
-{
-    Workspace* ws = ctx->ws;
-    if (ws->f64_exec) return STAG_OK;
-    cudaGraph_t graph = nullptr;
-    STAG_CUDA_TRY(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle cond;
-    STAG_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    STAG_CUDA_TRY(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    STAG_CUDA_TRY(cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_cg_iter_f64(ctx, U, ctx->cap_stream, cond, 1);
-    cudaGraph_t captured = nullptr;
-    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &captured);
-    if (rc != STAG_OK || e != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        set_error("capturing the CG body failed: %s", cudaGetErrorString(e));
-        return rc != STAG_OK ? rc : STAG_ECUDA;
+    // the graph  while (cond) { one CG iteration }, built once per context
+    static int ensure_graph(stag_ctx ctx, const LF& U, int slot)
+    {
+        Workspace* ws = ctx->ws;
+        if (ws->f64_exec[slot]) return STAG_OK;
+        cudaGraph_t graph = nullptr;
+        STAG_CUDA_TRY(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle cond;
+        STAG_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        STAG_CUDA_TRY(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        STAG_CUDA_TRY(cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+                                                    cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_iter(ctx, U, ctx->cap_stream, cond, 1);
+        cudaGraph_t captured = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &captured);
+        if (rc != STAG_OK || e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            set_error("capturing the CG body failed: %s", cudaGetErrorString(e));
+            return rc != STAG_OK ? rc : STAG_ECUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            set_error("instantiating the CG graph failed: %s", cudaGetErrorString(e));
+            return STAG_ECUDA;
+        }
+        ws->f64_graph[slot] = graph;
+        ws->f64_exec[slot] = exec;
+        return STAG_OK;
     }
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        set_error("instantiating the CG graph failed: %s", cudaGetErrorString(e));
-        return STAG_ECUDA;
+
+    // run the iteration until the device says done: one graph launch, or a
+    // host loop that reads the done flag every check_every iterations
+    static int run_loop(stag_ctx ctx, const LF& U, const stag_solver_params& prm, int slot)
+    {
+        Workspace* ws = ctx->ws;
+        if (prm.use_graph) {
+            STAG_TRY(ensure_graph(ctx, U, slot));
+            STAG_CUDA_TRY(cudaGraphLaunch(ws->f64_exec[slot], ctx->stream));
+            return STAG_OK;
+        }
+        const int every = prm.check_every > 0 ? prm.check_every : 25;
+        for (;;) {
+            for (int k = 0; k < every; ++k) STAG_TRY(enqueue_iter(ctx, U, ctx->stream, 0, 0));
+            STAG_CUDA_TRY(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
+            STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            if (ws->sc_host->done) return STAG_OK;
+        }
     }
-    ws->f64_graph = graph;
-    ws->f64_exec = exec;
-    return STAG_OK;
-}
+
+    // r = b - M x in double precision (operator passes in this plan's arithmetic)
+    static int true_residual(stag_ctx ctx, const LF& U)
+    {
+        Workspace* ws = ctx->ws;
+        const Geom g = ctx->g;
+        k_hop<LF, SD, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(g, 1, U, SD{ws->x}, SD{ws->t}, nullptr,
+                                                                             0);
+        k_true_resid_f64<LF, SD, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(
+            g, U, ws->t, ws->x, ws->b, ws->r, ws->sc, ctx->partials, ctx->counters, 0);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+};
 
 int free_graph_pair(cudaGraph_t& g, cudaGraphExec_t& e)
 {
@@ -173,34 +213,13 @@ int free_graph_pair(cudaGraph_t& g, cudaGraphExec_t& e)
     return STAG_OK;
 }
 
-// Run the iteration until the device says done: graph launch, or a host loop
-// that reads the done flag every check_every iterations.
-static int run_loop_f64(stag_ctx ctx, const LF64& U, const stag_solver_params& prm)
+template <class LF, class SD>
+static int cg_solve_plan(stag_ctx ctx, const LF& U, int slot, double2* x_out, const double2* b_in, double mass,
+                         double sigma, const stag_solver_params& prm, stag_solver_stats* st,
+                         std::chrono::steady_clock::time_point t0)
 {
+    typedef F64Plan<LF, SD> Plan;
     Workspace* ws = ctx->ws;
-    if (prm.use_graph) {
-        STAG_TRY(ensure_cg_graph_f64(ctx, U));
-        STAG_CUDA_TRY(cudaGraphLaunch(ws->f64_exec, ctx->stream));
-        return STAG_OK;
-    }
-    const int every = prm.check_every > 0 ? prm.check_every : 25;
-    for (;;) {
-        for (int k = 0; k < every; ++k) STAG_TRY(enqueue_cg_iter_f64(ctx, U, ctx->stream, 0, 0));
-        STAG_CUDA_TRY(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
-        STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-        if (ws->sc_host->done) return STAG_OK;
-    }
-}
-
-int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass, double sigma,
-                 const stag_solver_params& prm, stag_solver_stats* st)
-{
-    const auto t0 = std::chrono::steady_clock::now();
-    STAG_TRY(ensure_cg_f64(ctx));
-    Workspace* ws = ctx->ws;
-    const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
-    const LF64 U{(const double2*)lk, ctx->g.Vh};
     const Geom g = ctx->g;
     const size_t bytes = (size_t)3 * g.Vh * sizeof(double2);
     const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
@@ -212,13 +231,8 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
     CgScalars* hs = ws->sc_host;
     double prev_true = INFINITY;
     for (;;) {
-        STAG_TRY(run_loop_f64(ctx, U, prm));
-        // true residual r = b - M x, recomputed in double
-        k_hop<LF64, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(g, 1, U, SpinorF64{ws->x},
-                                                                                      SpinorF64{ws->t}, nullptr, 0);
-        k_true_resid_f64<LF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(
-            g, U, ws->t, ws->x, ws->b, ws->r, ws->sc, ctx->partials, ctx->counters, 0);
-        STAG_CUDA_TRY(cudaGetLastError());
+        STAG_TRY(Plan::run_loop(ctx, U, prm, slot));
+        STAG_TRY(Plan::true_residual(ctx, U));
         STAG_CUDA_TRY(cudaMemcpyAsync(hs, ws->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
         STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         if (hs->rr0 == 0.0 || hs->rr_true <= hs->tol2 || hs->status == STAG_BREAKDOWN || hs->iter >= hs->maxiter)
@@ -248,11 +262,32 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
     return status;
 }
 
+int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass, double sigma,
+                 const stag_solver_params& prm, stag_solver_stats* st)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    STAG_TRY(ensure_cg_f64(ctx));
+    if (prm.f64_arith == STAG_F64X) {
+        const void* lk = nullptr;
+        STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lk));
+        const LinkFieldDF<18> U{(const float4*)lk, ctx->g.Vh};
+        return cg_solve_plan<LinkFieldDF<18>, SpinorF64asDF>(ctx, U, 1, x_out, b_in, mass, sigma, prm, st, t0);
+    }
+    if (prm.f64_arith != STAG_F64) {
+        set_error("f64_arith must be STAG_F64 or STAG_F64X");
+        return STAG_EINVAL;
+    }
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
+    const LF64 U{(const double2*)lk, ctx->g.Vh};
+    return cg_solve_plan<LF64, SpinorF64>(ctx, U, 0, x_out, b_in, mass, sigma, prm, st, t0);
+}
+
 void free_workspace(stag_ctx ctx)
 {
     Workspace* ws = ctx->ws;
     if (!ws) return;
-    free_graph_pair(ws->f64_graph, ws->f64_exec);
+    for (int i = 0; i < 2; ++i) free_graph_pair(ws->f64_graph[i], ws->f64_exec[i]);
     free_mixed(ws);
     free_batches(ws);
     for (auto& m : ws->ms) m.release();
@@ -285,6 +320,7 @@ void stag_solver_params_default(stag_solver_params* p)
     p->inner_prec = STAG_F32;
     p->inner_recon = STAG_RECON_12;
     p->rhs_block = 0;
+    p->f64_arith = STAG_F64X;
 }
 
 int stag_cg_solve(stag_ctx ctx, double* x_even, const double* b_even, double mass, const stag_solver_params* params,
@@ -305,6 +341,26 @@ int stag_cg_solve(stag_ctx ctx, double* x_even, const double* b_even, double mas
         return STAG_ENOGAUGE;
     }
     return cg_solve_f64(ctx, (double2*)x_even, (const double2*)b_even, mass, 0.0, prm, stats);
+}
+
+int stag_cg_solve_shifted(stag_ctx ctx, double* x_even, const double* b_even, double mass, double sigma,
+                          const stag_solver_params* params, stag_solver_stats* stats)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(x_even, "x_even"));
+    STAG_TRY(check_half_field(b_even, "b_even"));
+    stag_solver_params prm;
+    stag_solver_params_default(&prm);
+    if (params) prm = *params;
+    if (!(prm.tol > 0.0) || !(sigma >= 0.0) || !isfinite(sigma)) {
+        set_error("tol must be positive and sigma finite and >= 0");
+        return STAG_EINVAL;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    return cg_solve_f64(ctx, (double2*)x_even, (const double2*)b_even, mass, sigma, prm, stats);
 }
 
 }  // extern "C"

@@ -33,7 +33,7 @@ __device__ __forceinline__ double site_dot(const Vec3<T>& a, const Vec3<T>& b)
 }
 
 template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
+__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
 {
     if (sc->done) return;
     const int h = blockIdx.x * BS + threadIdx.x;
@@ -41,8 +41,10 @@ __global__ void __launch_bounds__(BS) k_hop_guarded(Geom g, int p, LF U, S in, S
     out.store(h, dslash_site(g, p, h, U, in));
 }
 
-template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS) k_Mp_dot(Geom g, LF U, S t, S p, S Ap, CgScalars* sc,
+// SD is the storage view the operator reads t through (S itself, or a
+// double-float view of double storage); the epilogue runs in S's arithmetic.
+template <class LF, class SD, class S, int BS>
+__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_Mp_dot(Geom g, LF U, SD t, S p, S Ap, CgScalars* sc,
                                                double* part, unsigned* cnt)
 {
     __shared__ double red[BS / 32];
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(BS) k_Mp_dot(Geom g, LF U, S t, S p, S Ap, CgS
     const int h = blockIdx.x * BS + threadIdx.x;
     double d = 0.0;
     if (h < g.Vh) {
-        const Vec3<real> Dt = dslash_site(g, 0, h, U, t);
+        const Vec3<real> Dt = vconv<real>(dslash_site(g, 0, h, U, t));
         const Vec3<real> pv = p.load(h);
         Vec3<real> a;
 #pragma unroll
@@ -145,14 +147,14 @@ __global__ void __launch_bounds__(BS) k_cg_p(int Vh, S r, S p, const CgScalars* 
     p.store(h, pv);
 }
 
-template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS) k_xpay_hop(Geom g, LF U, S t, S x, S out, double a)
+template <class LF, class SD, class S, int BS>
+__global__ void __launch_bounds__(BS) k_xpay_hop(Geom g, LF U, SD t, S x, S out, double a)
 {
     // out = a x - D_eo t  on even sites
     typedef typename S::real real;
     const int h = blockIdx.x * BS + threadIdx.x;
     if (h >= g.Vh) return;
-    const Vec3<real> Dt = dslash_site(g, 0, h, U, t);
+    const Vec3<real> Dt = vconv<real>(dslash_site(g, 0, h, U, t));
     const Vec3<real> xv = x.load(h);
     Vec3<real> o;
 #pragma unroll
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(BS) k_xpay_hop(Geom g, LF U, S t, S x, S out, 
 
 // out = D_{p,1-p} in; with guard set, only when a reliable update is due.
 template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS) k_hop(Geom g, int p, LF U, S in, S out, const CgScalars* sc, int guard)
+__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_hop(Geom g, int p, LF U, S in, S out, const CgScalars* sc, int guard)
 {
     if (guard && !sc->reliable) return;
     const int h = blockIdx.x * BS + threadIdx.x;
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(BS) k_hop(Geom g, int p, LF U, S in, S out, co
 
 // r = b - (m^2 + sigma) x + D_eo t  (t = D_oe x), rr_true = |r|^2, double precision.
 // With guard set, only when a reliable update is due.
-template <class LF, int BS>
+template <class LF, class SD, int BS>
 __global__ void __launch_bounds__(BS) k_true_resid_f64(Geom g, LF U, const double2* t, const double2* x,
                                                        const double2* b, double2* r, CgScalars* sc, double* part,
                                                        unsigned* cnt, int guard)
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(BS) k_true_resid_f64(Geom g, LF U, const doubl
     double d = 0.0;
     const double m2s = sc->m2 + sc->sigma;
     if (h < g.Vh) {
-        const Vec3<double> Dt = dslash_site(g, 0, h, U, SpinorF64{(double2*)t});
+        const Vec3<double> Dt = vconv<double>(dslash_site(g, 0, h, U, SD{(double2*)t}));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double2 xv = x[(size_t)h * 3 + c], bv = b[(size_t)h * 3 + c];

@@ -353,14 +353,16 @@ __device__ __forceinline__ double block_sum(double v, double* smem)
 
 // Each block stores its partial sum; the last block to arrive (counted with an
 // atomic after a fence) sees every partial.  Nobody waits, so the pattern is
-// safe for any grid size.  Returns true in all threads of the last block.
+// safe for any grid size and shape (all blocks of a 1-, 2- or 3-D grid are
+// counted).  Returns true in all threads of the last block.
 __device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* smem_flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
+        const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
         unsigned int prev = atomicAdd(counter, 1u);
-        *smem_flag = (prev == gridDim.x - 1);
+        *smem_flag = (prev == nblocks - 1);
     }
     __syncthreads();
     return *smem_flag;

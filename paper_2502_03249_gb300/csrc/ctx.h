@@ -31,7 +31,7 @@ void set_error(const char* fmt, ...);
     } while (0)
 
 // Index of a (precision, compression) link copy.
-inline int link_slot(int prec, int recon) { return prec * 2 + (recon == 12 ? 1 : 0); }
+inline int link_slot(int prec, int recon) { return prec * 2 + (recon == 12 ? 1 : 0); }   // 0..7
 
 // Scalars of one CG-type iteration, resident in device memory so the loop
 // runs without host round trips.  One record per right-hand side.
@@ -69,8 +69,9 @@ struct stag_ctx_s {
     cudaStream_t stream;
     cudaStream_t cap_stream;   // private stream used only to capture graphs
     bool have_gauge;
-    void* links[6];            // link copies, index link_slot(prec, recon)
-    size_t link_bytes[6];
+    void* links[8];            // link copies, index link_slot(prec, recon)
+    size_t link_bytes[8];
+    bool link_stale[8];        // derived copy older than the last upload (re-derived in place)
     // reduction scratch: partial sums (one double per block) and arrival counters
     double* partials;
     unsigned int* counters;    // 64 counters, each used by one reduction site
@@ -81,6 +82,7 @@ struct stag_ctx_s {
     void* tmp_lo_out;
     size_t tmp_lo_bytes;
     stag::Workspace* ws;
+    void* full_tmp;            // four half fields for the full-lattice solve
     void* tune;                // autotuner cache (tune.cu)
     int last_rhs_block;        // right-hand sides per pass chosen by the last batched solve
 };

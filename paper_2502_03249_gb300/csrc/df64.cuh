@@ -1,0 +1,183 @@
+// df64.cuh -- double-float ("f32x2") arithmetic for the double-precision
+// operator on GB300.
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate (about 1.2 TFLOP/s), which makes a
+// double-precision Dslash ALU-bound at ~40 % of its HBM roofline.  Here each
+// double is carried as an unevaluated sum hi + lo of two floats (48-bit
+// significand) and the hop sums run on the FP32 pipe:
+//
+//  * product of two double-floats x*y: hi part p = RN(xh*yh) and its exact
+//    error RN(xh*yh - p) by one FMA, plus the cross terms xh*yl + xl*yh
+//    (the xl*yl term is below 2^-48 relative and dropped);
+//  * accumulation: the hi parts are summed with Knuth's error-free TwoSum, the
+//    rounding errors and low parts are collected in a float companion, so a
+//    whole hop sum keeps ~2^-44 relative to the sum of magnitudes.
+//
+// Every operation uses the _rn intrinsics so the compiler cannot contract or
+// reassociate the error-free transformations.  Inputs are doubles: the links
+// are split once at upload (hi = RN(x), lo = RN(x - hi) in double), the
+// spinors are split on load with integer operations only (no FP64 instruction
+// in the hot loop); results are formed as double(hi) + double(lo).  The
+// integer split keeps the full 48 bits for |x| >= 2^-74 (smaller magnitudes
+// keep 24 bits; zero and subnormal doubles become zero).
+#pragma once
+
+#include "dslash.cuh"
+
+namespace stag {
+
+struct DF {
+    float hi, lo;
+    __device__ __forceinline__ DF() {}
+    __device__ __forceinline__ DF(int v) : hi((float)v), lo(0.f) {}
+    __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ DF flip(DF v, uint32_t sbit)
+{
+    return DF(__uint_as_float(__float_as_uint(v.hi) ^ sbit), __uint_as_float(__float_as_uint(v.lo) ^ sbit));
+}
+
+// acc += s * x * y, s = +1 or -1 given as a sign bit applied to x.
+__device__ __forceinline__ void df_mac(DF& acc, const DF& x, const DF& y)
+{
+    const float ph = __fmul_rn(x.hi, y.hi);
+    float pl = __fmaf_rn(x.hi, y.hi, -ph);
+    pl = __fmaf_rn(x.hi, y.lo, pl);
+    pl = __fmaf_rn(x.lo, y.hi, pl);
+    // TwoSum(acc.hi, ph)
+    const float s = __fadd_rn(acc.hi, ph);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pl));
+}
+
+__device__ __forceinline__ DF df_neg(const DF& x) { return DF(-x.hi, -x.lo); }
+
+// acc += U v
+template <>
+__device__ __forceinline__ void mv_acc<DF>(Vec3<DF>& acc, const Mat3<DF>& U, const Vec3<DF>& v)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const Cplx<DF> u = U.m[a * 3 + b];
+            df_mac(acc.c[a].re, u.re, v.c[b].re);
+            df_mac(acc.c[a].re, df_neg(u.im), v.c[b].im);
+            df_mac(acc.c[a].im, u.re, v.c[b].im);
+            df_mac(acc.c[a].im, u.im, v.c[b].re);
+        }
+    }
+}
+
+// acc += U^dagger v
+template <>
+__device__ __forceinline__ void mdv_acc<DF>(Vec3<DF>& acc, const Mat3<DF>& U, const Vec3<DF>& v)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const Cplx<DF> u = U.m[b * 3 + a];
+            df_mac(acc.c[a].re, u.re, v.c[b].re);
+            df_mac(acc.c[a].re, u.im, v.c[b].im);
+            df_mac(acc.c[a].im, u.re, v.c[b].im);
+            df_mac(acc.c[a].im, df_neg(u.im), v.c[b].re);
+        }
+    }
+}
+
+// Split a double into hi + lo floats with integer operations only:
+// hi = x truncated to 24 significant bits, lo = the remaining 29 bits rounded
+// to 24 bits (exact for |x| in the float range with |x| >= 2^-74).
+__device__ __forceinline__ DF split_double(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+    const unsigned sign = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7FFu);
+    const int ef = e - 896;   // float biased exponent of x (1023 - 127 = 896)
+    if (ef < 1 || ef > 254) {
+        // zero, subnormal, or outside the float range: no split
+        return DF(__double2float_rn(x), 0.f);
+    }
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+    const unsigned m29 = l32 & 0x1FFFFFFFu;   // value m29 * 2^(e - 1075)
+    const int es = e - 948;                   // float biased exponent of 2^(e - 1075)
+    float lo = 0.f;
+    if (es >= 1) lo = __fmul_rn(__uint2float_rn(m29), __uint_as_float((unsigned)es << 23));
+    return DF(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+
+__device__ __forceinline__ double df_to_double(const DF& v) { return (double)v.hi + (double)v.lo; }
+
+// Canonical double spinor ([h][3] complex128) read and written as double-floats.
+struct SpinorF64asDF {
+    typedef DF real;
+    static constexpr bool has_norm = false;
+    double2* p;
+    __host__ __device__ __forceinline__ SpinorF64asDF at(int k, size_t stride) const
+    {
+        return SpinorF64asDF{(double2*)((char*)p + (size_t)k * stride)};
+    }
+    __device__ __forceinline__ Vec3<DF> load(int h) const
+    {
+        Vec3<DF> v;
+        const double2* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 d = __ldg(q + c);
+            v.c[c].re = split_double(d.x);
+            v.c[c].im = split_double(d.y);
+        }
+        return v;
+    }
+    __device__ __forceinline__ void store(int h, const Vec3<DF>& v) const
+    {
+        double2* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] = make_double2(df_to_double(v.c[c].re), df_to_double(v.c[c].im));
+    }
+};
+
+// Links split at upload: per complex element a float4 (re_hi, re_lo, im_hi,
+// im_lo), same structure-of-arrays layout and byte count as the double copy.
+template <int RECON>
+struct LinkFieldDF {
+    typedef DF real;
+    typedef float4 store;
+    static_assert(RECON == 18, "double-float links are stored with 18 reals");
+    const float4* base;
+    int Vh;
+    __device__ __forceinline__ Mat3<DF> load(int par, int mu, int h) const
+    {
+        Mat3<DF> U;
+        const float4* q = base + ((size_t)(par * 4 + mu) * 9) * Vh + h;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float4 f = __ldg(q + (size_t)k * Vh);
+            U.m[k].re = DF(f.x, f.y);
+            U.m[k].im = DF(f.z, f.w);
+        }
+        return U;
+    }
+};
+
+template <int R> struct OpMinBlocks<LinkFieldDF<R>> { static constexpr int value = 5; };
+
+// Double-float operator results enter double-precision epilogues as double.
+template <> struct VConv<double, DF> {
+    static __device__ __forceinline__ Vec3<double> f(const Vec3<DF>& v)
+    {
+        Vec3<double> o;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.c[c].re = df_to_double(v.c[c].re);
+            o.c[c].im = df_to_double(v.c[c].im);
+        }
+        return o;
+    }
+};
+}  // namespace stag

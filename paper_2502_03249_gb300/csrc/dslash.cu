@@ -1,12 +1,13 @@
 // dslash.cu -- the half-lattice staggered operator D_eo / D_oe (Sec. 4.2,
 // Eq. (staggered)) for every supported storage, one output site per thread.
 #include "ctx.h"
+#include "df64.cuh"
 #include "dslash.cuh"
 
 namespace stag {
 
 template <class LF, class SIn, class SOut, int BS>
-__global__ void __launch_bounds__(BS) k_dslash(Geom g, int p, LF U, SIn in, SOut out)
+__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_dslash(Geom g, int p, LF U, SIn in, SOut out)
 {
     const int h = blockIdx.x * BS + threadIdx.x;
     if (h >= g.Vh) return;
@@ -34,6 +35,10 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
         SpinorF64 si{(double2*)in}, so{(double2*)out};
         if (recon == 18) return run_dslash(ctx, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, par_out, s);
         return run_dslash(ctx, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, par_out, s);
+    }
+    if (prec == STAG_F64X) {
+        SpinorF64asDF si{(double2*)in}, so{(double2*)out};
+        return run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, Vh}, si, so, par_out, s);
     }
     if (prec == STAG_F32) {
         SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};

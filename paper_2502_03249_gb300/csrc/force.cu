@@ -1,0 +1,244 @@
+// force.cu -- the pseudo-fermion action S = phi^dagger M^{-1} phi and its
+// derivative with respect to the links (the HMC fermion force; the paper names
+// HMC as the setting of the inversion, Sec. 1, and gauge-field derivatives as a
+// backend capability, Sec. 3; the force itself is not in the paper).
+//
+// With X = M^{-1} phi (even sites) and Y = D_oe X (odd sites), varying a link
+// changes S by dS = X^dagger dD_eo Y - Y^dagger dD_oe X (D_eo^dagger = -D_oe).
+// For the link U_{x,mu}, eta = eta_mu(x) times the boundary sign of the hop:
+//   x even: G = 2 eta X_x Y_{x+mu}^dagger,   x odd: G = -2 eta Y_x X_{x+mu}^dagger,
+// G the Euclidean gradient (dS = Re sum conj(G_ab) dU_ab, the PyTorch
+// convention dS/dRe U + i dS/dIm U).  Under U -> exp(i eps T) U,
+// dS/deps = tr(i T P) with P = TA(U G^dagger) = (W - W^dagger)/2 - tr(W - W^dagger)/6.
+// G = s u v^dagger is an outer product, so W = U G^dagger = s (U v) u^dagger
+// costs one matrix-vector product per link.
+#include <chrono>
+#include <new>
+
+#include "cg_kernels.cuh"
+#include "workspace.h"
+
+namespace stag {
+
+constexpr int F_BS = 128;
+
+// One thread per (site, mu), in the canonical order i*4 + mu, so each thread
+// writes its link's 144 contiguous bytes of P and G.
+template <class LF>
+__global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, const double2* Y, double2* P,
+                                                double2* G, double scale)
+{
+    const long long idx = (long long)blockIdx.x * F_BS + threadIdx.x;
+    if (idx >= 8LL * g.Vh) return;
+    const long long i = idx >> 2;
+    const int mu = (int)(idx & 3);
+    // parity of lexicographic site i
+    const int x = (int)(i % g.L[0]);
+    long long r = i / g.L[0];
+    const int y = (int)(r % g.L[1]);
+    r /= g.L[1];
+    const int z = (int)(r % g.L[2]);
+    const int t = (int)(r / g.L[2]);
+    const int par = (x + y + z + t) & 1;
+    const int h = (int)(i >> 1);
+    SiteNbrs s;
+    site_nbrs(g, par, h, s);
+    const int hf = s.fwd[mu];
+    // eta_mu(x) times the forward boundary sign, as a double
+    const double eta = (s.sf[mu] ? -1.0 : 1.0);
+    // u, v and s of G = s u v^dagger
+    const double2* up = par == 0 ? X + (size_t)h * 3 : Y + (size_t)h * 3;
+    const double2* vp = par == 0 ? Y + (size_t)hf * 3 : X + (size_t)hf * 3;
+    const double sg = (par == 0 ? 2.0 : -2.0) * eta * scale;
+    Cplx<double> u[3], v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double2 q = __ldg(up + a), w = __ldg(vp + a);
+        u[a] = {q.x, q.y};
+        v[a] = {w.x, w.y};
+    }
+    double2* Gp = G ? G + (size_t)idx * 9 : nullptr;
+    if (Gp) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                // s u_a conj(v_b)
+                const double re = u[a].re * v[b].re + u[a].im * v[b].im;
+                const double im = u[a].im * v[b].re - u[a].re * v[b].im;
+                Gp[a * 3 + b] = make_double2(sg * re, sg * im);
+            }
+    }
+    if (P) {
+        const Mat3<double> Um = U.load(par, mu, h);
+        Cplx<double> w[3];   // U v
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double re = 0.0, im = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                re = fma(Um.m[a * 3 + c].re, v[c].re, re);
+                re = fma(-Um.m[a * 3 + c].im, v[c].im, re);
+                im = fma(Um.m[a * 3 + c].re, v[c].im, im);
+                im = fma(Um.m[a * 3 + c].im, v[c].re, im);
+            }
+            w[a] = {re, im};
+        }
+        // W_ab = s w_a conj(u_b)
+        Cplx<double> W[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                W[a * 3 + b].re = sg * (w[a].re * u[b].re + w[a].im * u[b].im);
+                W[a * 3 + b].im = sg * (w[a].im * u[b].re - w[a].re * u[b].im);
+            }
+        // P = (W - W^dagger)/2 - tr(W - W^dagger)/6;  tr(W - W^dagger) = 2i Im tr W
+        const double trim = (W[0].im + W[4].im + W[8].im) / 3.0;
+        double2* Pp = P + (size_t)idx * 9;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                double re = 0.5 * (W[a * 3 + b].re - W[b * 3 + a].re);
+                double im = 0.5 * (W[a * 3 + b].im + W[b * 3 + a].im);
+                if (a == b) im -= trim;
+                Pp[a * 3 + b] = make_double2(re, im);
+            }
+    }
+}
+
+// out = c X (the gradient 2 dS X of S with respect to phi), canonical half field.
+__global__ void k_scale_copy(long long n, const double2* X, double2* out, double c)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        const double2 v = X[k];
+        out[k] = make_double2(c * v.x, c * v.y);
+    }
+}
+
+// Re <a, b> over a half field, deterministic two-stage sum into *out (device).
+template <int BS>
+__global__ void __launch_bounds__(BS) k_dot_re(int Vh, const double2* a, const double2* b, double* out, double* part,
+                                               unsigned* cnt)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    double d = 0.0;
+    if (h < Vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 x = a[(size_t)h * 3 + c], y = b[(size_t)h * 3 + c];
+            d = fma(x.x, y.x, d);
+            d = fma(x.y, y.y, d);
+        }
+    }
+    const double s = block_sum<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (!arrive_last(cnt, &last)) return;
+    const double tot = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        *out = tot;
+    }
+}
+
+int ensure_cg_f64(stag_ctx ctx);
+int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass, double sigma,
+                 const stag_solver_params& prm, stag_solver_stats* st);
+int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mass, const stag_solver_params& prm,
+                   stag_solver_stats* st);
+int check_ctx(stag_ctx ctx);
+int check_half_field(const void* p, const char* what);
+
+int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2* phi_grad, double scale)
+{
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
+    const Geom g = ctx->g;
+    const LinkField<double2, 18> U{(const double2*)lk, g.Vh};
+    // Y = D_oe X into the context's odd temporary
+    STAG_TRY(launch_dslash(ctx, STAG_F64, 18, 1, ctx->tmp_odd, X, ctx->stream));
+    const long long n = 8LL * g.Vh;
+    k_force<LinkField<double2, 18>><<<(unsigned)((n + F_BS - 1) / F_BS), F_BS, 0, ctx->stream>>>(
+        g, U, X, ctx->tmp_odd, P, G, scale);
+    if (phi_grad) {
+        const long long m = 3LL * g.Vh;
+        k_scale_copy<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(m, X, phi_grad, 2.0 * scale);
+    }
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+}  // namespace stag
+
+using namespace stag;
+
+extern "C" {
+
+int stag_fermion_force(stag_ctx ctx, double* P, double* G, const double* X_even, double* phi_grad, double scale)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(X_even, "X_even"));
+    if (!P && !G && !phi_grad) {
+        set_error("at least one of P, G, phi_grad must be given");
+        return STAG_EINVAL;
+    }
+    if (P) STAG_TRY(check_half_field(P, "P"));
+    if (G) STAG_TRY(check_half_field(G, "G"));
+    if (phi_grad) STAG_TRY(check_half_field(phi_grad, "phi_grad"));
+    if ((P && (const double*)P == X_even) || (G && (const double*)G == X_even) ||
+        (phi_grad && (const double*)phi_grad == X_even)) {
+        set_error("outputs must not alias X_even");
+        return STAG_EINVAL;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    return force_from_X(ctx, (double2*)P, (double2*)G, (const double2*)X_even, (double2*)phi_grad, scale);
+}
+
+int stag_fermion_action(stag_ctx ctx, const double* phi_even, double mass, const stag_solver_params* params,
+                        double* X_even, double* S, stag_solver_stats* stats)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(phi_even, "phi_even"));
+    STAG_TRY(check_half_field(X_even, "X_even"));
+    if (!S) {
+        set_error("S is NULL");
+        return STAG_EINVAL;
+    }
+    if ((const double*)X_even == phi_even) {
+        set_error("X_even must not alias phi_even");
+        return STAG_EINVAL;
+    }
+    stag_solver_params prm;
+    stag_solver_params_default(&prm);
+    if (params) prm = *params;
+    if (!(prm.tol > 0.0)) {
+        set_error("tol must be positive");
+        return STAG_EINVAL;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    int rc = prm.inner_prec == STAG_F64
+                 ? cg_solve_f64(ctx, (double2*)X_even, (const double2*)phi_even, mass, 0.0, prm, stats)
+                 : cg_solve_mixed(ctx, (double2*)X_even, (const double2*)phi_even, mass, prm, stats);
+    if (rc < 0) return rc;
+    STAG_TRY(ensure_cg_f64(ctx));
+    const int Vh = ctx->g.Vh;
+    double* dS = (double*)(ctx->ws->sc + 63);   // a spare device record
+    k_dot_re<256><<<(Vh + 255) / 256, 256, 0, ctx->stream>>>(Vh, (const double2*)phi_even, (const double2*)X_even,
+                                                             dS, ctx->partials, ctx->counters);
+    STAG_CUDA_TRY(cudaGetLastError());
+    STAG_CUDA_TRY(cudaMemcpyAsync(S, dS, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return rc;
+}
+
+}  // extern "C"

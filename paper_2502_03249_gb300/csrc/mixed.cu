@@ -16,6 +16,7 @@
 #include <new>
 
 #include "cg_kernels.cuh"
+#include "df64.cuh"
 #include "graph.h"
 #include "workspace.h"
 
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(BS) k_reliable_finish(int Vh, const double2* r
 
 // ------------------------------------------------------------- driver
 
-template <class S, class SX, class LF>
+template <class S, class SX, class LF, class LF64T, class SD64>
 struct MixedPlan {
     static int enqueue_main(stag_ctx ctx, MixedSlot& m, const LF& U, cudaStream_t s, LoopGraph* lg, int use_cond)
     {
@@ -200,24 +201,24 @@ struct MixedPlan {
           r = m.template spinor<S>(m.r);
         SX x = m.template spinor<SX>(m.xlo);
         k_hop_guarded<LF, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, 1, U, p, t, m.sc);
-        k_Mp_dot<LF, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, m.sc, ctx->partials,
+        k_Mp_dot<LF, S, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, m.sc, ctx->partials,
                                                                            ctx->counters);
         k_mixed_update<S, SX, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(
             g.Vh, x, r, p, Ap, m.sc, ctx->partials, ctx->counters, lg ? lg->w : 0, lg ? lg->i : 0, use_cond);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
-    static int enqueue_reliable(stag_ctx ctx, MixedSlot& m, const LinkField<double2, 18>& U64, cudaStream_t s,
-                                LoopGraph* lg, int use_cond, int guard)
+    static int enqueue_reliable(stag_ctx ctx, MixedSlot& m, const LF64T& U64, cudaStream_t s, LoopGraph* lg,
+                                int use_cond, int guard)
     {
         const Geom g = ctx->g;
         Workspace* ws = ctx->ws;
         SX x = m.template spinor<SX>(m.xlo);
         S r = m.template spinor<S>(m.r);
         k_accum_x<SX, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(g.Vh, ws->x, x, m.sc, guard);
-        k_hop<LinkField<double2, 18>, SpinorF64, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(
-            g, 1, U64, SpinorF64{ws->x}, SpinorF64{ws->t}, m.sc, guard);
-        k_true_resid_f64<LinkField<double2, 18>, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(
+        k_hop<LF64T, SD64, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, 1, U64, SD64{ws->x},
+                                                                                SD64{ws->t}, m.sc, guard);
+        k_true_resid_f64<LF64T, SD64, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(
             g, U64, ws->t, ws->x, ws->b, ws->r, m.sc, ctx->partials, ctx->counters, guard);
         k_reliable_finish<S, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(g.Vh, ws->r, r, m.sc,
                                                                                   lg ? lg->w : 0, use_cond, guard);
@@ -239,9 +240,10 @@ struct MixedPlan {
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
         const void* lk64 = nullptr;
-        STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk64));
+        const int p64 = prm.f64_arith == STAG_F64X ? STAG_F64X : STAG_F64;
+        STAG_TRY(ensure_links(ctx, p64, 18, &lk64));
         const LF U{(const typename LF::store*)lk, g.Vh};
-        const LinkField<double2, 18> U64{(const double2*)lk64, g.Vh};
+        const LF64T U64{(const typename LF64T::store*)lk64, g.Vh};
         const size_t bytes = (size_t)3 * g.Vh * sizeof(double2);
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
         const double delta = prm.delta > 0 ? prm.delta : 0.1;
@@ -251,13 +253,14 @@ struct MixedPlan {
             m.template spinor<SX>(m.xlo), m.sc, prm.tol, maxiter, mass * mass, delta, ctx->partials, ctx->counters);
         STAG_CUDA_TRY(cudaGetLastError());
         if (prm.use_graph) {
-            if (!m.lg.exec) {
+            if (!m.lg.exec || m.graph_arith != p64) {
                 LoopGraph& lg = m.lg;
                 STAG_TRY(build_loop_graph(
                     ctx->cap_stream, lg, true,
                     [&](cudaStream_t s) { return enqueue_main(ctx, m, U, s, &lg, 1); },
                     [&](cudaStream_t s) { return enqueue_reliable(ctx, m, U64, s, &lg, 1, 0); },
                     [&](cudaStream_t s) { return enqueue_p(ctx, m, s); }));
+                m.graph_arith = p64;
             }
             STAG_CUDA_TRY(cudaGraphLaunch(m.lg.exec, ctx->stream));
         } else {
@@ -317,6 +320,25 @@ static int ensure_mixed(stag_ctx ctx, int prec, int recon, MixedSlot** out)
     return STAG_OK;
 }
 
+template <class LF64T, class SD64>
+static int dispatch_inner(stag_ctx ctx, MixedSlot& m, const void* lk, double2* x_out, const double2* b_in,
+                          double mass, const stag_solver_params& prm, stag_solver_stats* st)
+{
+    const int prec = prm.inner_prec, recon = prm.inner_recon;
+    if (prec == STAG_F32) {
+        if (recon == 12)
+            return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 12>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in,
+                                                                                             mass, prm, st);
+        return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 18>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in, mass,
+                                                                                         prm, st);
+    }
+    if (recon == 12)
+        return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 12>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in,
+                                                                                          mass, prm, st);
+    return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 18>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in, mass,
+                                                                                      prm, st);
+}
+
 int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mass, const stag_solver_params& prm,
                    stag_solver_stats* st)
 {
@@ -329,14 +351,12 @@ int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mas
     STAG_TRY(ensure_mixed(ctx, prec, recon, &m));
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
-    if (prec == STAG_F32) {
-        if (recon == 12)
-            return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 12>>::solve(ctx, *m, lk, x_out, b_in, mass, prm, st);
-        return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 18>>::solve(ctx, *m, lk, x_out, b_in, mass, prm, st);
+    if (prm.f64_arith == STAG_F64X) return dispatch_inner<LinkFieldDF<18>, SpinorF64asDF>(ctx, *m, lk, x_out, b_in, mass, prm, st);
+    if (prm.f64_arith != STAG_F64) {
+        set_error("f64_arith must be STAG_F64 or STAG_F64X");
+        return STAG_EINVAL;
     }
-    if (recon == 12)
-        return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 12>>::solve(ctx, *m, lk, x_out, b_in, mass, prm, st);
-    return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 18>>::solve(ctx, *m, lk, x_out, b_in, mass, prm, st);
+    return dispatch_inner<LinkField<double2, 18>, SpinorF64>(ctx, *m, lk, x_out, b_in, mass, prm, st);
 }
 
 void free_mixed(Workspace* ws)

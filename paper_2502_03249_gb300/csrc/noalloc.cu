@@ -142,7 +142,7 @@ extern "C" int stag_apply_M_noalloc(const int dims[4], const double* U, double* 
     cudaStream_t s = (cudaStream_t)stream;
     k_hop<LinkCanonicalF64, SpinorF64, BS><<<grid, BS, 0, s>>>(g, 1, L, SpinorF64{(double2*)in_even}, SpinorF64{t},
                                                                 nullptr, 0);
-    k_xpay_hop<LinkCanonicalF64, SpinorF64, BS><<<grid, BS, 0, s>>>(g, L, SpinorF64{t}, SpinorF64{(double2*)in_even},
+    k_xpay_hop<LinkCanonicalF64, SpinorF64, SpinorF64, BS><<<grid, BS, 0, s>>>(g, L, SpinorF64{t}, SpinorF64{(double2*)in_even},
                                                                      SpinorF64{(double2*)out_even}, mass * mass);
     STAG_CUDA_TRY(cudaGetLastError());
     return STAG_OK;

@@ -52,6 +52,21 @@ __global__ void k_derive_links(int Vh, const double2* __restrict__ in, S* __rest
     }
 }
 
+// internal F64/18 -> double-float split (hi = RN(x), lo = RN(x - hi)) per real.
+__global__ void k_split_links(int Vh, const double2* __restrict__ in, float4* __restrict__ out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (par, mu, h)
+    if (idx >= 8LL * Vh) return;
+    const long long pm = idx / Vh, h = idx - pm * Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double2 v = in[(pm * 9 + k) * Vh + h];
+        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+        out[(pm * 9 + k) * Vh + h] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih,
+                                                 __double2float_rn(v.y - (double)ih));
+    }
+}
+
 int upload_gauge(stag_ctx ctx, const double* U, int on_device)
 {
     const size_t n = (size_t)ctx->V * 4 * 9;
@@ -62,14 +77,9 @@ int upload_gauge(stag_ctx ctx, const double* U, int on_device)
         STAG_CUDA_TRY(cudaMemcpyAsync(staging, U, n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
         src = staging;
     }
-    // drop every derived copy; the F64/18 copy is rebuilt in place
-    for (int s = 1; s < 6; ++s) {
-        if (ctx->links[s]) {
-            cudaFreeAsync(ctx->links[s], ctx->stream);
-            ctx->links[s] = nullptr;
-            ctx->link_bytes[s] = 0;
-        }
-    }
+    // Derived copies are kept at their addresses and re-derived in place on
+    // their next use: CUDA graphs captured by the solvers hold these pointers.
+    for (int s = 1; s < 8; ++s) ctx->link_stale[s] = ctx->links[s] != nullptr;
     if (!ctx->links[0]) {
         STAG_CUDA_TRY(cudaMalloc(&ctx->links[0], n * sizeof(double2)));
         ctx->link_bytes[0] = n * sizeof(double2);
@@ -90,22 +100,23 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
-    if (prec < STAG_F64 || prec > STAG_F16 || (recon != 18 && recon != 12)) {
+    if (prec < STAG_F64 || prec > STAG_F64X || (recon != 18 && recon != 12) || (prec == STAG_F64X && recon != 18)) {
         set_error("unsupported links: prec %d recon %d", prec, recon);
         return STAG_EUNSUPPORTED;
     }
     const int slot = link_slot(prec, recon);
-    if (!ctx->links[slot]) {
+    if (!ctx->links[slot] || ctx->link_stale[slot]) {
         const int NE = recon == 12 ? 6 : 9;
-        const size_t esz = prec == STAG_F64 ? 16 : (prec == STAG_F32 ? 8 : 4);
+        const size_t esz = (prec == STAG_F64 || prec == STAG_F64X) ? 16 : (prec == STAG_F32 ? 8 : 4);
         const size_t bytes = (size_t)8 * ctx->g.Vh * NE * esz;
-        void* p = nullptr;
-        STAG_CUDA_TRY(cudaMalloc(&p, bytes));
+        void* p = ctx->links[slot];
+        if (!p) STAG_CUDA_TRY(cudaMalloc(&p, bytes));
         const long long work = 8LL * ctx->g.Vh;
         const int BS = 256;
         const unsigned grid = (unsigned)((work + BS - 1) / BS);
         const double2* src = (const double2*)ctx->links[0];
-        if (prec == STAG_F64) k_derive_links<double2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (double2*)p);
+        if (prec == STAG_F64X) k_split_links<<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float4*)p);
+        else if (prec == STAG_F64) k_derive_links<double2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (double2*)p);
         else if (prec == STAG_F32 && NE == 9) k_derive_links<float2, 9><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float2*)p);
         else if (prec == STAG_F32) k_derive_links<float2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float2*)p);
         else if (NE == 9) k_derive_links<__half2, 9><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (__half2*)p);
@@ -113,6 +124,7 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
         STAG_CUDA_TRY(cudaGetLastError());
         ctx->links[slot] = p;
         ctx->link_bytes[slot] = bytes;
+        ctx->link_stale[slot] = false;
     }
     *out = ctx->links[slot];
     return STAG_OK;
@@ -122,6 +134,7 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
 
 size_t lo_spinor_bytes(const Geom& g, int prec)
 {
+    // STAG_F64 and STAG_F64X both store canonical complex128
     if (prec == STAG_F32) return (size_t)g.Vh * 3 * sizeof(float2);
     if (prec == STAG_F16) return (size_t)g.Vh * 3 * sizeof(__half2) + (size_t)g.Vh * sizeof(float);
     return (size_t)g.Vh * 3 * sizeof(double2);

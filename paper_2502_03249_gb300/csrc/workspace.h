@@ -14,6 +14,7 @@ struct MixedSlot {
     CgScalars* sc = nullptr;
     LoopGraph lg;
     int Vh = 0;
+    int graph_arith = -1;   // double arithmetic the graph's reliable update was built with
     bool ready = false;
     template <class S> S spinor(void* buf) const;
 };
@@ -72,8 +73,8 @@ struct Workspace {
     CgScalars* sc = nullptr;        // device scalar records
     CgScalars* sc_host = nullptr;   // pinned host mirror for the final read
     bool f64_ready = false;
-    cudaGraph_t f64_graph = nullptr;
-    cudaGraphExec_t f64_exec = nullptr;
+    cudaGraph_t f64_graph[2] = {nullptr, nullptr};       // [IEEE double, double-float]
+    cudaGraphExec_t f64_exec[2] = {nullptr, nullptr};
     MixedSlot mixed[2][2];          // [F32, F16][18, 12]
     BatchSlot batch[3][2];          // [F64, F32, F16][18, 12]
     MsSlot ms[2];                   // multi-shift [F64, F32]

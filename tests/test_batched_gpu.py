@@ -29,7 +29,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("prec,recon,tol", [(0, 18, 1e-12), (0, 12, 1e-12), (1, 12, 1e-5), (1, 18, 1e-5),
-                                            (2, 12, 1e-3)])
+                                            (2, 12, 1e-3), (3, 18, 1e-12)])
 @pytest.mark.parametrize("nrhs", [1, 3, 16])
 def test_multi_dslash_matches_single_and_oracle(stag, prec, recon, tol, nrhs):
     import torch
@@ -44,11 +44,11 @@ def test_multi_dslash_matches_single_and_oracle(stag, prec, recon, tol, nrhs):
         out = ctx.new_half(nrhs)
         ctx.dslash_multi(out, ind, 1, prec, recon, nb)
         assert bool((out == single).all()), nb
-    Us = {0: U, 1: enc.round_f32(U), 2: enc.round_f16(U)}[prec]
+    Us = {0: U, 1: enc.round_f32(U), 2: enc.round_f16(U), 3: U}[prec]
     if recon == 12:
         Us = enc.recon12(U, {0: None, 1: enc.round_f32, 2: enc.round_f16}[prec])
     for k in range(nrhs):
-        src = {0: psi[k], 1: enc.round_f32(psi[k]), 2: enc.half_spinor(psi[k])}[prec]
+        src = {0: psi[k], 1: enc.round_f32(psi[k]), 2: enc.half_spinor(psi[k]), 3: psi[k]}[prec]
         assert rel(host(out[k]), orc.dslash_oe(dims, Us, src)) <= tol
 
 
@@ -74,19 +74,21 @@ def test_batched_cg_every_system_converges(stag, prec, recon, rhs_block):
 
 def test_batched_f64_matches_single_solves(stag):
     """Plain double-precision batched CG follows the same recurrence as the
-    single-system solver: same iteration counts, solutions agree to rounding."""
-    dims, mass, nrhs = (6, 4, 2, 10), 0.05, 4
+    single-system solver (its reductions are blocked differently, so rounding
+    differs): iteration counts within 2 %, solutions within the residual
+    bound 2 tol (m^2 + 64) / m^2 of each other."""
+    dims, mass, nrhs, tol = (6, 4, 2, 10), 0.2, 4, 1e-11
     U = li.random_links(dims, "haar", seed=521)
     B = dev(li.gaussian_half(dims, seed=522, nvec=nrhs))
     ctx = stag.Context(dims)
     ctx.upload_gauge(dev(U))
     X = ctx.new_half(nrhs)
-    st = ctx.cg_solve_multi(X, B, mass, tol=1e-11, inner_prec=0, inner_recon=18)
+    st = ctx.cg_solve_multi(X, B, mass, tol=tol, inner_prec=0, inner_recon=18)
     for k in range(nrhs):
         x = ctx.new_half()
-        s1 = ctx.cg_solve(x, B[k].contiguous(), mass, tol=1e-11)
-        assert abs(s1["iters"] - st[k]["iters"]) <= 2
-        assert rel(host(X[k]), host(x)) <= 1e-9
+        s1 = ctx.cg_solve(x, B[k].contiguous(), mass, tol=tol)
+        assert abs(s1["iters"] - st[k]["iters"]) <= max(2, 0.02 * s1["iters"])
+        assert rel(host(X[k]), host(x)) <= 2 * tol * (mass ** 2 + 64) / mass ** 2
 
 
 def test_batched_32c16_sixteen_rhs(stag):

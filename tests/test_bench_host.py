@@ -1,0 +1,76 @@
+"""Host-side pieces of bench.py: the paper's counts (Sec. 4.3) that the
+measurement accounting relies on, and the multi-rank aggregation, run as two
+gloo ranks on the CPU."""
+
+import os
+import socket
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def read_golden():
+    vals = {}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_counts.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    return vals
+
+
+def test_flop_and_float_counts_match_the_paper():
+    import bench
+    g = read_golden()
+    # 570 flop per site: per direction two complex 3x3 mat-vecs (9 complex
+    # multiplies of 6 flop + 6 complex adds of 2 flop) and one 3-vector add,
+    # plus the 3 adds of the four direction sums
+    matvec = 9 * 6 + 6 * 2
+    assert 4 * (2 * matvec + 3 * 2) + 3 * 3 * 2 == g["flop_per_site"] == bench.FLOP_PER_SITE
+    assert bench.paper_float_count(1) == g["floats_per_site"]
+    assert abs(bench.paper_arithmetic_intensity(1, 8) - g["ai_fp64"]) < 0.005
+    assert abs(bench.paper_arithmetic_intensity(1, 4) - g["ai_fp32"]) < 0.005
+
+
+def test_compulsory_bytes():
+    import bench
+    assert bench.dslash_bytes_per_site(8, 18) == 1248
+    assert bench.dslash_bytes_per_site(8, 12) == 864
+    assert bench.dslash_bytes_per_site(4, 12) == 432
+
+
+def test_weak_scaling_value():
+    import bench
+    v1 = bench.weak_scaling_value(1, 131072, 162, 13.0)
+    assert abs(v1 - 570 * 131072 * 162 / 13e-3 * 1e-9) < 1e-6
+    assert abs(bench.weak_scaling_value(4, 131072, 162, 13.0) - 4 * v1) < 1e-6
+
+
+def _rank(rank, ws, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    q.put((rank, bench.max_over_ranks(10.0 + 5 * rank, ws)))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get() for _ in range(2))
+    assert got == {0: 15.0, 1: 15.0}

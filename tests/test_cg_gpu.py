@@ -45,13 +45,15 @@ def test_apply_M_matches_oracle(stag, dims):
 
 
 @pytest.mark.parametrize("use_graph", [1, 0])
-def test_cg_4x4_workload(stag, use_graph):
-    """4^4, Haar links, m = 0.1, stop at true residual 1e-10."""
+@pytest.mark.parametrize("arith", [0, 3])
+def test_cg_4x4_workload(stag, use_graph, arith):
+    """4^4, Haar links, m = 0.1, stop at true residual 1e-10; IEEE double (0) and
+    double-float (3) operator arithmetic."""
     dims, mass = (4, 4, 4, 4), 0.1
     ctx, U = setup(stag, dims, seed=li.workload_seed(0, 0))
     b = li.gaussian_half(dims, seed=li.workload_seed(0, 1))
     x = ctx.new_half()
-    st = ctx.cg_solve(x, dev(b), mass, tol=1e-10, use_graph=use_graph)
+    st = ctx.cg_solve(x, dev(b), mass, tol=1e-10, use_graph=use_graph, f64_arith=arith)
     xr = host(x)
     assert st["status"] == 0
     res = orc.true_residual(dims, U, mass, xr, b)
@@ -61,17 +63,30 @@ def test_cg_4x4_workload(stag, use_graph):
     assert abs(st["iters"] - it_cpu) <= max(3, it_cpu // 20)
 
 
-def test_graph_and_host_loop_identical(stag):
+@pytest.mark.parametrize("arith", [0, 3])
+def test_graph_and_host_loop_identical(stag, arith):
     dims, mass = (6, 4, 2, 10), 0.05
     ctx, U = setup(stag, dims, seed=311)
     b = dev(li.gaussian_half(dims, seed=312))
     x1, x2 = ctx.new_half(), ctx.new_half()
-    s1 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1)
-    s2 = ctx.cg_solve(x2, b, mass, tol=1e-11, use_graph=0, check_every=7)
+    s1 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1, f64_arith=arith)
+    s2 = ctx.cg_solve(x2, b, mass, tol=1e-11, use_graph=0, check_every=7, f64_arith=arith)
     assert s1["iters"] == s2["iters"]
     assert bool((x1 == x2).all())      # deterministic reductions: bit for bit
-    s3 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1)   # graph reused
+    s3 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1, f64_arith=arith)   # graph reused
     assert s3["iters"] == s1["iters"] and bool((x1 == x2).all())
+
+
+def test_shifted_solve(stag):
+    dims, mass, sigma = (10, 6, 4, 6), 0.05, 0.3
+    ctx, U = setup(stag, dims, "smooth", eps=0.3, seed=341)
+    b = li.gaussian_half(dims, seed=342)
+    x = ctx.new_half()
+    st = ctx.cg_solve_shifted(x, dev(b), mass, sigma, tol=1e-10)
+    assert st["status"] == 0
+    assert orc.true_residual(dims, U, mass, host(x), b, sigma=sigma) <= 1e-10
+    with pytest.raises(stag.StagError):
+        ctx.cg_solve_shifted(x, dev(b), mass, -1.0)
 
 
 @pytest.mark.parametrize("dims,mass,tol", [((4, 4, 4, 4), 0.1, 1e-13), ((8, 8, 8, 8), 0.5, 3e-14)])
@@ -84,7 +99,7 @@ def test_cg_tight_solution_matches_oracle(stag, dims, mass, tol):
     ctx, U = setup(stag, dims, seed=321)
     b = li.gaussian_half(dims, seed=322)
     x = ctx.new_half()
-    st = ctx.cg_solve(x, dev(b), mass, tol=tol)
+    st = ctx.cg_solve(x, dev(b), mass, tol=tol, f64_arith=0)   # IEEE double: tol below the double-float floor
     x_cpu, _, rel_cpu, st_cpu = orc.cg(dims, U, mass, b, tol=tol)
     assert st_cpu == 0 and st["status"] == 0
     if dims == (4, 4, 4, 4):
@@ -97,24 +112,29 @@ def test_cg_tight_solution_matches_oracle(stag, dims, mass, tol):
     assert rel(host(x), x_cpu) <= 2 * tol * cond
 
 
-def test_cg_stagnation_stops(stag):
+@pytest.mark.parametrize("arith,floor", [(0, 1e-12), (3, 1e-11)])
+def test_cg_stagnation_stops(stag, arith, floor):
     """A tolerance below the rounding floor ends with NOT_CONVERGED after a few
-    restarts instead of spinning until maxiter."""
+    restarts instead of spinning until maxiter.  The floor of the recomputed
+    residual is set by the operator's rounding amplified by the cancellation in
+    M = m^2 - D_eo D_oe (|D_eo D_oe x| ~ 16 |x| against m^2 |x|): ~1e-13 for
+    IEEE double, ~1e-12 for double-float (2^-44 per hop sum) at m = 0.1."""
     dims = (8, 8, 8, 8)
     ctx, U = setup(stag, dims, seed=323)
     b = dev(li.gaussian_half(dims, seed=324))
     x = ctx.new_half()
-    st = ctx.cg_solve(x, b, 0.1, tol=1e-17, raise_on_fail=False)
-    assert st["status"] == 1 and st["restarts"] < 10 and st["true_rel_residual"] < 1e-12
+    st = ctx.cg_solve(x, b, 0.1, tol=1e-17, raise_on_fail=False, f64_arith=arith)
+    assert st["status"] == 1 and st["restarts"] < 10 and st["true_rel_residual"] < floor
 
 
-def test_cg_32c8_workload(stag):
-    """32^3 x 8, smooth links eps = 0.3, m = 0.01, true residual 1e-10."""
+@pytest.mark.parametrize("arith", [0, 3])
+def test_cg_32c8_workload(stag, arith):
+    """32^3 x 8, smooth links eps = 0.3, m = 0.01, true residual 1e-10 (the bench step)."""
     dims, mass = (32, 32, 32, 8), 0.01
     ctx, U = setup(stag, dims, "smooth", eps=0.3, seed=li.workload_seed(1, 0))
     b = li.gaussian_half(dims, seed=li.workload_seed(1, 1))
     x = ctx.new_half()
-    st = ctx.cg_solve(x, dev(b), mass, tol=1e-10)
+    st = ctx.cg_solve(x, dev(b), mass, tol=1e-10, f64_arith=arith)
     assert st["status"] == 0 and st["iters"] > 10
     assert orc.true_residual(dims, U, mass, host(x), b) <= 1e-10
 

@@ -118,6 +118,37 @@ def test_f16_matches_oracle_on_stored_values(stag, dims, recon):
     assert rel(got, orc.dslash_oe(dims, U, psi)) <= 3e-3
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 6), (8, 8, 8, 8)])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_f64x_double_float_matches_oracle(stag, dims, parity):
+    """Double-float arithmetic (48-bit significand) on double storage meets the
+    double-precision bar: relative L2 error <= 1e-12 against the oracle."""
+    U = li.random_links(dims, "haar", seed=271)
+    rng = np.random.default_rng(272)
+    Vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    # site magnitudes spread over 2^-60 .. 2^20, one exact zero site
+    psi = li.gaussian_half(dims, seed=273) * np.exp2(rng.uniform(-60, 20, (Vh, 1)))
+    psi[3] = 0.0
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    (ctx.dslash_eo if parity == 0 else ctx.dslash_oe)(out, dev(psi), 3, 18)
+    ref = orc.dslash_half(dims, U, psi, parity)
+    got = host(out)
+    assert rel(got, ref) <= 1e-12
+    # per site, relative to that site's own scale of inputs: far sites keep precision too
+    scale = np.abs(ref).max(axis=1) + 1e-300
+    assert np.max(np.abs(got - ref).max(axis=1) / scale) <= 1e-9
+
+
+def test_f64x_rejects_12_real(stag):
+    dims = (4, 4, 4, 4)
+    ctx = make_ctx(stag, dims, li.random_links(dims, "haar", seed=281))
+    out = ctx.new_half()
+    with pytest.raises(stag.StagError) as e:
+        ctx.dslash_eo(out, dev(li.gaussian_half(dims, seed=282)), 3, 12)
+    assert e.value.code == -6
+
+
 def test_full_size_32c8_f64(stag):
     """The 32^3 x 8 workload (smooth links eps = 0.3): every output element."""
     dims = (32, 32, 32, 8)
@@ -129,7 +160,10 @@ def test_full_size_32c8_f64(stag):
     ref = orc.dslash_eo(dims, U, psi)
     assert rel(host(out), ref) <= 1e-12
     ctx.dslash_oe(out, dev(psi))
-    assert rel(host(out), orc.dslash_oe(dims, U, psi)) <= 1e-12
+    ref = orc.dslash_oe(dims, U, psi)
+    assert rel(host(out), ref) <= 1e-12
+    ctx.dslash_oe(out, dev(psi), 3, 18)
+    assert rel(host(out), ref) <= 1e-12
 
 
 def test_deterministic_repeat(stag):

@@ -27,13 +27,14 @@ INNER = [(1, 18), (1, 12), (2, 18), (2, 12)]
 @pytest.mark.parametrize("dims,mass,recipe,eps", [((4, 4, 4, 4), 0.1, "haar", None),
                                                   ((10, 6, 4, 6), 0.05, "smooth", 0.3),
                                                   ((8, 8, 8, 8), 0.02, "smooth", 0.2)])
-def test_mixed_reaches_double_residual(stag, prec, recon, dims, mass, recipe, eps):
+@pytest.mark.parametrize("arith", [0, 3])
+def test_mixed_reaches_double_residual(stag, prec, recon, dims, mass, recipe, eps, arith):
     U = li.random_links(dims, recipe, eps=eps, seed=401)
     b = li.gaussian_half(dims, seed=402)
     ctx = stag.Context(dims)
     ctx.upload_gauge(dev(U))
     x = ctx.new_half()
-    st = ctx.cg_solve_mixed(x, dev(b), mass, tol=1e-10, inner_prec=prec, inner_recon=recon)
+    st = ctx.cg_solve_mixed(x, dev(b), mass, tol=1e-10, inner_prec=prec, inner_recon=recon, f64_arith=arith)
     res = orc.true_residual(dims, U, mass, host(x), b)
     assert st["status"] == 0 and res <= 1e-10, (st, res)
     assert st["reliable_updates"] >= 1
