@@ -251,7 +251,9 @@ class Timer:
 
 
 def dslash_kernel_entry(timer, ctx, psi, out, prec, recon, vh, hbm):
-    ms, _ = timer(lambda: ctx.dslash_eo(out, psi, prec, recon), reps=20, warm=3)
+    """The bare operator kernel (internal storage, no conversions), one launch per timing."""
+    ctx.dslash_prepare(psi, prec)
+    ms, _ = timer(lambda: ctx.dslash_repeat(prec, recon, 1), reps=20, warm=3)
     pb = {0: 8, 3: 8, 1: 4, 2: 2}[prec]
     per_site = dslash_bytes_per_site(pb, recon) + (8 if prec == 2 else 0)
     gbs = per_site * vh / (ms * 1e-3) * 1e-9

@@ -118,6 +118,15 @@ int stag_dslash_eo(stag_ctx ctx, double *out_even, const double *in_odd, int pre
 /* out_odd = D_oe in_even, as stag_dslash_eo with the parities exchanged. */
 int stag_dslash_oe(stag_ctx ctx, double *out_odd, const double *in_even, int prec, int recon);
 
+/* Measurement support: stag_dslash_prepare converts one canonical half field
+ * (device) into the internal storage of prec (once); stag_dslash_repeat then
+ * applies D_eo to it nrep times into a context-owned output with no
+ * conversions, so that a caller's CUDA events on the context's stream around
+ * it time the bare operator kernel.  Asynchronous.  Errors: STAG_EINVAL
+ * (repeat before prepare, other precision), STAG_ENOGAUGE, STAG_EUNSUPPORTED. */
+int stag_dslash_prepare(stag_ctx ctx, const double *in, int prec);
+int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep);
+
 /* Multi-vector operator (Sec. 4.3, NMULTI): out_k = D_{p,1-p} in_k for
  * k = 0..nrhs-1, with each link loaded once per site for a block of
  * rhs_block vectors (1, 2, 4, 8 or 16; 0 = autotuned, cached per context).

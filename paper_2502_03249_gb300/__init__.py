@@ -84,6 +84,8 @@ def _declare(lib):
         "stag_dslash_eo": ([P, P, P, I, I], I),
         "stag_dslash_oe": ([P, P, P, I, I], I),
         "stag_apply_M": ([P, P, P, D], I),
+        "stag_dslash_prepare": ([P, P, I], I),
+        "stag_dslash_repeat": ([P, I, I, I], I),
         "stag_solver_params_default": ([ctypes.POINTER(SolverParams)], None),
         "stag_cg_solve": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_cg_solve_mixed": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
@@ -212,6 +214,16 @@ class Context:
         self._sync_stream()
         _check(self._lib.stag_dslash_oe(self._h, self._field(out, "out"), self._field(inp, "in"), prec, recon))
         return out
+
+    def dslash_prepare(self, inp, prec):
+        """stag_dslash_prepare: convert inp once into the internal storage of prec."""
+        self._sync_stream()
+        _check(self._lib.stag_dslash_prepare(self._h, self._field(inp, "in"), int(prec)))
+
+    def dslash_repeat(self, prec, recon, nrep=1):
+        """stag_dslash_repeat: nrep bare operator launches on the prepared internal field."""
+        self._sync_stream()
+        _check(self._lib.stag_dslash_repeat(self._h, int(prec), int(recon), int(nrep)))
 
     def apply_M(self, out, inp, mass):
         """stag_apply_M: out = (m^2 - D_eo D_oe) inp on even sites."""

@@ -159,6 +159,7 @@ int stag_create(stag_ctx* out, const int dims[4], void* stream)
     ctx->g.Vh = (int)(V / 2);
     ctx->V = V;
     ctx->stream = (cudaStream_t)stream;
+    ctx->prepared_prec = -1;
     int rc = STAG_OK;
     do {
         if (cudaGetDevice(&ctx->device) != cudaSuccess) { rc = STAG_ECUDA; break; }
@@ -240,6 +241,44 @@ int stag_dslash_eo(stag_ctx ctx, double* out_even, const double* in_odd, int pre
 int stag_dslash_oe(stag_ctx ctx, double* out_odd, const double* in_even, int prec, int recon)
 {
     return dslash_entry(ctx, out_odd, in_even, prec, recon, 1);
+}
+
+int stag_dslash_prepare(stag_ctx ctx, const double* in, int prec)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(in, "in"));
+    if (prec < STAG_F64 || prec > STAG_F64X) {
+        set_error("unsupported prec %d", prec);
+        return STAG_EUNSUPPORTED;
+    }
+    const size_t bytes = lo_spinor_bytes(ctx->g, prec);
+    STAG_TRY(ensure_lo_tmp(ctx, bytes));
+    if (prec == STAG_F64 || prec == STAG_F64X)
+        STAG_CUDA_TRY(cudaMemcpyAsync(ctx->tmp_lo_in, in, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+        STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, 1, ctx->stream));
+    ctx->prepared_prec = prec;
+    return STAG_OK;
+}
+
+int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep)
+{
+    STAG_TRY(check_ctx(ctx));
+    if (ctx->prepared_prec != prec || !ctx->tmp_lo_in) {
+        set_error("call stag_dslash_prepare with this precision first");
+        return STAG_EINVAL;
+    }
+    if (nrep < 1 || recon != 18 && recon != 12 || (prec == STAG_F64X && recon != 18)) {
+        set_error("nrep must be >= 1 and recon 18 or 12");
+        return STAG_EINVAL;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    for (int k = 0; k < nrep; ++k)
+        STAG_TRY(launch_dslash(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream));
+    return STAG_OK;
 }
 
 int stag_apply_M(stag_ctx ctx, double* out_even, const double* in_even, double mass)

@@ -566,9 +566,7 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
         return multi_dslash_tuned(ctx, tag, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, stride, nrhs,
                                   par_out, nb, nb_used);
     }
-    const size_t codes = (size_t)3 * Vh;
-    SpinorF16 si{(__half2*)in, (float*)((__half2*)in + codes), Vh};
-    SpinorF16 so{(__half2*)out, (float*)((__half2*)out + codes), Vh};
+    SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
     if (recon == 18)
         return multi_dslash_tuned(ctx, tag, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, stride, nrhs,
                                   par_out, nb, nb_used);

@@ -205,6 +205,93 @@ struct LinkField {
     }
 };
 
+// Float and half links are stored in 16-byte chunks so that a thread loads a
+// whole link with two to five vector loads.  For each (parity, direction) the
+// NE elements of a link (8 bytes each for float, 4 for half) are cut into NC
+// full 16-byte chunks plus a remainder of RB bytes; chunk j of all sites is a
+// plane [Vh] of uint4, the remainder a plane [Vh] of RB-byte words:
+//     block(par, mu) = base + (par*4 + mu) * NE*EB*Vh bytes
+//     chunk j at block + j*16*Vh + 16*h,  remainder at block + NC*16*Vh + RB*h
+template <int EB, int NE> struct LinkChunks {
+    static constexpr int BYTES = EB * NE;
+    static constexpr int NC = BYTES / 16;
+    static constexpr int RB = BYTES % 16;     // 0, 4 or 8
+    static constexpr int WORDS = BYTES / 4;
+    // all 32-bit words of the link at (block, h)
+    static __device__ __forceinline__ void load(const char* block, int Vh, int h, uint32_t* w)
+    {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(block + (size_t)j * 16 * Vh) + h);
+            w[4 * j] = q.x;
+            w[4 * j + 1] = q.y;
+            w[4 * j + 2] = q.z;
+            w[4 * j + 3] = q.w;
+        }
+        const char* rem = block + (size_t)NC * 16 * Vh;
+        if constexpr (RB == 8) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2*>(rem) + h);
+            w[4 * NC] = q.x;
+            w[4 * NC + 1] = q.y;
+        } else if constexpr (RB == 4) {
+            w[4 * NC] = __ldg(reinterpret_cast<const unsigned int*>(rem) + h);
+        }
+    }
+    static __device__ __forceinline__ void store(char* block, int Vh, int h, const uint32_t* w)
+    {
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+            reinterpret_cast<uint4*>(block + (size_t)j * 16 * Vh)[h] =
+                make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+        char* rem = block + (size_t)NC * 16 * Vh;
+        if constexpr (RB == 8) reinterpret_cast<uint2*>(rem)[h] = make_uint2(w[4 * NC], w[4 * NC + 1]);
+        else if constexpr (RB == 4) reinterpret_cast<unsigned int*>(rem)[h] = w[4 * NC];
+    }
+};
+
+template <int RECON>
+struct LinkField<float2, RECON> {
+    typedef float real;
+    typedef float2 store;
+    static constexpr int NE = (RECON == 12) ? 6 : 9;
+    typedef LinkChunks<8, NE> C;
+    const float2* base;
+    int Vh;
+    __device__ __forceinline__ Mat3<float> load(int par, int mu, int h) const
+    {
+        uint32_t w[C::WORDS];
+        C::load(reinterpret_cast<const char*>(base) + (size_t)(par * 4 + mu) * C::BYTES * Vh, Vh, h, w);
+        Mat3<float> U;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) U.m[k] = {__uint_as_float(w[2 * k]), __uint_as_float(w[2 * k + 1])};
+        if (RECON == 12) reconstruct_row2(U);
+        return U;
+    }
+};
+
+template <int RECON>
+struct LinkField<__half2, RECON> {
+    typedef float real;
+    typedef __half2 store;
+    static constexpr int NE = (RECON == 12) ? 6 : 9;
+    typedef LinkChunks<4, NE> C;
+    const __half2* base;
+    int Vh;
+    __device__ __forceinline__ Mat3<float> load(int par, int mu, int h) const
+    {
+        uint32_t w[C::WORDS];
+        C::load(reinterpret_cast<const char*>(base) + (size_t)(par * 4 + mu) * C::BYTES * Vh, Vh, h, w);
+        Mat3<float> U;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+            U.m[k] = {f.x, f.y};
+        }
+        if (RECON == 12) reconstruct_row2(U);
+        return U;
+    }
+};
+
 // ---------------------------------------------------------- spinor storage
 //
 // F64: the canonical layout, complex128 [h][3] (double2 per colour).
@@ -216,7 +303,6 @@ struct LinkField {
 
 struct SpinorF64 {
     typedef double real;
-    static constexpr bool has_norm = false;
     double2* p;
     // field k of a multi field whose fields are stride bytes apart
     __host__ __device__ __forceinline__ SpinorF64 at(int k, size_t stride) const
@@ -247,70 +333,61 @@ struct SpinorF64 {
     }
 };
 
+// F32: two planes per field, colours 0 and 1 as a float4 [Vh], colour 2 as a
+// float2 [Vh] right after it (24 bytes per site, two vector loads).
 struct SpinorF32 {
     typedef float real;
-    static constexpr bool has_norm = false;
-    float2* p;
+    float2* p;   // start of the field (the float4 plane)
     int Vh;
     __host__ __device__ __forceinline__ SpinorF32 at(int k, size_t stride) const
     {
         return SpinorF32{(float2*)((char*)p + (size_t)k * stride), Vh};
     }
-    __device__ __forceinline__ Vec3<float> load(int h) const
+    __device__ __forceinline__ const float4* pa() const { return reinterpret_cast<const float4*>(p); }
+    __device__ __forceinline__ const float2* pb() const { return reinterpret_cast<const float2*>(pa() + Vh); }
+    __device__ __forceinline__ Vec3<float> unpack(float4 a, float2 b) const
     {
         Vec3<float> v;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v.c[c] = to_cplx(__ldg(p + (size_t)c * Vh + h));
+        v.c[0] = {a.x, a.y};
+        v.c[1] = {a.z, a.w};
+        v.c[2] = {b.x, b.y};
         return v;
     }
-    __device__ __forceinline__ Vec3<float> load_rw(int h) const
-    {
-        Vec3<float> v;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v.c[c] = to_cplx(p[(size_t)c * Vh + h]);
-        return v;
-    }
+    __device__ __forceinline__ Vec3<float> load(int h) const { return unpack(__ldg(pa() + h), __ldg(pb() + h)); }
+    __device__ __forceinline__ Vec3<float> load_rw(int h) const { return unpack(pa()[h], pb()[h]); }
     __device__ __forceinline__ void store(int h, const Vec3<float>& v) const
     {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) p[(size_t)c * Vh + h] = make_float2(v.c[c].re, v.c[c].im);
+        reinterpret_cast<float4*>(p)[h] = make_float4(v.c[0].re, v.c[0].im, v.c[1].re, v.c[1].im);
+        const_cast<float2*>(pb())[h] = make_float2(v.c[2].re, v.c[2].im);
     }
 };
 
+// F16: one 16-byte record per site: three __half2 codes and the float norm;
+// the value is code * norm, the norm being the largest magnitude of the six
+// real components of the site.
 struct SpinorF16 {
     typedef float real;
-    static constexpr bool has_norm = true;
-    __half2* p;
-    float* norm;
+    uint4* p;
     int Vh;
     __host__ __device__ __forceinline__ SpinorF16 at(int k, size_t stride) const
     {
-        return SpinorF16{(__half2*)((char*)p + (size_t)k * stride), (float*)((char*)norm + (size_t)k * stride), Vh};
+        return SpinorF16{(uint4*)((char*)p + (size_t)k * stride), Vh};
     }
-    __device__ __forceinline__ Vec3<float> load(int h) const
+    __device__ __forceinline__ Vec3<float> unpack(uint4 q) const
     {
+        const float n = __uint_as_float(q.w);
+        const unsigned int w[3] = {q.x, q.y, q.z};
         Vec3<float> v;
-        const float n = __ldg(norm + h);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            Cplx<float> q = to_cplx(ldg_nc(p + (size_t)c * Vh + h));
-            v.c[c].re = q.re * n;
-            v.c[c].im = q.im * n;
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[c]));
+            v.c[c].re = f.x * n;
+            v.c[c].im = f.y * n;
         }
         return v;
     }
-    __device__ __forceinline__ Vec3<float> load_rw(int h) const
-    {
-        Vec3<float> v;
-        const float n = norm[h];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Cplx<float> q = to_cplx(p[(size_t)c * Vh + h]);
-            v.c[c].re = q.re * n;
-            v.c[c].im = q.im * n;
-        }
-        return v;
-    }
+    __device__ __forceinline__ Vec3<float> load(int h) const { return unpack(__ldg(p + h)); }
+    __device__ __forceinline__ Vec3<float> load_rw(int h) const { return unpack(p[h]); }
     // Encode: norm = max |component| (float), code = RN_half(component / norm)
     // with an IEEE float division; a zero site stores zeros.
     __device__ __forceinline__ void store(int h, const Vec3<float>& v) const
@@ -318,7 +395,7 @@ struct SpinorF16 {
         float n = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) n = fmaxf(n, fmaxf(fabsf(v.c[c].re), fabsf(v.c[c].im)));
-        norm[h] = n;
+        unsigned int w[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float re = 0.f, im = 0.f;
@@ -326,8 +403,10 @@ struct SpinorF16 {
                 re = __fdiv_rn(v.c[c].re, n);
                 im = __fdiv_rn(v.c[c].im, n);
             }
-            p[(size_t)c * Vh + h] = __floats2half2_rn(re, im);
+            const __half2 q = __floats2half2_rn(re, im);
+            w[c] = *reinterpret_cast<const unsigned int*>(&q);
         }
+        p[h] = make_uint4(w[0], w[1], w[2], __float_as_uint(n));
     }
 };
 

@@ -83,6 +83,7 @@ struct stag_ctx_s {
     size_t tmp_lo_bytes;
     stag::Workspace* ws;
     void* full_tmp;            // four half fields for the full-lattice solve
+    int prepared_prec;         // storage of tmp_lo_in after stag_dslash_prepare (-1: none)
     void* tune;                // autotuner cache (tune.cu)
     int last_rhs_block;        // right-hand sides per pass chosen by the last batched solve
 };

@@ -116,7 +116,6 @@ __device__ __forceinline__ double df_to_double(const DF& v) { return (double)v.h
 // Canonical double spinor ([h][3] complex128) read and written as double-floats.
 struct SpinorF64asDF {
     typedef DF real;
-    static constexpr bool has_norm = false;
     double2* p;
     __host__ __device__ __forceinline__ SpinorF64asDF at(int k, size_t stride) const
     {

@@ -46,9 +46,7 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
         return run_dslash(ctx, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, par_out, s);
     }
     if (prec == STAG_F16) {
-        const size_t codes = (size_t)3 * Vh;
-        SpinorF16 si{(__half2*)in, (float*)((__half2*)in + codes), Vh};
-        SpinorF16 so{(__half2*)out, (float*)((__half2*)out + codes), Vh};
+        SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
         if (recon == 18) return run_dslash(ctx, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, par_out, s);
         return run_dslash(ctx, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, par_out, s);
     }

@@ -28,28 +28,40 @@ __global__ void k_pack_gauge(Geom g, const double2* __restrict__ U, double2* __r
     for (int k = 0; k < 9; ++k) dst[(size_t)k * g.Vh] = src[k];
 }
 
-// internal F64/18 -> another (precision, compression); element k of NE kept.
-template <typename S, int NE>
-__global__ void k_derive_links(int Vh, const double2* __restrict__ in, S* __restrict__ out)
+// internal F64/18 -> F64/12: elements 0..5 (rows 0 and 1) kept, same layout.
+__global__ void k_derive_links_f64_12(int Vh, const double2* __restrict__ in, double2* __restrict__ out)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (par, mu, h)
     if (idx >= 8LL * Vh) return;
     const long long pm = idx / Vh, h = idx - pm * Vh;
 #pragma unroll
+    for (int k = 0; k < 6; ++k) out[(pm * 6 + k) * Vh + h] = in[(pm * 9 + k) * Vh + h];
+}
+
+// internal F64/18 -> float (EB = 8) or half (EB = 4) links in 16-byte chunks,
+// elements 0..NE-1 (NE = 6 keeps rows 0 and 1).  Conversions round to nearest
+// (double -> float, then float -> half).
+template <int EB, int NE>
+__global__ void k_derive_links_vec(int Vh, const double2* __restrict__ in, char* __restrict__ out)
+{
+    typedef LinkChunks<EB, NE> C;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (par, mu, h)
+    if (idx >= 8LL * Vh) return;
+    const long long pm = idx / Vh, h = idx - pm * Vh;
+    uint32_t w[C::WORDS];
+#pragma unroll
     for (int k = 0; k < NE; ++k) {
         const double2 v = in[(pm * 9 + k) * Vh + h];
-        S o;
-        if constexpr (sizeof(S) == 16) {
-            o = *reinterpret_cast<const S*>(&v);
-        } else if constexpr (sizeof(S) == 8) {
-            float2 f = make_float2((float)v.x, (float)v.y);   // double -> float, RN
-            o = *reinterpret_cast<S*>(&f);
+        const float re = (float)v.x, im = (float)v.y;
+        if constexpr (EB == 8) {
+            w[2 * k] = __float_as_uint(re);
+            w[2 * k + 1] = __float_as_uint(im);
         } else {
-            __half2 q = __floats2half2_rn((float)v.x, (float)v.y);  // via float, both RN
-            o = *reinterpret_cast<S*>(&q);
+            const __half2 q = __floats2half2_rn(re, im);
+            w[k] = *reinterpret_cast<const uint32_t*>(&q);
         }
-        out[(pm * NE + k) * Vh + h] = o;
     }
+    C::store(out + (size_t)pm * C::BYTES * Vh, Vh, (int)h, w);
 }
 
 // internal F64/18 -> double-float split (hi = RN(x), lo = RN(x - hi)) per real.
@@ -115,12 +127,13 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
         const int BS = 256;
         const unsigned grid = (unsigned)((work + BS - 1) / BS);
         const double2* src = (const double2*)ctx->links[0];
-        if (prec == STAG_F64X) k_split_links<<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float4*)p);
-        else if (prec == STAG_F64) k_derive_links<double2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (double2*)p);
-        else if (prec == STAG_F32 && NE == 9) k_derive_links<float2, 9><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float2*)p);
-        else if (prec == STAG_F32) k_derive_links<float2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (float2*)p);
-        else if (NE == 9) k_derive_links<__half2, 9><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (__half2*)p);
-        else k_derive_links<__half2, 6><<<grid, BS, 0, ctx->stream>>>(ctx->g.Vh, src, (__half2*)p);
+        const int Vh = ctx->g.Vh;
+        if (prec == STAG_F64X) k_split_links<<<grid, BS, 0, ctx->stream>>>(Vh, src, (float4*)p);
+        else if (prec == STAG_F64) k_derive_links_f64_12<<<grid, BS, 0, ctx->stream>>>(Vh, src, (double2*)p);
+        else if (prec == STAG_F32 && NE == 9) k_derive_links_vec<8, 9><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
+        else if (prec == STAG_F32) k_derive_links_vec<8, 6><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
+        else if (NE == 9) k_derive_links_vec<4, 9><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
+        else k_derive_links_vec<4, 6><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
         STAG_CUDA_TRY(cudaGetLastError());
         ctx->links[slot] = p;
         ctx->link_bytes[slot] = bytes;
@@ -136,7 +149,7 @@ size_t lo_spinor_bytes(const Geom& g, int prec)
 {
     // STAG_F64 and STAG_F64X both store canonical complex128
     if (prec == STAG_F32) return (size_t)g.Vh * 3 * sizeof(float2);
-    if (prec == STAG_F16) return (size_t)g.Vh * 3 * sizeof(__half2) + (size_t)g.Vh * sizeof(float);
+    if (prec == STAG_F16) return (size_t)g.Vh * 16;   // three __half2 codes + float norm per site
     return (size_t)g.Vh * 3 * sizeof(double2);
 }
 
@@ -153,10 +166,7 @@ __global__ void k_to_lo(int Vh, int nvec, const double2* __restrict__ in, SOut o
         f.c[c].re = (float)q[c].x;
         f.c[c].im = (float)q[c].y;
     }
-    SOut o = out;
-    o.p = (decltype(o.p))((char*)out.p + v * out_stride_bytes);
-    if constexpr (SOut::has_norm) o.norm = (float*)((char*)out.norm + v * out_stride_bytes);
-    o.store(h, f);
+    out.at(v, out_stride_bytes).store(h, f);
 }
 
 template <class SIn>
@@ -165,10 +175,7 @@ __global__ void k_from_lo(int Vh, int nvec, SIn in, size_t in_stride_bytes, doub
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)nvec * Vh) return;
     const int v = (int)(idx / Vh), h = (int)(idx - (long long)v * Vh);
-    SIn s = in;
-    s.p = (decltype(s.p))((char*)in.p + v * in_stride_bytes);
-    if constexpr (SIn::has_norm) s.norm = (float*)((char*)in.norm + v * in_stride_bytes);
-    const Vec3<float> f = s.load_rw(h);
+    const Vec3<float> f = in.at(v, in_stride_bytes).load_rw(h);
     double2* q = out + ((size_t)v * Vh + h) * 3;
 #pragma unroll
     for (int c = 0; c < 3; ++c) q[c] = make_double2((double)f.c[c].re, (double)f.c[c].im);
@@ -184,8 +191,7 @@ int convert_f64_to_lo(stag_ctx ctx, int prec, const double2* in, void* out, int 
     if (prec == STAG_F32) {
         k_to_lo<SpinorF32><<<grid, BS, 0, s>>>(Vh, nvec, in, SpinorF32{(float2*)out, Vh}, stride);
     } else if (prec == STAG_F16) {
-        SpinorF16 o{(__half2*)out, (float*)((__half2*)out + (size_t)3 * Vh), Vh};
-        k_to_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, in, o, stride);
+        k_to_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, in, SpinorF16{(uint4*)out, Vh}, stride);
     } else {
         set_error("convert_f64_to_lo: bad precision %d", prec);
         return STAG_EUNSUPPORTED;
@@ -204,8 +210,7 @@ int convert_lo_to_f64(stag_ctx ctx, int prec, const void* in, double2* out, int 
     if (prec == STAG_F32) {
         k_from_lo<SpinorF32><<<grid, BS, 0, s>>>(Vh, nvec, SpinorF32{(float2*)in, Vh}, stride, out);
     } else if (prec == STAG_F16) {
-        SpinorF16 i{(__half2*)in, (float*)((__half2*)in + (size_t)3 * Vh), Vh};
-        k_from_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, i, stride, out);
+        k_from_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, SpinorF16{(uint4*)in, Vh}, stride, out);
     } else {
         set_error("convert_lo_to_f64: bad precision %d", prec);
         return STAG_EUNSUPPORTED;

@@ -21,7 +21,7 @@ struct MixedSlot {
 template <> inline SpinorF32 MixedSlot::spinor<SpinorF32>(void* buf) const { return SpinorF32{(float2*)buf, Vh}; }
 template <> inline SpinorF16 MixedSlot::spinor<SpinorF16>(void* buf) const
 {
-    return SpinorF16{(__half2*)buf, (float*)((__half2*)buf + (size_t)3 * Vh), Vh};
+    return SpinorF16{(uint4*)buf, Vh};
 }
 
 // Buffers of one batched configuration (inner precision x compression), for
@@ -44,7 +44,7 @@ template <> inline SpinorF64 BatchSlot::spinor<SpinorF64>(void* buf) const { ret
 template <> inline SpinorF32 BatchSlot::spinor<SpinorF32>(void* buf) const { return SpinorF32{(float2*)buf, Vh}; }
 template <> inline SpinorF16 BatchSlot::spinor<SpinorF16>(void* buf) const
 {
-    return SpinorF16{(__half2*)buf, (float*)((__half2*)buf + (size_t)3 * Vh), Vh};
+    return SpinorF16{(uint4*)buf, Vh};
 }
 
 // Buffers of the multi-shift Krylov phase (inner precision): p_i and x_i of
