@@ -295,6 +295,14 @@ int stag_fermion_action(stag_ctx ctx, const double *phi_even, double mass, const
  * scale.  Double-precision arithmetic, 18-real links.  Asynchronous. */
 int stag_fermion_force(stag_ctx ctx, double *P, double *G, const double *X_even, double *phi_grad, double scale);
 
+/* Sum of forces sum_i coeffs[i] F(X_i) for n solutions X (device multi field
+ * [n][V/2][3]), coeffs a host array of n reals: the force of a rational
+ * approximation S = sum_i r_i phi^dagger (M + sigma_i)^{-1} phi with X_i the
+ * multi-shift solutions (the shift changes M's diagonal only, so each term
+ * has the single-solution form of stag_fermion_force).  P, G as in
+ * stag_fermion_force (overwritten).  n in [1, STAG_MAX_RHS].  Asynchronous. */
+int stag_fermion_force_multi(stag_ctx ctx, double *P, double *G, const double *X, const double *coeffs, int n);
+
 /* Right-hand sides per operator pass used by the last batched solve of this
  * context (the autotuner's choice when rhs_block was 0). */
 int stag_last_rhs_block(stag_ctx ctx);

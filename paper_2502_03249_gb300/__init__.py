@@ -97,6 +97,7 @@ def _declare(lib):
         "stag_fermion_action": ([P, P, D, ctypes.POINTER(SolverParams), P, ctypes.POINTER(D),
                                  ctypes.POINTER(SolverStats)], I),
         "stag_fermion_force": ([P, P, P, P, P, D], I),
+        "stag_fermion_force_multi": ([P, P, P, P, P, I], I),
         "stag_solve_full": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_strerror": ([I], ctypes.c_char_p),
         "stag_last_error": ([], ctypes.c_char_p),
@@ -337,6 +338,21 @@ class Context:
                                             None if phi_grad is None else self._field(phi_grad, "phi_grad"),
                                             float(scale)))
         return P, G, phi_grad
+
+    def fermion_force_multi(self, X, coeffs, P=None, G=None):
+        """stag_fermion_force_multi: P, G = sum_i coeffs[i] * force(X[i])."""
+        torch = _torch()
+        n = int(X.shape[0])
+        c = (ctypes.c_double * n)(*[float(v) for v in coeffs])
+        for t, name in ((P, "P"), (G, "G")):
+            if t is not None and (t.dtype != torch.complex128 or not t.is_cuda or
+                                  tuple(t.shape) != (self.V, 4, 3, 3) or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor of shape (V, 4, 3, 3)")
+        self._sync_stream()
+        _check(self._lib.stag_fermion_force_multi(
+            self._h, None if P is None else ctypes.c_void_p(P.data_ptr()),
+            None if G is None else ctypes.c_void_p(G.data_ptr()), self._field(X, "X", n), c, n))
+        return P, G
 
     def last_rhs_block(self):
         """stag_last_rhs_block: rhs block of the last batched solve."""

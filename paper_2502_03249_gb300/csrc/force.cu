@@ -26,7 +26,7 @@ constexpr int F_BS = 128;
 // writes its link's 144 contiguous bytes of P and G.
 template <class LF>
 __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, const double2* Y, double2* P,
-                                                double2* G, double scale)
+                                                double2* G, double scale, int accumulate)
 {
     const long long idx = (long long)blockIdx.x * F_BS + threadIdx.x;
     if (idx >= 8LL * g.Vh) return;
@@ -66,7 +66,13 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
                 // s u_a conj(v_b)
                 const double re = u[a].re * v[b].re + u[a].im * v[b].im;
                 const double im = u[a].im * v[b].re - u[a].re * v[b].im;
-                Gp[a * 3 + b] = make_double2(sg * re, sg * im);
+                double2 o = make_double2(sg * re, sg * im);
+                if (accumulate) {
+                    const double2 q = Gp[a * 3 + b];
+                    o.x += q.x;
+                    o.y += q.y;
+                }
+                Gp[a * 3 + b] = o;
             }
     }
     if (P) {
@@ -103,6 +109,11 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
                 double re = 0.5 * (W[a * 3 + b].re - W[b * 3 + a].re);
                 double im = 0.5 * (W[a * 3 + b].im + W[b * 3 + a].im);
                 if (a == b) im -= trim;
+                if (accumulate) {
+                    const double2 q = Pp[a * 3 + b];
+                    re += q.x;
+                    im += q.y;
+                }
                 Pp[a * 3 + b] = make_double2(re, im);
             }
     }
@@ -153,7 +164,8 @@ int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mas
 int check_ctx(stag_ctx ctx);
 int check_half_field(const void* p, const char* what);
 
-int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2* phi_grad, double scale)
+int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2* phi_grad, double scale,
+                 int accumulate = 0)
 {
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
@@ -163,7 +175,7 @@ int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2
     STAG_TRY(launch_dslash(ctx, STAG_F64, 18, 1, ctx->tmp_odd, X, ctx->stream));
     const long long n = 8LL * g.Vh;
     k_force<LinkField<double2, 18>><<<(unsigned)((n + F_BS - 1) / F_BS), F_BS, 0, ctx->stream>>>(
-        g, U, X, ctx->tmp_odd, P, G, scale);
+        g, U, X, ctx->tmp_odd, P, G, scale, accumulate);
     if (phi_grad) {
         const long long m = 3LL * g.Vh;
         k_scale_copy<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(m, X, phi_grad, 2.0 * scale);
@@ -199,6 +211,31 @@ int stag_fermion_force(stag_ctx ctx, double* P, double* G, const double* X_even,
         return STAG_ENOGAUGE;
     }
     return force_from_X(ctx, (double2*)P, (double2*)G, (const double2*)X_even, (double2*)phi_grad, scale);
+}
+
+int stag_fermion_force_multi(stag_ctx ctx, double* P, double* G, const double* X, const double* coeffs, int n)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(X, "X"));
+    if (!P && !G) {
+        set_error("at least one of P, G must be given");
+        return STAG_EINVAL;
+    }
+    if (P) STAG_TRY(check_half_field(P, "P"));
+    if (G) STAG_TRY(check_half_field(G, "G"));
+    if (!coeffs || n < 1 || n > STAG_MAX_RHS) {
+        set_error("coeffs must be a host array of 1..%d values", STAG_MAX_RHS);
+        return STAG_EINVAL;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    const size_t stride = (size_t)3 * ctx->g.Vh;
+    for (int i = 0; i < n; ++i)
+        STAG_TRY(force_from_X(ctx, (double2*)P, (double2*)G, (const double2*)X + i * stride, nullptr, coeffs[i],
+                              i > 0));
+    return STAG_OK;
 }
 
 int stag_fermion_action(stag_ctx ctx, const double* phi_even, double mass, const stag_solver_params* params,

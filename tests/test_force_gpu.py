@@ -178,3 +178,46 @@ def test_reupload_keeps_cached_solver_graphs_valid(stag):
         assert all(s["status"] == 0 for s in st)
         assert orc.true_residual(dims, U, mass, host(X[1]), 2 * b) <= 1e-10
     torch.cuda.synchronize()
+
+
+def test_rational_force_is_weighted_sum(stag):
+    """sum_i r_i F(X_i) with X_i from the multi-shift solver equals the oracle's
+    weighted sum of single forces; and the rational action's derivative, checked
+    against central finite differences of S = sum_i r_i phi^dagger (M+s_i)^-1 phi."""
+    import torch
+    dims, mass = (4, 4, 4, 4), 0.2
+    shifts = [0.01, 0.1, 1.0]
+    coeffs = [0.5, 0.3, 0.2]
+    U = li.random_links(dims, "haar", seed=851)
+    phi = li.gaussian_half(dims, seed=852)
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(dev(U))
+    X = ctx.new_half(3)
+    ctx.cg_solve_multishift(X, dev(phi), shifts, mass, tol=1e-12, inner_prec=0)
+    P = torch.empty((ctx.V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    G = torch.empty_like(P)
+    ctx.fermion_force_multi(X, coeffs, P=P, G=G)
+    Xh = host(X)
+    Pref = sum(c * orc.force(dims, U, Xh[i])[0] for i, c in enumerate(coeffs))
+    Gref = sum(c * orc.force(dims, U, Xh[i])[1] for i, c in enumerate(coeffs))
+    assert np.linalg.norm(host(P) - Pref) <= 1e-12 * np.linalg.norm(Pref)
+    assert np.linalg.norm(host(G) - Gref) <= 1e-12 * np.linalg.norm(Gref)
+    # finite differences of the rational action on the group (oracle solves)
+    def S_of(Ux):
+        tot = 0.0
+        for c, s in zip(coeffs, shifts):
+            Xs = orc.multishift_cg(dims, Ux, mass, [s], phi, tol=1e-14)[0][0]
+            tot += c * orc.action(dims, phi, Xs)
+        return tot
+    rng = np.random.default_rng(853)
+    h = 1e-5
+    Ph = host(P)
+    for _ in range(4):
+        i, mu, a = int(rng.integers(ctx.V)), int(rng.integers(4)), int(rng.integers(8))
+        T = GELL_MANN[a] / 2
+        Up, Um = U.copy(), U.copy()
+        Up[i, mu] = expm_herm(h * T) @ U[i, mu]
+        Um[i, mu] = expm_herm(-h * T) @ U[i, mu]
+        fd = (S_of(Up) - S_of(Um)) / (2 * h)
+        an = np.trace(1j * T @ Ph[i, mu]).real
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.abs(Ph).max())
