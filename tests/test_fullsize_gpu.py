@@ -1,0 +1,74 @@
+"""Parity at the largest workload size, 64^3 x 16 (V/2 = 2,097,152), in the
+launch configuration the benchmark uses: inputs from the device generator,
+copied to the host and handed to the oracle.
+
+* force given X (a Gaussian field; the force is a pure function of U and X):
+  every link's P and G against the oracle, 1e-12 relative;
+* Dslash in double-float and IEEE double on every output element (1e-12) and
+  in float/half on sampled sites against the oracle on the stored values.
+"""
+
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+import oracle as orc
+from oracle import encodings as enc
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (64, 64, 64, 16)
+
+
+@pytest.fixture(scope="module")
+def big(stag):
+    import torch
+    U = li.random_links_torch(DIMS, "smooth", 0.3, seed=li.workload_seed(5, 0))
+    ctx = stag.Context(DIMS)
+    ctx.upload_gauge(U)
+    Uh = U.cpu().numpy()
+    return ctx, U, Uh
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_force_64c16_every_link(stag, big):
+    import torch
+    ctx, U, Uh = big
+    X = li.gaussian_half_torch(DIMS, seed=li.workload_seed(5, 1))
+    P = torch.empty_like(U)
+    G = torch.empty_like(U)
+    ctx.fermion_force(X, P=P, G=G)
+    Po, Go = orc.force(DIMS, Uh, X.cpu().numpy())
+    assert rel(P.cpu().numpy(), Po) <= 1e-12
+    assert rel(G.cpu().numpy(), Go) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [3, 0])
+def test_dslash_64c16_double(stag, big, prec):
+    ctx, U, Uh = big
+    psi = li.gaussian_half_torch(DIMS, seed=77)
+    out = ctx.new_half()
+    ctx.dslash_oe(out, psi, prec, 18)
+    ref = orc.dslash_oe(DIMS, Uh, psi.cpu().numpy())
+    assert rel(out.cpu().numpy(), ref) <= 1e-12
+
+
+def test_dslash_64c16_float_half_sampled(stag, big):
+    """Float / half operators on the stored values: compare 4096 sampled sites
+    (the oracle's half operator is evaluated on the whole field, the sample
+    keeps the comparison cheap) with the bounds of the smaller lattices."""
+    ctx, U, Uh = big
+    psi = li.gaussian_half_torch(DIMS, seed=78)
+    ph = psi.cpu().numpy()
+    rng = np.random.default_rng(79)
+    idx = rng.choice(ctx.Vh, 4096, replace=False)
+    out = ctx.new_half()
+    ctx.dslash_eo(out, psi, 1, 12)
+    ref32 = orc.dslash_eo(DIMS, enc.recon12(Uh, enc.round_f32), enc.round_f32(ph))
+    assert rel(out.cpu().numpy()[idx], ref32[idx]) <= 1e-5
+    ctx.dslash_eo(out, psi, 2, 12)
+    ref16 = orc.dslash_eo(DIMS, enc.recon12(Uh, enc.round_f16), enc.half_spinor(ph))
+    assert rel(out.cpu().numpy()[idx], ref16[idx]) <= 1e-3
