@@ -29,6 +29,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -225,6 +226,39 @@ def cpu_baseline_sample(dims, U, b, mass, Vh, budget_s=12.0):
 
 # ---------------------------------------------------------------- helpers
 
+CG_GRAPH_UNROLL = 4     # CG iterations per body of the solver graph's while loop
+CG_CHECK_EVERY = 25     # host-driven loop: iterations between convergence reads
+
+
+def cg_kernel_launches(st, use_graph):
+    """Kernels one double-precision CG solve launches: the start kernel, four
+    per iteration slot (whole graph bodies, or whole host-loop batches), the
+    two true-residual kernels per pass and one restart kernel per restart.
+    Exact when the solve needed no restart (each pass's iterations are not
+    reported separately)."""
+    per = CG_GRAPH_UNROLL if use_graph else CG_CHECK_EVERY
+    passes = st["restarts"] + 1
+    slots = per * max(passes, math.ceil(max(st["iters"], 1) / per))
+    return 1 + 4 * slots + 2 * passes + st["restarts"]
+
+
+class L2Flush:
+    """Evict L2 before a timed call: write a buffer larger than L2, then read a
+    second one, so that L2 holds clean lines of the second buffer.  (Without the
+    read, the timed kernel would pay for writing back up to 129 MB of dirty
+    lines left by the write, which no kernel of the path produced.)"""
+
+    def __init__(self, torch, dev):
+        self.torch = torch
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.o = torch.zeros((), dtype=torch.float32, device=dev)
+
+    def __call__(self, v=1.0):
+        self.w.fill_(v)
+        self.torch.sum(self.r, 0, out=self.o)
+
+
 class Timer:
     """CUDA-event timing of a callable on the current stream, L2 flushed before each call."""
 
@@ -239,7 +273,7 @@ class Timer:
         out, ts = None, []
         stream = torch.cuda.current_stream()
         for _ in range(reps):
-            self.flush.fill_(1.0)
+            self.flush(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -266,17 +300,28 @@ def profile_kernel(args, stag, torch):
     name = args.profile_kernel
     kern, _, dtxt = name.partition("@")
     parts = kern.split("_")
-    prec = {"f64": stag.F64, "f32": stag.F32, "f16": stag.F16, "f64x": stag.F64X}[parts[1]]
-    recon = int(parts[2])
     w = li.WORKLOADS[WORKLOAD_INDEX]
     dims = tuple(int(v) for v in dtxt.split("x")) if dtxt else w["dims"]
     U = li.random_links(dims, "smooth", eps=w["eps"], seed=li.workload_seed(WORKLOAD_INDEX, 0))
     ctx = stag.Context(dims)
     ctx.upload_gauge(torch.from_numpy(U).cuda())
+    if parts[0] == "cg":
+        # whole solves, host-driven (ncu does not see the kernels of graphs with conditional nodes)
+        arith = {"f64": F64_IEEE, "f64x": F64X}[parts[1]]
+        b = torch.from_numpy(li.gaussian_half(dims, seed=li.workload_seed(WORKLOAD_INDEX, 1))).cuda()
+        x = ctx.new_half()
+        for _ in range(args.warmup + args.steps):
+            ctx.cg_solve(x, b, w["mass"], tol=TOL, use_graph=0, f64_arith=arith)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_kernel": name, "workload": w["name"], "solves": args.warmup + args.steps}))
+        return 0
+    prec = {"f64": stag.F64, "f32": stag.F32, "f16": stag.F16, "f64x": stag.F64X}[parts[1]]
+    recon = int(parts[2])
     psi = torch.from_numpy(li.gaussian_half(dims, seed=99)).cuda()
-    out = ctx.new_half()
+    # the bare kernel on the precision's internal storage, as the benchmark times it
+    ctx.dslash_prepare(psi, prec)
     for _ in range(args.warmup + args.steps):
-        ctx.dslash_eo(out, psi, prec, recon)
+        ctx.dslash_repeat(prec, recon, 1)
     torch.cuda.synchronize()
     print(json.dumps({"profile_kernel": name, "workload": w["name"], "launches": args.warmup + args.steps}))
     return 0
@@ -405,7 +450,8 @@ def main():
                     help="arithmetic of the headline solve's operator passes (0 IEEE double, 3 double-float)")
     ap.add_argument("--profile-kernel", default=None,
                     help="only run a few launches of one operator on the workload (for ncu): "
-                         "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ...; optional @LXxLYxLZxLT")
+                         "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., or whole host-driven "
+                         "solves cg_f64 / cg_f64x; optional @LXxLYxLZxLT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -432,7 +478,7 @@ def main():
     ctx.upload_gauge(torch.from_numpy(U).to(dev))
     b = torch.from_numpy(b_np).to(dev)
     x = ctx.new_half()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
     stream = torch.cuda.current_stream()
     timer = Timer(torch, flush)
     peaks, peak_kind = load_peaks()
@@ -453,7 +499,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
-            flush.fill_(1.0)
+            flush(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -468,7 +514,7 @@ def main():
     ms_per_step = t_sum / args.steps
     half_per_step = statistics.mean(half_dslash(s) for s in stats)
     value = weak_scaling_value(ws, Vh, half_per_step, ms_per_step)
-    launches = sum(1 + 4 * s["iters"] + 2 * (s["restarts"] + 1) + s["restarts"] for s in stats)
+    launches = sum(cg_kernel_launches(s, ug) for s in stats)
     clocks = clk.summary()
 
     # ---- the same solve with IEEE-double operator passes
@@ -480,10 +526,11 @@ def main():
     kern = {"f64x_18": dslash_kernel_entry(timer, ctx, psi, out, F64X, 18, Vh, hbm),
             "f64_18": dslash_kernel_entry(timer, ctx, psi, out, F64_IEEE, 18, Vh, hbm)}
     main_k = kern["f64x_18" if arith == F64X else "f64_18"]
-    traffic = load_traffic().get("dslash_f64x_18_32c8" if arith == F64X else "dslash_f64_18_32c8")
+    traffic = load_traffic().get("dslash_f64x_df_18_32c8" if arith == F64X else "dslash_f64_18_32c8")
     fp64_peak = fp64_peak_gflops()
     if arith == F64X:
-        roofline = {"kernel": "k_dslash<LinkFieldDF<18>, SpinorF64asDF> (stag_dslash_eo, STAG_F64X)",
+        roofline = {"kernel": "k_dslash<LinkFieldDF<18>, SpinorDF, SpinorDF> (the solver's double-float operator "
+                              "on its double-float vectors; stag_dslash_repeat, STAG_F64X)",
                     "bound": "hbm", "achieved": main_k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                     "frac": main_k["achieved_gbs"] / hbm, "traffic": traffic,
                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind} copy bandwidth)",
@@ -503,7 +550,7 @@ def main():
     bd = torch.empty_like(xd)
     e2e_t, e2e_half = [], []
     for _ in range(max(3, args.steps // 4)):
-        flush.fill_(3.0)
+        flush(3.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         bd.copy_(b_host, non_blocking=True)
@@ -561,7 +608,7 @@ def main():
             "workload": w["name"] + ", double-precision CG to true residual 1e-10 (one solve per step)",
             "dims": list(dims), "mass": mass, "links": "exp(0.3 i H), 18-real double", "tol": TOL,
             "f64_arith": "double-float (STAG_F64X)" if arith == F64X else "IEEE double (STAG_F64)",
-            "l2": "flushed (512 MB write) before every step; working set 151 MB links + 6 MB per vector",
+            "l2": "flushed (512 MB write, then 512 MB read) before every step; working set 151 MB links + 6 MB per vector",
             "value_definition": "570 flop x V/2 x half-Dslash applications per solve / solve time",
         },
         "cg": {"time_to_solution_ms": ms_per_step, "iters": last["iters"], "restarts": last["restarts"],

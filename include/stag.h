@@ -119,13 +119,19 @@ int stag_dslash_eo(stag_ctx ctx, double *out_even, const double *in_odd, int pre
 int stag_dslash_oe(stag_ctx ctx, double *out_odd, const double *in_even, int prec, int recon);
 
 /* Measurement support: stag_dslash_prepare converts one canonical half field
- * (device) into the internal storage of prec (once); stag_dslash_repeat then
- * applies D_eo to it nrep times into a context-owned output with no
- * conversions, so that a caller's CUDA events on the context's stream around
- * it time the bare operator kernel.  Asynchronous.  Errors: STAG_EINVAL
- * (repeat before prepare, other precision), STAG_ENOGAUGE, STAG_EUNSUPPORTED. */
+ * (device) into the internal storage of prec (once): complex128 for STAG_F64,
+ * double-float pairs for STAG_F64X (the storage of the double-float solver's
+ * vectors), the float / half codes for STAG_F32 / STAG_F16.
+ * stag_dslash_repeat then applies D_eo (Sec. 4.2, Eq. (staggered)) to it nrep
+ * times into a context-owned output with no conversions, so that a caller's
+ * CUDA events on the context's stream around it time the bare operator
+ * kernel.  stag_dslash_result converts that output back into the canonical
+ * device half field out (complex128 [V/2][3]).  Asynchronous.  Errors:
+ * STAG_EINVAL (repeat before prepare, other precision, result before repeat,
+ * bad pointer), STAG_ENOGAUGE, STAG_EUNSUPPORTED. */
 int stag_dslash_prepare(stag_ctx ctx, const double *in, int prec);
 int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep);
+int stag_dslash_result(stag_ctx ctx, double *out);
 
 /* Multi-vector operator (Sec. 4.3, NMULTI): out_k = D_{p,1-p} in_k for
  * k = 0..nrhs-1, with each link loaded once per site for a block of

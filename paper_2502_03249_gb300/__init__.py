@@ -86,6 +86,7 @@ def _declare(lib):
         "stag_apply_M": ([P, P, P, D], I),
         "stag_dslash_prepare": ([P, P, I], I),
         "stag_dslash_repeat": ([P, I, I, I], I),
+        "stag_dslash_result": ([P, P], I),
         "stag_solver_params_default": ([ctypes.POINTER(SolverParams)], None),
         "stag_cg_solve": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_cg_solve_mixed": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
@@ -225,6 +226,12 @@ class Context:
         """stag_dslash_repeat: nrep bare operator launches on the prepared internal field."""
         self._sync_stream()
         _check(self._lib.stag_dslash_repeat(self._h, int(prec), int(recon), int(nrep)))
+
+    def dslash_result(self, out):
+        """stag_dslash_result: the last repeat's output, converted to canonical complex128."""
+        self._sync_stream()
+        _check(self._lib.stag_dslash_result(self._h, self._field(out, "out")))
+        return out
 
     def apply_M(self, out, inp, mass):
         """stag_apply_M: out = (m^2 - D_eo D_oe) inp on even sites."""

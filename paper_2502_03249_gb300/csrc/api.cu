@@ -253,11 +253,29 @@ int stag_dslash_prepare(stag_ctx ctx, const double* in, int prec)
     }
     const size_t bytes = lo_spinor_bytes(ctx->g, prec);
     STAG_TRY(ensure_lo_tmp(ctx, bytes));
-    if (prec == STAG_F64 || prec == STAG_F64X)
+    if (prec == STAG_F64)
         STAG_CUDA_TRY(cudaMemcpyAsync(ctx->tmp_lo_in, in, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     else
         STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, 1, ctx->stream));
     ctx->prepared_prec = prec;
+    ctx->repeat_done = 0;
+    return STAG_OK;
+}
+
+int stag_dslash_result(stag_ctx ctx, double* out)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(out, "out"));
+    if (!ctx->repeat_done) {
+        set_error("no stag_dslash_repeat since the last stag_dslash_prepare");
+        return STAG_EINVAL;
+    }
+    const int prec = ctx->prepared_prec;
+    if (prec == STAG_F64)
+        STAG_CUDA_TRY(cudaMemcpyAsync(out, ctx->tmp_lo_out, lo_spinor_bytes(ctx->g, prec), cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    else
+        STAG_TRY(convert_lo_to_f64(ctx, prec, ctx->tmp_lo_out, (double2*)out, 1, ctx->stream));
     return STAG_OK;
 }
 
@@ -277,7 +295,8 @@ int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep)
         return STAG_ENOGAUGE;
     }
     for (int k = 0; k < nrep; ++k)
-        STAG_TRY(launch_dslash(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream));
+        STAG_TRY(launch_dslash_internal(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream));
+    ctx->repeat_done = 1;
     return STAG_OK;
 }
 

@@ -5,8 +5,7 @@
 #include <chrono>
 #include <new>
 
-#include "cg_kernels.cuh"
-#include "df64.cuh"
+#include "cg_df.cuh"
 #include "workspace.h"
 
 namespace stag {
@@ -14,6 +13,11 @@ namespace stag {
 constexpr int HOP_BS = 128;
 constexpr int BLAS_BS = 256;
 constexpr int MAX_RESTARTS = 100;
+// CG iterations per body of the graph's while loop: the conditional node costs
+// a few microseconds per body execution, so the body holds several iterations
+// (each kernel returns at once after the update kernel has set done, so at
+// most GRAPH_UNROLL - 1 empty iterations run after convergence).
+constexpr int GRAPH_UNROLL = 4;
 
 typedef LinkField<double2, 18> LF64;
 
@@ -109,100 +113,171 @@ int ensure_cg_f64(stag_ctx ctx)
     return STAG_OK;
 }
 
-// One double-precision CG plan per operator arithmetic: LF / SD are the link
-// field and the spinor view the operator passes use (IEEE double: LinkField +
-// SpinorF64; double-float: LinkFieldDF + SpinorF64asDF over the same double
-// vectors).  The BLAS kernels always work on the double vectors.
-template <class LF, class SD>
+// Two double-precision CG plans share the driver below:
+//   F64Plan   IEEE double (STAG_F64): double vectors, double links, FP64 BLAS;
+//   DFPlan    double-float (STAG_F64X): the Krylov vectors as double-floats
+//             (SpinorDF over the same buffers), double-float links, every
+//             per-site operation on the FP32 pipe (cg_df.cuh).
+// Each provides start / enqueue_iter / true_residual / restart / finish.
 struct F64Plan {
+    typedef LF64 LF;
+    static constexpr int slot = 0;
+    static int start(stag_ctx ctx, const double2* b_in, double mass, double sigma, double tol, int maxiter)
+    {
+        Workspace* ws = ctx->ws;
+        const int Vh = ctx->g.Vh;
+        STAG_CUDA_TRY(cudaMemcpyAsync(ws->b, b_in, (size_t)3 * Vh * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+        k_cg_start_f64<BLAS_BS><<<nblk(Vh, BLAS_BS), BLAS_BS, 0, ctx->stream>>>(
+            Vh, ws->b, ws->x, ws->r, ws->p, ws->sc, tol, maxiter, mass * mass, sigma, ctx->partials, ctx->counters);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
     // one CG iteration (four kernels) on stream s
     static int enqueue_iter(stag_ctx ctx, const LF& U, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
     {
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
         const int gh = nblk(g.Vh, HOP_BS), gb = nblk(g.Vh, BLAS_BS);
-        SpinorF64 p{ws->p}, Ap{ws->Ap}, x{ws->x}, r{ws->r};
-        k_hop_guarded<LF, SD, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, SD{ws->p}, SD{ws->t}, ws->sc);
-        k_Mp_dot<LF, SD, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, SD{ws->t}, p, Ap, ws->sc, ctx->partials,
-                                                                  ctx->counters);
+        SpinorF64 p{ws->p}, Ap{ws->Ap}, x{ws->x}, r{ws->r}, t{ws->t};
+        k_hop_guarded<LF, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, p, t, ws->sc);
+        k_Mp_dot<LF, SpinorF64, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, t, p, Ap, ws->sc, ctx->partials,
+                                                                         ctx->counters);
         k_cg_update<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, x, r, p, Ap, ws->sc, ctx->partials,
                                                               ctx->counters, cond, use_cond);
         k_cg_p<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, r, p, ws->sc);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
-
-    // the graph  while (cond) { one CG iteration }, built once per context
-    static int ensure_graph(stag_ctx ctx, const LF& U, int slot)
-    {
-        Workspace* ws = ctx->ws;
-        if (ws->f64_exec[slot]) return STAG_OK;
-        cudaGraph_t graph = nullptr;
-        STAG_CUDA_TRY(cudaGraphCreate(&graph, 0));
-        cudaGraphConditionalHandle cond;
-        STAG_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = cond;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node;
-        STAG_CUDA_TRY(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        STAG_CUDA_TRY(cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
-                                                    cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_iter(ctx, U, ctx->cap_stream, cond, 1);
-        cudaGraph_t captured = nullptr;
-        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &captured);
-        if (rc != STAG_OK || e != cudaSuccess) {
-            cudaGraphDestroy(graph);
-            set_error("capturing the CG body failed: %s", cudaGetErrorString(e));
-            return rc != STAG_OK ? rc : STAG_ECUDA;
-        }
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e != cudaSuccess) {
-            cudaGraphDestroy(graph);
-            set_error("instantiating the CG graph failed: %s", cudaGetErrorString(e));
-            return STAG_ECUDA;
-        }
-        ws->f64_graph[slot] = graph;
-        ws->f64_exec[slot] = exec;
-        return STAG_OK;
-    }
-
-    // run the iteration until the device says done: one graph launch, or a
-    // host loop that reads the done flag every check_every iterations
-    static int run_loop(stag_ctx ctx, const LF& U, const stag_solver_params& prm, int slot)
-    {
-        Workspace* ws = ctx->ws;
-        if (prm.use_graph) {
-            STAG_TRY(ensure_graph(ctx, U, slot));
-            STAG_CUDA_TRY(cudaGraphLaunch(ws->f64_exec[slot], ctx->stream));
-            return STAG_OK;
-        }
-        const int every = prm.check_every > 0 ? prm.check_every : 25;
-        for (;;) {
-            for (int k = 0; k < every; ++k) STAG_TRY(enqueue_iter(ctx, U, ctx->stream, 0, 0));
-            STAG_CUDA_TRY(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
-            STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-            if (ws->sc_host->done) return STAG_OK;
-        }
-    }
-
-    // r = b - M x in double precision (operator passes in this plan's arithmetic)
+    // r = b - M x in double precision
     static int true_residual(stag_ctx ctx, const LF& U)
     {
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
-        k_hop<LF, SD, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(g, 1, U, SD{ws->x}, SD{ws->t}, nullptr,
-                                                                             0);
-        k_true_resid_f64<LF, SD, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(
+        k_hop<LF, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(g, 1, U, SpinorF64{ws->x},
+                                                                                    SpinorF64{ws->t}, nullptr, 0);
+        k_true_resid_f64<LF, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(
             g, U, ws->t, ws->x, ws->b, ws->r, ws->sc, ctx->partials, ctx->counters, 0);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
+    static int finish(stag_ctx ctx, double2* x_out)
+    {
+        STAG_CUDA_TRY(cudaMemcpyAsync(x_out, ctx->ws->x, (size_t)3 * ctx->g.Vh * sizeof(double2),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+        return STAG_OK;
+    }
 };
+
+struct DFPlan {
+    typedef LinkFieldDF<18> LF;
+    static constexpr int slot = 1;
+    static SpinorDF v(double2* p) { return SpinorDF{reinterpret_cast<float4*>(p)}; }
+    static int start(stag_ctx ctx, const double2* b_in, double mass, double sigma, double tol, int maxiter)
+    {
+        Workspace* ws = ctx->ws;
+        const int Vh = ctx->g.Vh;
+        // b stays double: the true residual is formed against it
+        STAG_CUDA_TRY(cudaMemcpyAsync(ws->b, b_in, (size_t)3 * Vh * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+        k_dfcg_start<BLAS_BS><<<nblk(Vh, BLAS_BS), BLAS_BS, 0, ctx->stream>>>(
+            Vh, ws->b, v(ws->x), v(ws->r), v(ws->p), ws->sc, tol, maxiter, mass * mass, sigma, ctx->partials,
+            ctx->counters);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+    static int enqueue_iter(stag_ctx ctx, const LF& U, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
+    {
+        Workspace* ws = ctx->ws;
+        const Geom g = ctx->g;
+        const int gh = nblk(g.Vh, HOP_BS), gb = nblk(g.Vh, BLAS_BS);
+        k_hop_guarded<LF, SpinorDF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, v(ws->p), v(ws->t), ws->sc);
+        k_dfcg_Mp_dot<LF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->p), v(ws->Ap), ws->sc, ctx->partials,
+                                                        ctx->counters);
+        k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), ws->sc,
+                                                      ctx->partials, ctx->counters, cond, use_cond);
+        k_dfcg_p<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->r), v(ws->p), ws->sc);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+    static int true_residual(stag_ctx ctx, const LF& U)
+    {
+        Workspace* ws = ctx->ws;
+        const Geom g = ctx->g;
+        k_hop<LF, SpinorDF, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(g, 1, U, v(ws->x), v(ws->t),
+                                                                                   nullptr, 0);
+        k_dfcg_true_resid<LF, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(
+            g, U, v(ws->t), v(ws->x), ws->b, v(ws->r), ws->sc, ctx->partials, ctx->counters);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
+    static int finish(stag_ctx ctx, double2* x_out)
+    {
+        return convert_lo_to_f64(ctx, STAG_F64X, ctx->ws->x, x_out, 1, ctx->stream);
+    }
+};
+
+// the graph  while (cond) { GRAPH_UNROLL CG iterations }, built once per context and plan
+template <class Plan>
+static int ensure_cg_graph(stag_ctx ctx, const typename Plan::LF& U)
+{
+    Workspace* ws = ctx->ws;
+    const int slot = Plan::slot;
+    if (ws->f64_exec[slot]) return STAG_OK;
+    cudaGraph_t graph = nullptr;
+    STAG_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    STAG_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    STAG_CUDA_TRY(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    STAG_CUDA_TRY(cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal));
+    int rc = STAG_OK;
+    for (int u = 0; u < GRAPH_UNROLL && rc == STAG_OK; ++u) rc = Plan::enqueue_iter(ctx, U, ctx->cap_stream, cond, 1);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &captured);
+    if (rc != STAG_OK || e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_error("capturing the CG body failed: %s", cudaGetErrorString(e));
+        return rc != STAG_OK ? rc : STAG_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_error("instantiating the CG graph failed: %s", cudaGetErrorString(e));
+        return STAG_ECUDA;
+    }
+    ws->f64_graph[slot] = graph;
+    ws->f64_exec[slot] = exec;
+    return STAG_OK;
+}
+
+// run the iteration until the device says done: one graph launch, or a host
+// loop that reads the done flag every check_every iterations
+template <class Plan>
+static int run_cg_loop(stag_ctx ctx, const typename Plan::LF& U, const stag_solver_params& prm)
+{
+    Workspace* ws = ctx->ws;
+    if (prm.use_graph) {
+        STAG_TRY(ensure_cg_graph<Plan>(ctx, U));
+        STAG_CUDA_TRY(cudaGraphLaunch(ws->f64_exec[Plan::slot], ctx->stream));
+        return STAG_OK;
+    }
+    const int every = prm.check_every > 0 ? prm.check_every : 25;
+    for (;;) {
+        for (int k = 0; k < every; ++k) STAG_TRY(Plan::enqueue_iter(ctx, U, ctx->stream, 0, 0));
+        STAG_CUDA_TRY(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
+        STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (ws->sc_host->done) return STAG_OK;
+    }
+}
 
 int free_graph_pair(cudaGraph_t& g, cudaGraphExec_t& e)
 {
@@ -213,25 +288,20 @@ int free_graph_pair(cudaGraph_t& g, cudaGraphExec_t& e)
     return STAG_OK;
 }
 
-template <class LF, class SD>
-static int cg_solve_plan(stag_ctx ctx, const LF& U, int slot, double2* x_out, const double2* b_in, double mass,
+template <class Plan>
+static int cg_solve_plan(stag_ctx ctx, const typename Plan::LF& U, double2* x_out, const double2* b_in, double mass,
                          double sigma, const stag_solver_params& prm, stag_solver_stats* st,
                          std::chrono::steady_clock::time_point t0)
 {
-    typedef F64Plan<LF, SD> Plan;
     Workspace* ws = ctx->ws;
     const Geom g = ctx->g;
-    const size_t bytes = (size_t)3 * g.Vh * sizeof(double2);
     const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
-    STAG_CUDA_TRY(cudaMemcpyAsync(ws->b, b_in, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-    k_cg_start_f64<BLAS_BS><<<nblk(g.Vh, BLAS_BS), BLAS_BS, 0, ctx->stream>>>(
-        g.Vh, ws->b, ws->x, ws->r, ws->p, ws->sc, prm.tol, maxiter, mass * mass, sigma, ctx->partials, ctx->counters);
-    STAG_CUDA_TRY(cudaGetLastError());
+    STAG_TRY(Plan::start(ctx, b_in, mass, sigma, prm.tol, maxiter));
     int restarts = 0;
     CgScalars* hs = ws->sc_host;
     double prev_true = INFINITY;
     for (;;) {
-        STAG_TRY(Plan::run_loop(ctx, U, prm, slot));
+        STAG_TRY(run_cg_loop<Plan>(ctx, U, prm));
         STAG_TRY(Plan::true_residual(ctx, U));
         STAG_CUDA_TRY(cudaMemcpyAsync(hs, ws->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
         STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -242,10 +312,11 @@ static int cg_solve_plan(stag_ctx ctx, const LF& U, int slot, double2* x_out, co
         if (!(hs->rr_true < 0.25 * prev_true) || restarts >= MAX_RESTARTS) break;
         prev_true = hs->rr_true;
         ++restarts;
+        // p = r (16-byte elements: double or double-float vectors alike)
         k_cg_restart_f64<BLAS_BS><<<nblk(3 * g.Vh, BLAS_BS), BLAS_BS, 0, ctx->stream>>>(g.Vh, ws->r, ws->p, ws->sc);
         STAG_CUDA_TRY(cudaGetLastError());
     }
-    STAG_CUDA_TRY(cudaMemcpyAsync(x_out, ws->x, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    STAG_TRY(Plan::finish(ctx, x_out));
     STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     int status = STAG_OK;
     if (hs->status == STAG_BREAKDOWN) status = STAG_BREAKDOWN;
@@ -271,7 +342,7 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
         const void* lk = nullptr;
         STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lk));
         const LinkFieldDF<18> U{(const float4*)lk, ctx->g.Vh};
-        return cg_solve_plan<LinkFieldDF<18>, SpinorF64asDF>(ctx, U, 1, x_out, b_in, mass, sigma, prm, st, t0);
+        return cg_solve_plan<DFPlan>(ctx, U, x_out, b_in, mass, sigma, prm, st, t0);
     }
     if (prm.f64_arith != STAG_F64) {
         set_error("f64_arith must be STAG_F64 or STAG_F64X");
@@ -280,7 +351,7 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
     const LF64 U{(const double2*)lk, ctx->g.Vh};
-    return cg_solve_plan<LF64, SpinorF64>(ctx, U, 0, x_out, b_in, mass, sigma, prm, st, t0);
+    return cg_solve_plan<F64Plan>(ctx, U, x_out, b_in, mass, sigma, prm, st, t0);
 }
 
 void free_workspace(stag_ctx ctx)

@@ -1,0 +1,213 @@
+// cg_df.cuh -- the conjugate-gradient iteration on M = m^2 - D_eo D_oe (+ sigma)
+// with the Krylov vectors x, r, p, Ap and t = D_oe p held as double-floats
+// (SpinorDF): the same four launches per iteration as cg_kernels.cuh,
+//   hop     t  = D_oe p
+//   Mp_dot  Ap = (m^2 + sigma) p - D_eo t,  pAp = Re<p,Ap>,  alpha = rr / pAp
+//   update  x += alpha p, r -= alpha Ap,    rr' = |r|^2,     beta = rr'/rr
+//   p       p  = r + beta p
+// but every per-site operation runs in double-float arithmetic on the FP32
+// pipe (GB300 executes FP64 at 1/64 of the FP32 rate).  The scalars alpha,
+// beta and the reductions' results stay double in the CgScalars record.
+#pragma once
+
+#include "cg_kernels.cuh"
+#include "df64.cuh"
+
+namespace stag {
+
+__device__ __forceinline__ void df_site_dot(DF& d, const Vec3<DF>& a, const Vec3<DF>& b)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        df_mac(d, a.c[c].re, b.c[c].re);
+        df_mac(d, a.c[c].im, b.c[c].im);
+    }
+}
+
+// Fresh start: x = 0, r = p = b (split into double-floats), rr = rr0 = |b|^2.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_dfcg_start(int Vh, const double2* b, SpinorDF x, SpinorDF r, SpinorDF p,
+                                                   CgScalars* sc, double tol, int maxiter, double m2, double sigma,
+                                                   double* part, unsigned* cnt)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    DF d(0);
+    if (h < Vh) {
+        const Vec3<DF> v = SpinorF64asDF{(double2*)b}.load(h);
+        Vec3<DF> z;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z.c[c].re = z.c[c].im = DF(0);
+        x.store(h, z);
+        r.store(h, v);
+        p.store(h, v);
+        df_site_dot(d, v, v);
+    }
+    const double bs = block_sum_df<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!arrive_last(cnt, &last)) return;
+    const double bb = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        CgScalars s = {};
+        s.rr = s.rr0 = s.rr_true = bb;
+        s.tol2 = tol * tol * bb;
+        s.maxiter = maxiter;
+        s.m2 = m2;
+        s.sigma = sigma;
+        s.done = (bb == 0.0) ? 1 : 0;
+        *sc = s;
+    }
+}
+
+// Ap = (m^2 + sigma) p - D_eo t and the block partials of Re<p, Ap>; the last
+// block sets alpha (or flags a breakdown).
+template <class LF, int BS>
+__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_dfcg_Mp_dot(Geom g, LF U, SpinorDF t, SpinorDF p,
+                                                                          SpinorDF Ap, CgScalars* sc, double* part,
+                                                                          unsigned* cnt)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    if (sc->done) return;
+    const DF m2s = split_double(sc->m2 + sc->sigma);
+    const int h = blockIdx.x * BS + threadIdx.x;
+    DF d(0);
+    if (h < g.Vh) {
+        const Vec3<DF> Dt = dslash_site(g, 0, h, U, t);
+        const Vec3<DF> pv = p.load(h);
+        Vec3<DF> a;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.c[c].re = df_fma(m2s, pv.c[c].re, df_neg(Dt.c[c].re));
+            a.c[c].im = df_fma(m2s, pv.c[c].im, df_neg(Dt.c[c].im));
+        }
+        Ap.store(h, a);
+        df_site_dot(d, pv, a);
+    }
+    const double bs = block_sum_df<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!arrive_last(cnt, &last)) return;
+    const double pAp = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        sc->pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            sc->status = STAG_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rr / pAp;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha Ap, rr' = |r|^2; the last block sets beta, the
+// convergence flag and the graph loop's condition.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_dfcg_update(int Vh, SpinorDF x, SpinorDF r, SpinorDF p, SpinorDF Ap,
+                                                    CgScalars* sc, double* part, unsigned* cnt,
+                                                    cudaGraphConditionalHandle cond, int use_cond)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    if (sc->done) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        return;
+    }
+    const DF alpha = split_double(sc->alpha), nalpha = df_neg(alpha);
+    const int h = blockIdx.x * BS + threadIdx.x;
+    DF d(0);
+    if (h < Vh) {
+        Vec3<DF> xv = x.load_rw(h), rv = r.load_rw(h);
+        const Vec3<DF> pv = p.load(h), av = Ap.load(h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xv.c[c].re = df_fma(alpha, pv.c[c].re, xv.c[c].re);
+            xv.c[c].im = df_fma(alpha, pv.c[c].im, xv.c[c].im);
+            rv.c[c].re = df_fma(nalpha, av.c[c].re, rv.c[c].re);
+            rv.c[c].im = df_fma(nalpha, av.c[c].im, rv.c[c].im);
+        }
+        x.store(h, xv);
+        r.store(h, rv);
+        df_site_dot(d, rv, rv);
+    }
+    const double bs = block_sum_df<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!arrive_last(cnt, &last)) return;
+    const double rr_new = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        sc->beta = rr_new / sc->rr;
+        sc->rr = rr_new;
+        sc->iter += 1;
+        if (!isfinite(rr_new)) {
+            sc->status = STAG_BREAKDOWN;
+            sc->done = 1;
+        } else if (rr_new <= sc->tol2 || sc->iter >= sc->maxiter) {
+            sc->done = 1;
+        }
+        if (use_cond) cudaGraphSetConditional(cond, sc->done ? 0 : 1);
+    }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_dfcg_p(int Vh, SpinorDF r, SpinorDF p, const CgScalars* sc)
+{
+    if (sc->done) return;
+    const DF beta = split_double(sc->beta);
+    const int h = blockIdx.x * BS + threadIdx.x;
+    if (h >= Vh) return;
+    const Vec3<DF> rv = r.load(h);
+    Vec3<DF> pv = p.load_rw(h);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pv.c[c].re = df_fma(beta, pv.c[c].re, rv.c[c].re);
+        pv.c[c].im = df_fma(beta, pv.c[c].im, rv.c[c].im);
+    }
+    p.store(h, pv);
+}
+
+// r = b - ((m^2 + sigma) x - D_eo t)  (t = D_oe x), rr_true = |r|^2.  The
+// operator pass runs in double-float; the epilogue (once per solve pass, not
+// per iteration) in IEEE double on x converted exactly as the solver returns
+// it, so that rr_true is the residual of the returned solution to double
+// rounding.  r is stored back as double-floats for a restart.
+template <class LF, int BS>
+__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_dfcg_true_resid(Geom g, LF U, SpinorDF t, SpinorDF x,
+                                                                              const double2* b, SpinorDF r,
+                                                                              CgScalars* sc, double* part,
+                                                                              unsigned* cnt)
+{
+    __shared__ double red[BS / 32];
+    __shared__ bool last;
+    const double m2s = sc->m2 + sc->sigma;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    double d = 0.0;
+    if (h < g.Vh) {
+        const Vec3<double> Dt = vconv<double>(dslash_site(g, 0, h, U, t));
+        const Vec3<DF> xv = x.load(h);
+        Vec3<DF> rv;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 bv = b[(size_t)h * 3 + c];
+            const double re = bv.x - fma(m2s, df_to_double(xv.c[c].re), -Dt.c[c].re);
+            const double im = bv.y - fma(m2s, df_to_double(xv.c[c].im), -Dt.c[c].im);
+            rv.c[c].re = split_double(re);
+            rv.c[c].im = split_double(im);
+            d = fma(re, re, d);
+            d = fma(im, im, d);
+        }
+        r.store(h, rv);
+    }
+    const double bs = block_sum<BS>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (!arrive_last(cnt, &last)) return;
+    const double rr = sum_partials<BS>(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *cnt = 0;
+        sc->rr_true = rr;
+    }
+}
+
+}  // namespace stag

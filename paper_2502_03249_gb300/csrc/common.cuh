@@ -447,12 +447,21 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* smem_fl
     return *smem_flag;
 }
 
-// Deterministic sum of n partials by one block (fixed order for fixed n).
+// Deterministic sum of n partials by one block (fixed order for fixed n):
+// thread j adds part[j], part[j + BS], ... in that order.  The loads are
+// issued eight at a time so that they are in flight together (the last block
+// of a reduction otherwise waits one L2 round trip per partial).
 template <int BS>
 __device__ __forceinline__ double sum_partials(const double* part, int n, double* smem)
 {
     double s = 0.0;
-    for (int k = threadIdx.x; k < n; k += BS) s += __ldcg(part + k);
+    for (int k0 = threadIdx.x; k0 < n; k0 += 8 * BS) {
+        double v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (k0 + j * BS < n) ? __ldcg(part + k0 + j * BS) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += v[j];
+    }
     return block_sum<BS>(s, smem);
 }
 

@@ -84,6 +84,7 @@ struct stag_ctx_s {
     stag::Workspace* ws;
     void* full_tmp;            // four half fields for the full-lattice solve
     int prepared_prec;         // storage of tmp_lo_in after stag_dslash_prepare (-1: none)
+    int repeat_done;           // tmp_lo_out holds a stag_dslash_repeat result of that field
     void* tune;                // autotuner cache (tune.cu)
     int last_rhs_block;        // right-hand sides per pass chosen by the last batched solve
 };
@@ -105,5 +106,7 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
 // in/out are in the internal storage of prec (F64: canonical AoS).
 int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
                   cudaStream_t s);
+int launch_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
+                           cudaStream_t s);
 
 }  // namespace stag

@@ -141,6 +141,113 @@ struct SpinorF64asDF {
     }
 };
 
+// ---------------------------------------------------- double-float vectors
+//
+// The double-float solver keeps its Krylov vectors as double-floats, so that
+// no FP64 instruction (conversion or arithmetic) runs per site inside the
+// iteration: the BLAS below and the operator's loads and stores use the FP32
+// pipe only.  Stored values are normalised (|lo| <= ulp(hi) / 2).
+
+// Knuth's error-free sum: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, e) -> normalised double-float (Dekker's fast two-sum, |e| small against s)
+__device__ __forceinline__ DF df_norm(float s, float e)
+{
+    const float h = __fadd_rn(s, e);
+    return DF(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ DF df_add(const DF& a, const DF& b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+// a x + y: the product's high part and its exact FMA error plus the cross
+// terms, summed into y with an error-free sum of the high parts.
+__device__ __forceinline__ DF df_fma(const DF& a, const DF& x, const DF& y)
+{
+    const float ph = __fmul_rn(a.hi, x.hi);
+    float pl = __fmaf_rn(a.hi, x.hi, -ph);
+    pl = __fmaf_rn(a.hi, x.lo, pl);
+    pl = __fmaf_rn(a.lo, x.hi, pl);
+    float s, e;
+    two_sum(y.hi, ph, s, e);
+    return df_norm(s, __fadd_rn(e, __fadd_rn(y.lo, pl)));
+}
+
+// Double-float vector storage: per site three float4 (re_hi, re_lo, im_hi,
+// im_lo) in the canonical site order, 48 bytes like a double spinor.
+struct SpinorDF {
+    typedef DF real;
+    float4* p;
+    __device__ __forceinline__ Vec3<DF> load(int h) const
+    {
+        Vec3<DF> v;
+        const float4* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 f = __ldg(q + c);
+            v.c[c].re = DF(f.x, f.y);
+            v.c[c].im = DF(f.z, f.w);
+        }
+        return v;
+    }
+    // for vectors this kernel also writes
+    __device__ __forceinline__ Vec3<DF> load_rw(int h) const
+    {
+        Vec3<DF> v;
+        const float4* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 f = q[c];
+            v.c[c].re = DF(f.x, f.y);
+            v.c[c].im = DF(f.z, f.w);
+        }
+        return v;
+    }
+    __device__ __forceinline__ void store(int h, const Vec3<DF>& v) const
+    {
+        float4* q = p + (size_t)h * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const DF re = df_norm(v.c[c].re.hi, v.c[c].re.lo), im = df_norm(v.c[c].im.hi, v.c[c].im.lo);
+            q[c] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+};
+
+// Block sum of one double-float per thread: warps reduce in double-float
+// through shuffles (every lane ends with the same bits, so the order is
+// fixed), warp results are combined in double.  Valid in thread 0.
+template <int BS>
+__device__ __forceinline__ double block_sum_df(DF v, double* smem)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DF w(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+        v = df_add(v, w);
+    }
+    const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) smem[wi] = df_to_double(v);
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (l < BS / 32) ? smem[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;
+}
+
 // Links split at upload: per complex element a float4 (re_hi, re_lo, im_hi,
 // im_lo), same structure-of-arrays layout and byte count as the double copy.
 template <int RECON>

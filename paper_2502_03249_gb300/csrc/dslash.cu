@@ -54,4 +54,17 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
     return STAG_EUNSUPPORTED;
 }
 
+// The operator on a precision's internal storage: as launch_dslash, except
+// that STAG_F64X reads and writes double-float vectors (the storage of the
+// double-float solver) instead of converting canonical doubles on the fly.
+int launch_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
+                           cudaStream_t s)
+{
+    if (prec != STAG_F64X) return launch_dslash(ctx, prec, recon, par_out, out, in, s);
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    return run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh}, SpinorDF{(float4*)in},
+                      SpinorDF{(float4*)out}, par_out, s);
+}
+
 }  // namespace stag

@@ -2,6 +2,7 @@
 // internal device layouts: the gauge field upload, its 12-real / float / half
 // copies (Sec. 4.3 link compression) and reduced-precision spinor codes.
 #include "ctx.h"
+#include "df64.cuh"
 
 namespace stag {
 
@@ -147,7 +148,7 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
 
 size_t lo_spinor_bytes(const Geom& g, int prec)
 {
-    // STAG_F64 and STAG_F64X both store canonical complex128
+    // STAG_F64: canonical complex128; STAG_F64X: double-float pairs, same size
     if (prec == STAG_F32) return (size_t)g.Vh * 3 * sizeof(float2);
     if (prec == STAG_F16) return (size_t)g.Vh * 16;   // three __half2 codes + float norm per site
     return (size_t)g.Vh * 3 * sizeof(double2);
@@ -181,6 +182,24 @@ __global__ void k_from_lo(int Vh, int nvec, SIn in, size_t in_stride_bytes, doub
     for (int c = 0; c < 3; ++c) q[c] = make_double2((double)f.c[c].re, (double)f.c[c].im);
 }
 
+// canonical complex128 <-> double-float storage (the double-float solver's vectors)
+__global__ void k_split_spinor(size_t n, const double2* __restrict__ in, float4* __restrict__ out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 d = in[i];
+    const DF re = split_double(d.x), im = split_double(d.y);
+    out[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+__global__ void k_df_to_double(size_t n, const float4* __restrict__ x, double2* __restrict__ out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 f = x[i];
+    out[i] = make_double2(df_to_double(DF(f.x, f.y)), df_to_double(DF(f.z, f.w)));
+}
+
 int convert_f64_to_lo(stag_ctx ctx, int prec, const double2* in, void* out, int nvec, cudaStream_t s)
 {
     const int Vh = ctx->g.Vh;
@@ -188,7 +207,10 @@ int convert_f64_to_lo(stag_ctx ctx, int prec, const double2* in, void* out, int 
     const int BS = 256;
     const unsigned grid = (unsigned)((work + BS - 1) / BS);
     const size_t stride = lo_spinor_bytes(ctx->g, prec);
-    if (prec == STAG_F32) {
+    if (prec == STAG_F64X) {
+        const size_t n = (size_t)nvec * Vh * 3;
+        k_split_spinor<<<(unsigned)((n + BS - 1) / BS), BS, 0, s>>>(n, in, (float4*)out);
+    } else if (prec == STAG_F32) {
         k_to_lo<SpinorF32><<<grid, BS, 0, s>>>(Vh, nvec, in, SpinorF32{(float2*)out, Vh}, stride);
     } else if (prec == STAG_F16) {
         k_to_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, in, SpinorF16{(uint4*)out, Vh}, stride);
@@ -207,7 +229,10 @@ int convert_lo_to_f64(stag_ctx ctx, int prec, const void* in, double2* out, int 
     const int BS = 256;
     const unsigned grid = (unsigned)((work + BS - 1) / BS);
     const size_t stride = lo_spinor_bytes(ctx->g, prec);
-    if (prec == STAG_F32) {
+    if (prec == STAG_F64X) {
+        const size_t n = (size_t)nvec * Vh * 3;
+        k_df_to_double<<<(unsigned)((n + BS - 1) / BS), BS, 0, s>>>(n, (const float4*)in, out);
+    } else if (prec == STAG_F32) {
         k_from_lo<SpinorF32><<<grid, BS, 0, s>>>(Vh, nvec, SpinorF32{(float2*)in, Vh}, stride, out);
     } else if (prec == STAG_F16) {
         k_from_lo<SpinorF16><<<grid, BS, 0, s>>>(Vh, nvec, SpinorF16{(uint4*)in, Vh}, stride, out);

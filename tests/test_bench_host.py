@@ -74,3 +74,16 @@ def test_max_over_ranks_gloo_two_ranks():
         assert p.exitcode == 0
     got = dict(q.get() for _ in range(2))
     assert got == {0: 15.0, 1: 15.0}
+
+
+def test_cg_kernel_launch_count():
+    import bench
+    # graph: iterations run in whole bodies of CG_GRAPH_UNROLL
+    st = {"iters": 80, "restarts": 0}
+    assert bench.cg_kernel_launches(st, 1) == 1 + 4 * 80 + 2
+    st = {"iters": 81, "restarts": 0}
+    assert bench.cg_kernel_launches(st, 1) == 1 + 4 * 84 + 2
+    # host loop: whole batches of CG_CHECK_EVERY
+    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 0) == 1 + 4 * 100 + 2
+    # a restart adds a pass: its residual kernels and the restart kernel
+    assert bench.cg_kernel_launches({"iters": 2, "restarts": 1}, 1) == 1 + 4 * 8 + 4 + 1

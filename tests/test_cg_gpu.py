@@ -58,7 +58,12 @@ def test_cg_4x4_workload(stag, use_graph, arith):
     assert st["status"] == 0
     res = orc.true_residual(dims, U, mass, xr, b)
     assert res <= 1e-10
-    assert abs(res - st["true_rel_residual"]) <= 1e-3 * res + 1e-16
+    # The library recomputes the residual with its own operator arithmetic:
+    # IEEE double agrees with the oracle to rounding; double-float carries the
+    # operator's error (~1e-14 relative per application, times |x|/|b| <= 1/m^2),
+    # the 1e-12 residual floor of that arithmetic at m = 0.1.
+    floor = 1e-16 if arith == 0 else 1e-12
+    assert abs(res - st["true_rel_residual"]) <= 1e-3 * res + floor
     x_cpu, it_cpu, _, _ = orc.cg(dims, U, mass, b, tol=1e-10)
     assert abs(st["iters"] - it_cpu) <= max(3, it_cpu // 20)
 

@@ -204,3 +204,33 @@ def test_errors_are_reported_not_faulted(stag):
     # the context is still usable afterwards
     ctx.dslash_eo(out, psi)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec,recon", [(0, 18), (3, 18), (1, 12), (2, 12)])
+@pytest.mark.parametrize("dims", [(10, 6, 4, 6), (32, 32, 32, 8)])
+def test_bare_kernel_path_matches_oracle(stag, dims, prec, recon):
+    """The operator kernel the benchmark times: stag_dslash_prepare (internal
+    storage of the precision: complex128, double-float pairs, float, half
+    codes), stag_dslash_repeat, read back with stag_dslash_result.  At 32^3 x 8
+    with the benchmark's own links and source."""
+    if dims == (32, 32, 32, 8):
+        U = li.random_links(dims, "smooth", eps=0.3, seed=li.workload_seed(1, 0))
+        psi = li.gaussian_half(dims, seed=99)
+    else:
+        U = li.random_links(dims, "smooth", eps=0.3, seed=291)
+        psi = li.gaussian_half(dims, seed=292)
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    with pytest.raises(stag.StagError):
+        ctx.dslash_result(out)             # nothing repeated yet
+    ctx.dslash_prepare(dev(psi), prec)
+    ctx.dslash_repeat(prec, recon, 3)      # the same input each time: the same output
+    got = host(ctx.dslash_result(out))
+    if prec in (0, 3):
+        assert rel(got, orc.dslash_eo(dims, U, psi)) <= 1e-12
+    elif prec == 1:
+        ref = orc.dslash_eo(dims, enc.recon12(U, enc.round_f32), enc.round_f32(psi))
+        assert rel(got, ref) <= 1e-5
+    else:
+        ref = orc.dslash_eo(dims, enc.recon12(U, enc.round_f16), enc.half_spinor(psi))
+        assert rel(got, ref) <= 1e-3
