@@ -305,6 +305,25 @@ def profile_kernel(args, stag, torch):
     U = li.random_links(dims, "smooth", eps=w["eps"], seed=li.workload_seed(WORKLOAD_INDEX, 0))
     ctx = stag.Context(dims)
     ctx.upload_gauge(torch.from_numpy(U).cuda())
+    if parts[0] in ("multi", "multishift"):
+        # the 32^3 x 16 batched (16 RHS) or multi-shift (12 shifts) solve, host-driven
+        w3 = li.WORKLOADS[3]
+        dims3 = tuple(int(v) for v in dtxt.split("x")) if dtxt else w3["dims"]
+        ctx = stag.Context(dims3)
+        ctx.upload_gauge(li.random_links_torch(dims3, "smooth", w3["eps"], seed=li.workload_seed(3, 0)))
+        B = li.gaussian_half_torch(dims3, seed=li.workload_seed(3, 1), nvec=16)
+        prec = {"f32": stag.F32, "f16": stag.F16}[parts[1]]
+        for _ in range(args.warmup + args.steps):
+            if parts[0] == "multi":
+                X = ctx.new_half(16)
+                ctx.cg_solve_multi(X, B, w3["mass"], tol=TOL, inner_prec=prec, inner_recon=int(parts[2]), use_graph=0)
+            else:
+                X = ctx.new_half(12)
+                ctx.cg_solve_multishift(X, B[0].contiguous(), SHIFTS12, w3["mass"], tol=TOL, inner_prec=prec,
+                                        inner_recon=int(parts[2]), use_graph=0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_kernel": name, "workload": w3["name"], "solves": args.warmup + args.steps}))
+        return 0
     if parts[0] == "cg":
         # whole solves, host-driven (ncu does not see the kernels of graphs with conditional nodes)
         arith = {"f64": F64_IEEE, "f64x": F64X}[parts[1]]
@@ -451,7 +470,7 @@ def main():
     ap.add_argument("--profile-kernel", default=None,
                     help="only run a few launches of one operator on the workload (for ncu): "
                          "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., or whole host-driven "
-                         "solves cg_f64 / cg_f64x; optional @LXxLYxLZxLT")
+                         "solves cg_f64 / cg_f64x, multi_f32_12 / multishift_f32_12 (32^3 x 16); optional @LXxLYxLZxLT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

@@ -27,15 +27,52 @@
 namespace stag {
 
 constexpr int BBS = 128;      // threads (sites) per block of every batched kernel
-constexpr int NB64 = 4;       // right-hand sides per thread of the double-precision passes
+
+// Right-hand sides per thread of the double-precision passes (reliable
+// updates): the systems reach their updates at different iterations, so a
+// pass usually works on one or two of them.  IEEE double (FP64-ALU bound)
+// shares each link load among 4; double-float uses 1 per thread, which keeps
+// its operator at 96 registers and full occupancy (4 per thread needs 128-152).
+template <class LF64> struct Nb64 { static constexpr int value = 4; };
+template <> struct Nb64<LinkFieldDF<18>> { static constexpr int value = 1; };
 
 struct BatchScal {
     CgScalars* sc;      // [nrhs]
     int nrhs;
     double* part;       // [nrhs][gx]
-    unsigned* cnt;
+    unsigned* cnt;      // one counter over all blocks (or over finished systems)
     int gx;             // blocks along the sites
+    unsigned* cnt_sys;  // [nrhs] one counter per system: blocks that wrote its partial
 };
+
+// Per-system completion of a reduction: after the block has written its
+// partials of the systems in `mine` (bit k: system k0 + k), count it in for
+// each of them.  Returns the systems this block finished last (the whole row
+// of gx blocks has written their partials), whose final sums it must form;
+// those counters are reset.  Each system is finalised by its own last block,
+// so the systems' final sums run in parallel.
+template <int NB>
+__device__ __forceinline__ unsigned arrive_last_sys(const BatchScal& bs, int k0, unsigned mine, unsigned* smem)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned last = 0;
+        if (mine) {
+            __threadfence();
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (mine & (1u << k)) {
+                    if (atomicAdd(bs.cnt_sys + k0 + k, 1u) == (unsigned)bs.gx - 1) {
+                        last |= 1u << k;
+                        bs.cnt_sys[k0 + k] = 0;
+                    }
+                }
+        }
+        *smem = last;
+    }
+    __syncthreads();
+    return *smem;
+}
 
 __device__ __forceinline__ bool active(const CgScalars& s) { return !s.done; }
 __device__ __forceinline__ bool updating(const CgScalars& s) { return !s.done && s.reliable; }
@@ -112,7 +149,8 @@ __global__ void __launch_bounds__(BBS) k_b_init(int Vh, const double2* b, const 
 
 // t_k = D_oe p_k for the systems selected by MODE (0: active, 1: updating).
 template <class LF, class S, int NB, int MODE>
-__global__ void __launch_bounds__(BBS) k_b_hop(Geom g, LF U, S in, S out, size_t stride, BatchScal bs)
+__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_hop(Geom g, LF U, S in, S out,
+                                                                               size_t stride, BatchScal bs)
 {
     const int k0 = blockIdx.y * NB;
     const unsigned mask = MODE == 0 ? mask_active<NB>(bs, k0) : mask_updating<NB>(bs, k0);
@@ -128,10 +166,11 @@ __global__ void __launch_bounds__(BBS) k_b_hop(Geom g, LF U, S in, S out, size_t
 
 // Ap_k = (m^2 + sigma_k) p_k - D_eo t_k, pAp_k, alpha_k = rr_k / pAp_k.
 template <class LF, class S, int NB>
-__global__ void __launch_bounds__(BBS) k_b_Mp_dot(Geom g, LF U, S t, S p, S Ap, size_t stride, BatchScal bs)
+__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_Mp_dot(Geom g, LF U, S t, S p, S Ap,
+                                                                                  size_t stride, BatchScal bs)
 {
-    __shared__ double red[BBS / 32];
-    __shared__ bool last;
+    __shared__ double red[(BBS / 32) * (NB > 1 ? NB : 1)];
+    __shared__ unsigned lastm;
     typedef typename S::real real;
     const int k0 = blockIdx.y * NB;
     const unsigned mask = mask_active<NB>(bs, k0);
@@ -157,15 +196,16 @@ __global__ void __launch_bounds__(BBS) k_b_Mp_dot(Geom g, LF U, S t, S p, S Ap, 
             d[k] = site_dot(pv, a);
         }
     }
+    {
+        const double s = block_sum_n<BBS, NB>(d, mask, red);
+        if (threadIdx.x < NB && (mask & (1u << threadIdx.x)))
+            bs.part[(size_t)(k0 + threadIdx.x) * bs.gx + blockIdx.x] = s;
+    }
+    const unsigned fin = arrive_last_sys<NB>(bs, k0, mask, &lastm);
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
-        if (!(mask & (1u << k))) continue;   // uniform over the block
-        const double s = block_sum<BBS>(d[k], red);
-        if (threadIdx.x == 0) bs.part[(size_t)(k0 + k) * bs.gx + blockIdx.x] = s;
-    }
-    if (!arrive_last(bs.cnt, &last)) return;
-    for (int kk = 0; kk < bs.nrhs; ++kk) {
-        if (!active(bs.sc[kk])) continue;
+        if (!(fin & (1u << k))) continue;
+        const int kk = k0 + k;
         const double pAp = sum_partials<BBS>(bs.part + (size_t)kk * bs.gx, bs.gx, red);
         if (threadIdx.x == 0) {
             CgScalars& c = bs.sc[kk];
@@ -179,7 +219,6 @@ __global__ void __launch_bounds__(BBS) k_b_Mp_dot(Geom g, LF U, S t, S p, S Ap, 
             }
         }
     }
-    if (threadIdx.x == 0) *bs.cnt = 0;
 }
 
 // x_k += alpha_k p_k, r_k -= alpha_k Ap_k, rr_k; flag reliable updates.  grid (gx, nrhs).
@@ -189,7 +228,7 @@ __global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride
                                                   cudaGraphConditionalHandle ih, int use_cond)
 {
     __shared__ double red[BBS / 32];
-    __shared__ bool last;
+    __shared__ unsigned lastm;
     typedef typename S::real real;
     const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
     const bool on = active(bs.sc[k]);
@@ -216,32 +255,41 @@ __global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride
         const double s = block_sum<BBS>(d, red);
         if (threadIdx.x == 0) bs.part[(size_t)k * bs.gx + blockIdx.x] = s;
     }
-    if (!arrive_last(bs.cnt, &last)) return;
-    int any_rel = 0, any_on = 0;
-    for (int kk = 0; kk < bs.nrhs; ++kk) {
-        if (!active(bs.sc[kk])) {
-            if (threadIdx.x == 0) bs.sc[kk].reliable = 0;
-            continue;
-        }
-        const double rr_new = sum_partials<BBS>(bs.part + (size_t)kk * bs.gx, bs.gx, red);
-        if (threadIdx.x == 0) {
-            CgScalars& c = bs.sc[kk];
-            c.rr_prev = c.rr;
-            c.beta = rr_new / c.rr;
-            c.rr = rr_new;
-            c.iter += 1;
-            if (rr_new > c.rmax2) c.rmax2 = rr_new;
-            c.reliable = !isfinite(rr_new) || rr_new < c.delta2 * c.rmax2 || rr_new <= c.tol2 || c.iter >= c.maxiter;
-            any_rel |= c.reliable;
-            any_on = 1;
+    // Which systems are active does not change during this kernel; with none
+    // active, block (0, 0) ends the graph loop.
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        int n_on = 0;
+        for (int kk = 0; kk < bs.nrhs; ++kk) n_on += active(bs.sc[kk]);
+        if (n_on == 0 && use_cond) {
+            cudaGraphSetConditional(ih, 0);
+            cudaGraphSetConditional(wh, 0);
         }
     }
-    if (threadIdx.x == 0) {
-        *bs.cnt = 0;
-        if (use_cond) {
-            cudaGraphSetConditional(ih, any_rel ? 1 : 0);
-            cudaGraphSetConditional(wh, any_on ? 1 : 0);
-        }
+    // system k finished by its last block ...
+    if (!arrive_last_sys<1>(bs, k, on ? 1u : 0u, &lastm)) return;
+    const double rr_new = sum_partials<BBS>(bs.part + (size_t)k * bs.gx, bs.gx, red);
+    if (threadIdx.x != 0) return;
+    CgScalars& c = bs.sc[k];
+    c.rr_prev = c.rr;
+    c.beta = rr_new / c.rr;
+    c.rr = rr_new;
+    c.iter += 1;
+    if (rr_new > c.rmax2) c.rmax2 = rr_new;
+    c.reliable = !isfinite(rr_new) || rr_new < c.delta2 * c.rmax2 || rr_new <= c.tol2 || c.iter >= c.maxiter;
+    // ... and the last system to finish sets the loop's conditions
+    int n_on = 0;
+    for (int kk = 0; kk < bs.nrhs; ++kk) n_on += active(bs.sc[kk]);
+    __threadfence();
+    if (atomicAdd(bs.cnt, 1u) != (unsigned)n_on - 1) return;
+    *bs.cnt = 0;
+    __threadfence();
+    // other systems' flags were written by other blocks in this kernel: read past L1
+    const volatile CgScalars* vs = bs.sc;
+    int any_rel = 0;
+    for (int kk = 0; kk < bs.nrhs; ++kk) any_rel |= !vs[kk].done && vs[kk].reliable;
+    if (use_cond) {
+        cudaGraphSetConditional(ih, any_rel ? 1 : 0);
+        cudaGraphSetConditional(wh, 1);
     }
 }
 
@@ -267,12 +315,16 @@ __global__ void __launch_bounds__(BBS) k_b_accum_x(int Vh, double2* x_hi, SX xlo
 }
 
 // r_hi_k = b_k - (m^2 + sigma_k) x_hi_k + D_eo t_k, rr_true_k (double) for updating systems.
-template <class LF, int NB>
-__global__ void __launch_bounds__(BBS) k_b_resid64(Geom g, LF U, const double2* t, const double2* x_hi,
-                                                   const double2* b, double2* r_hi, BatchScal bs)
+// The operator pass runs in LF's arithmetic (IEEE double, or double-float on
+// the same double vectors through SD), the epilogue in double.
+template <class LF, class SD, int NB>
+__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_resid64(Geom g, LF U, const double2* t,
+                                                                                        const double2* x_hi,
+                                                                                        const double2* b, double2* r_hi,
+                                                                                        BatchScal bs)
 {
-    __shared__ double red[BBS / 32];
-    __shared__ bool last;
+    __shared__ double red[(BBS / 32) * (NB > 1 ? NB : 1)];
+    __shared__ unsigned lastm;
     const int k0 = blockIdx.y * NB;
     const unsigned mask = mask_updating<NB>(bs, k0);
     const int h = blockIdx.x * BBS + threadIdx.x;
@@ -281,37 +333,37 @@ __global__ void __launch_bounds__(BBS) k_b_resid64(Geom g, LF U, const double2* 
 #pragma unroll
     for (int k = 0; k < NB; ++k) d[k] = 0.0;
     if (mask && h < g.Vh) {
-        Vec3<double> acc[NB];
-        dslash_site_multi<LF, SpinorF64, NB>(g, 0, h, U, SpinorF64{(double2*)t}, stride, k0, mask, acc);
+        Vec3<typename LF::real> acc[NB];
+        dslash_site_multi<LF, SD, NB>(g, 0, h, U, SD{(double2*)t}, stride, k0, mask, acc);
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             if (!(mask & (1u << k))) continue;
             const double m2s = bs.sc[k0 + k].m2 + bs.sc[k0 + k].sigma;
             const size_t o = ((size_t)(k0 + k) * g.Vh + h) * 3;
+            const Vec3<double> Dt = vconv<double>(acc[k]);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const double2 xv = x_hi[o + c], bv = b[o + c];
-                const double re = bv.x - fma(m2s, xv.x, -acc[k].c[c].re);
-                const double im = bv.y - fma(m2s, xv.y, -acc[k].c[c].im);
+                const double re = bv.x - fma(m2s, xv.x, -Dt.c[c].re);
+                const double im = bv.y - fma(m2s, xv.y, -Dt.c[c].im);
                 r_hi[o + c] = make_double2(re, im);
                 d[k] = fma(re, re, d[k]);
                 d[k] = fma(im, im, d[k]);
             }
         }
     }
+    {
+        const double s = block_sum_n<BBS, NB>(d, mask, red);
+        if (threadIdx.x < NB && (mask & (1u << threadIdx.x)))
+            bs.part[(size_t)(k0 + threadIdx.x) * bs.gx + blockIdx.x] = s;
+    }
+    const unsigned fin = arrive_last_sys<NB>(bs, k0, mask, &lastm);
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
-        if (!(mask & (1u << k))) continue;
-        const double s = block_sum<BBS>(d[k], red);
-        if (threadIdx.x == 0) bs.part[(size_t)(k0 + k) * bs.gx + blockIdx.x] = s;
+        if (!(fin & (1u << k))) continue;
+        const double rr = sum_partials<BBS>(bs.part + (size_t)(k0 + k) * bs.gx, bs.gx, red);
+        if (threadIdx.x == 0) bs.sc[k0 + k].rr_true = rr;
     }
-    if (!arrive_last(bs.cnt, &last)) return;
-    for (int kk = 0; kk < bs.nrhs; ++kk) {
-        if (!updating(bs.sc[kk])) continue;
-        const double rr = sum_partials<BBS>(bs.part + (size_t)kk * bs.gx, bs.gx, red);
-        if (threadIdx.x == 0) bs.sc[kk].rr_true = rr;
-    }
-    if (threadIdx.x == 0) *bs.cnt = 0;
 }
 
 // r_k = lo(r_hi_k) (and p_k = r_k at the start); then, in the last block,
@@ -388,22 +440,25 @@ __global__ void __launch_bounds__(BBS) k_b_p(int Vh, S r, S p, size_t stride, Ba
 
 typedef LinkField<double2, 18> LF64B;
 
-template <class S, class SX, class LF, int NB>
+// LF64 / SD64: link field and spinor view of the double-precision passes
+// (reliable updates): IEEE double (LinkField<double2,18>, SpinorF64) or
+// double-float on the same double vectors (LinkFieldDF<18>, SpinorF64asDF).
+template <class S, class SX, class LF, int NB, class LF64, class SD64>
 struct BatchPlan {
+    static constexpr int NB64 = Nb64<LF64>::value;
     static S spin(const BatchSlot& m, void* buf) { return m.template spinor<S>(buf); }
     static SX spinx(const BatchSlot& m, void* buf) { return m.template spinor<SX>(buf); }
 
-    static int enqueue_start(stag_ctx ctx, BatchSlot& m, const LF64B& U64, cudaStream_t s, const double2* x0,
+    static int enqueue_start(stag_ctx ctx, BatchSlot& m, const LF64& U64, cudaStream_t s, const double2* x0,
                              double tol, int maxiter, double mass, const double* shifts_dev, double delta)
     {
         const Geom g = ctx->g;
-        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
         const dim3 gb(m.gx, m.nrhs), g64(m.gx, (m.nrhs + NB64 - 1) / NB64);
         k_b_init<SX><<<gb, BBS, 0, s>>>(g.Vh, m.b, x0, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs, tol, maxiter,
                                         mass * mass, shifts_dev, delta);
-        k_b_hop<LF64B, SpinorF64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SpinorF64{m.x_hi}, SpinorF64{m.t64},
-                                                                m.f64_stride, bs);
-        k_b_resid64<LF64B, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+        k_b_hop<LF64, SD64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
+        k_b_resid64<LF64, SD64, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
         k_b_finish<S><<<gb, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 1, 0, 0);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
@@ -411,7 +466,7 @@ struct BatchPlan {
     static int enqueue_main(stag_ctx ctx, BatchSlot& m, const LF& U, cudaStream_t s, LoopGraph* lg, int use_cond)
     {
         const Geom g = ctx->g;
-        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
         const dim3 gb(m.gx, m.nrhs), gn(m.gx, (m.nrhs + NB - 1) / NB);
         k_b_hop<LF, S, NB, 0><<<gn, BBS, 0, s>>>(g, U, spin(m, m.p), spin(m, m.t), m.s_stride, bs);
         k_b_Mp_dot<LF, S, NB><<<gn, BBS, 0, s>>>(g, U, spin(m, m.t), spin(m, m.p), spin(m, m.Ap), m.s_stride, bs);
@@ -420,16 +475,15 @@ struct BatchPlan {
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
-    static int enqueue_reliable(stag_ctx ctx, BatchSlot& m, const LF64B& U64, cudaStream_t s, LoopGraph* lg,
+    static int enqueue_reliable(stag_ctx ctx, BatchSlot& m, const LF64& U64, cudaStream_t s, LoopGraph* lg,
                                 int use_cond)
     {
         const Geom g = ctx->g;
-        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
         const dim3 gb(m.gx, m.nrhs), g64(m.gx, (m.nrhs + NB64 - 1) / NB64);
         k_b_accum_x<SX><<<gb, BBS, 0, s>>>(g.Vh, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs);
-        k_b_hop<LF64B, SpinorF64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SpinorF64{m.x_hi}, SpinorF64{m.t64},
-                                                                m.f64_stride, bs);
-        k_b_resid64<LF64B, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+        k_b_hop<LF64, SD64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
+        k_b_resid64<LF64, SD64, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
         k_b_finish<S><<<gb, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 0,
                                          lg ? lg->w : 0, use_cond);
         STAG_CUDA_TRY(cudaGetLastError());
@@ -437,29 +491,30 @@ struct BatchPlan {
     }
     static int enqueue_p(stag_ctx ctx, BatchSlot& m, cudaStream_t s)
     {
-        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx};
+        const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
         k_b_p<S><<<dim3(m.gx, m.nrhs), BBS, 0, s>>>(ctx->g.Vh, spin(m, m.r), spin(m, m.p), m.s_stride, bs);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
 
     static int run(stag_ctx ctx, BatchSlot& m, const void* lk, const double2* x0, double mass,
-                   const double* shifts_dev, const stag_solver_params& prm, double delta)
+                   const double* shifts_dev, const stag_solver_params& prm, double delta, int arith)
     {
         const void* lk64 = nullptr;
-        STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk64));
+        STAG_TRY(ensure_links(ctx, arith, 18, &lk64));
         const LF U{(const typename LF::store*)lk, ctx->g.Vh};
-        const LF64B U64{(const double2*)lk64, ctx->g.Vh};
+        const LF64 U64{(const typename LF64::store*)lk64, ctx->g.Vh};
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
         STAG_TRY(enqueue_start(ctx, m, U64, ctx->stream, x0, prm.tol, maxiter, mass, shifts_dev, delta));
         if (prm.use_graph) {
-            if (!m.lg.exec || m.graph_nb != NB) {
+            if (!m.lg.exec || m.graph_nb != NB || m.graph_arith != arith) {
                 LoopGraph& lg = m.lg;
                 STAG_TRY(build_loop_graph(
                     ctx->cap_stream, lg, true, [&](cudaStream_t s) { return enqueue_main(ctx, m, U, s, &lg, 1); },
                     [&](cudaStream_t s) { return enqueue_reliable(ctx, m, U64, s, &lg, 1); },
                     [&](cudaStream_t s) { return enqueue_p(ctx, m, s); }));
                 m.graph_nb = NB;
+                m.graph_arith = arith;
             }
             STAG_CUDA_TRY(cudaGraphLaunch(m.lg.exec, ctx->stream));
         } else {
@@ -485,7 +540,8 @@ struct BatchPlan {
 
 // Multi operator pass for the autotuner and the public multi Dslash.
 template <class LF, class S, int NB>
-__global__ void __launch_bounds__(BBS) k_multi_dslash(Geom g, int p, LF U, S in, S out, size_t stride, int nrhs)
+__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_multi_dslash(Geom g, int p, LF U, S in,
+                                                                                      S out, size_t stride, int nrhs)
 {
     const int k0 = blockIdx.y * NB;
     unsigned mask = 0;
@@ -608,6 +664,8 @@ static int ensure_batch(stag_ctx ctx, int prec, int recon, int nrhs, BatchSlot**
         STAG_CUDA_TRY(cudaMalloc(&m.sc, n * sizeof(CgScalars)));
         STAG_CUDA_TRY(cudaMalloc(&m.part, n * m.gx * sizeof(double)));
         STAG_CUDA_TRY(cudaMalloc(&m.shifts, n * sizeof(double)));
+        STAG_CUDA_TRY(cudaMalloc(&m.cnt_sys, n * sizeof(unsigned)));
+        STAG_CUDA_TRY(cudaMemset(m.cnt_sys, 0, n * sizeof(unsigned)));
         m.ready = true;
     }
     if (m.nrhs != nrhs) m.lg.destroy();   // the graph bakes the batch size into its grids
@@ -616,18 +674,33 @@ static int ensure_batch(stag_ctx ctx, int prec, int recon, int nrhs, BatchSlot**
     return STAG_OK;
 }
 
+template <class S, class SX, class LF, class LF64, class SD64>
+static int run_with_nb_arith(stag_ctx ctx, BatchSlot& m, const void* lk, const double2* x0, double mass,
+                             const double* shifts_dev, const stag_solver_params& prm, double delta, int nb, int arith)
+{
+    switch (nb) {
+    case 1: return BatchPlan<S, SX, LF, 1, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
+    case 2: return BatchPlan<S, SX, LF, 2, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
+    case 4: return BatchPlan<S, SX, LF, 4, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
+    case 8: return BatchPlan<S, SX, LF, 8, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
+    case 16: return BatchPlan<S, SX, LF, 16, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
+    default: set_error("unsupported rhs block %d", nb); return STAG_EINVAL;
+    }
+}
+
+// The double-precision passes follow prm.f64_arith (IEEE double or double-float).
 template <class S, class SX, class LF>
 static int run_with_nb(stag_ctx ctx, BatchSlot& m, const void* lk, const double2* x0, double mass,
                        const double* shifts_dev, const stag_solver_params& prm, double delta, int nb)
 {
-    switch (nb) {
-    case 1: return BatchPlan<S, SX, LF, 1>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
-    case 2: return BatchPlan<S, SX, LF, 2>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
-    case 4: return BatchPlan<S, SX, LF, 4>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
-    case 8: return BatchPlan<S, SX, LF, 8>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
-    case 16: return BatchPlan<S, SX, LF, 16>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta);
-    default: set_error("unsupported rhs block %d", nb); return STAG_EINVAL;
+    if (prm.f64_arith == STAG_F64X)
+        return run_with_nb_arith<S, SX, LF, LinkFieldDF<18>, SpinorF64asDF>(ctx, m, lk, x0, mass, shifts_dev, prm,
+                                                                           delta, nb, STAG_F64X);
+    if (prm.f64_arith != STAG_F64) {
+        set_error("f64_arith must be STAG_F64 or STAG_F64X");
+        return STAG_EINVAL;
     }
+    return run_with_nb_arith<S, SX, LF, LF64B, SpinorF64>(ctx, m, lk, x0, mass, shifts_dev, prm, delta, nb, STAG_F64);
 }
 
 // X (device, [nrhs][Vh][3] complex128) = solutions of (M + shifts_k) X_k = B_k.
@@ -709,7 +782,7 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
 void BatchSlot::release()
 {
     lg.destroy();
-    void* bufs[] = {r, p, Ap, t, xlo, x_hi, r_hi, b, t64, sc, part, shifts};
+    void* bufs[] = {r, p, Ap, t, xlo, x_hi, r_hi, b, t64, sc, part, shifts, cnt_sys};
     for (void* q : bufs)
         if (q) cudaFree(q);
     *this = BatchSlot();

@@ -8,6 +8,14 @@
 
 namespace stag {
 
+// Minimum resident blocks of 128 threads for a batched operator kernel: the
+// single-RHS bound of the link field for NB = 1, else 4 (at most 128
+// registers per thread; unbounded, the compiler takes up to 222 for NB = 8
+// and runs 2 blocks per SM).
+template <class LF, int NB> struct MultiMinBlocks {
+    static constexpr int value = NB == 1 ? OpMinBlocks<LF>::value : 4;
+};
+
 // acc[k] = (D_{p,1-p} in_{k0+k})_h for the k with bit k of mask set.
 // in.at(j, stride) is field j of the multi field.
 template <class LF, class S, int NB>

@@ -447,6 +447,32 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* smem_fl
     return *smem_flag;
 }
 
+// Block sums of NB per-thread values at once (the bits of mask select them;
+// mask is uniform over the block): each warp reduces through shuffles, one
+// barrier, then thread k adds the warps' results for value k in warp order.
+// Valid in thread k < NB for value k.  smem: BS / 32 * NB doubles.
+template <int BS, int NB>
+__device__ __forceinline__ double block_sum_n(const double* v, unsigned mask, double* smem)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (!(mask & (1u << k))) continue;
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (l == 0) smem[w * NB + k] = x;
+    }
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < NB && (mask & (1u << threadIdx.x))) {
+#pragma unroll
+        for (int ww = 0; ww < BS / 32; ++ww) s += smem[ww * NB + threadIdx.x];
+    }
+    __syncthreads();
+    return s;
+}
+
 // Deterministic sum of n partials by one block (fixed order for fixed n):
 // thread j adds part[j], part[j + BS], ... in that order.  The loads are
 // issued eight at a time so that they are in flight together (the last block

@@ -33,8 +33,9 @@ struct BatchSlot {
     CgScalars* sc = nullptr;
     double* part = nullptr;
     double* shifts = nullptr;
+    unsigned* cnt_sys = nullptr;   // per-system reduction counters, zero between kernels
     size_t s_stride = 0, sx_stride = 0, f64_stride = 0;
-    int Vh = 0, cap = 0, nrhs = 0, gx = 0, prec = 0, graph_nb = 0;
+    int Vh = 0, cap = 0, nrhs = 0, gx = 0, prec = 0, graph_nb = 0, graph_arith = -1;
     bool ready = false;
     LoopGraph lg;
     template <class S> S spinor(void* buf) const;
