@@ -419,6 +419,56 @@ def section_32c16(stag, torch, timer):
     return res
 
 
+# The paper's own tables (A100, OpenCL; context, not targets)
+PAPER_TABLE2_A100 = {1: (2.244, 1.245), 2: (2.532, 1.530), 3: (2.953, 1.929), 4: (3.205, 2.199), 6: (3.090, 2.039),
+                     8: (3.006, 2.026), 10: (3.439, 1.693), 12: (3.196, 2.055), 14: (3.091, 1.562),
+                     16: (3.045, 2.122)}   # NMULTI: (FP32, FP64) TFLOP/s, 32^4
+PAPER_TABLE1_A100_GBS = 1351.0             # CG update routine, FP64, 48^4 (OpenCL; CUDA backend 1317)
+
+
+def section_paper_tables(stag, torch, timer, hbm):
+    """The paper's Table 2 (Dslash TFLOP/s against NMULTI on 32^4) and Table 1
+    (bandwidth of the double-precision CG update on 48^4), measured here on the
+    same lattices: the multi-vector operator on internal storage, one launch per
+    CUDA-event pair with L2 flushed before it; the update kernel back to back
+    on vectors 4 x 48 B/site (> L2)."""
+    res = {}
+    w6 = li.WORKLOADS[6]
+    dims = w6["dims"]
+    Vh = li.volume(dims) // 2
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(li.random_links_torch(dims, w6["links"], w6["eps"], seed=li.workload_seed(6, 0)))
+    psi = li.gaussian_half_torch(dims, seed=li.workload_seed(6, 1), nvec=16)
+    scan = {}
+    for label, prec, recon in (("f32_12", stag.F32, 12), ("f64x_18", stag.F64X, 18), ("f64_12", stag.F64, 12)):
+        row, blocks = {}, {}
+        for n in sorted(PAPER_TABLE2_A100):
+            ctx.dslash_prepare_multi(psi[:n].contiguous(), prec)
+            ctx.dslash_repeat_multi(prec, recon, 0, 1)      # the autotuner picks the vectors per link load
+            blocks[n] = ctx.last_rhs_block()
+            ms, _ = timer(lambda: ctx.dslash_repeat_multi(prec, recon, blocks[n], 1), reps=5, warm=2)
+            row[n] = FLOP_PER_SITE * Vh * n / (ms * 1e-3) * 1e-12
+        scan[label] = {"tflops_by_nmulti": row, "rhs_block": blocks, "best": max(row.values())}
+    res["nmulti_32x4"] = {"unit": "TFLOP/s (570 flop per site per vector)", "scan": scan,
+                          "paper_a100_fp32_fp64": PAPER_TABLE2_A100,
+                          "note": "n vectors per launch, each link loaded once per rhs_block of them (autotuned: "
+                                  "larger register blocks spill); paper: 12-real links with temporal gauge (6 links "
+                                  "read per site); here 8 links per site, no gauge fixing"}
+    ctx.close()
+    dims = li.WORKLOADS[7]["dims"]
+    Vh = li.volume(dims) // 2
+    ctx = stag.Context(dims)
+    upd = {}
+    for label, arith in (("f64_ieee", F64_IEEE), ("f64x", F64X)):
+        ms = ctx.cg_update_time(arith, nrep=20)
+        gbs = 288.0 * Vh / (ms * 1e-3) * 1e-9
+        upd[label] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / hbm}
+    res["cg_update_48x4"] = {"bytes_per_site": 288, "kernels": upd, "paper_a100_gbs": PAPER_TABLE1_A100_GBS,
+                             "paper_a100_frac": PAPER_TABLE1_A100_GBS / 1555.0}
+    ctx.close()
+    return res
+
+
 def section_force(stag, torch, timer, hbm):
     """64^3 x 16, eps = 0.3, m = 0.01: force kernel given X, and the autograd forward + backward."""
     w = li.WORKLOADS[5]
@@ -594,7 +644,8 @@ def main():
         ctx.close()
         for name, fn in (("w48c12", lambda: section_48c12(stag, torch, timer, hbm)),
                          ("w32c16", lambda: section_32c16(stag, torch, timer)),
-                         ("force_64c16", lambda: section_force(stag, torch, timer, hbm))):
+                         ("force_64c16", lambda: section_force(stag, torch, timer, hbm)),
+                         ("paper_tables", lambda: section_paper_tables(stag, torch, timer, hbm))):
             try:
                 sections[name] = fn()
             except Exception as e:   # a failed section is reported, not hidden

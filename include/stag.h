@@ -133,6 +133,27 @@ int stag_dslash_prepare(stag_ctx ctx, const double *in, int prec);
 int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep);
 int stag_dslash_result(stag_ctx ctx, double *out);
 
+/* The same for nrhs fields (device multi field [nrhs][V/2][3] complex128,
+ * nrhs in [1, STAG_MAX_RHS]): stag_dslash_repeat_multi applies the
+ * multi-vector operator of stag_dslash_multi (Sec. 4.3, NMULTI: each link
+ * loaded once per site for rhs_block vectors; 0 = autotuned) nrep times;
+ * stag_dslash_result then writes nrhs fields.  Any other operator call of the
+ * context that converts fields (F32 / F16 dslash, dslash_multi) discards the
+ * prepared fields (STAG_EINVAL on the next repeat or result).  Errors as above. */
+int stag_dslash_prepare_multi(stag_ctx ctx, const double *in, int nrhs, int prec);
+int stag_dslash_repeat_multi(stag_ctx ctx, int prec, int recon, int rhs_block, int nrep);
+
+/* Measurement support: times nrep back-to-back launches of the fused CG
+ * vector update (x += alpha p, r -= alpha Ap, |r|^2 with its grid reduction;
+ * the CG step the paper's Table 1 measures) of the double-precision solver
+ * (f64_arith STAG_F64: double vectors and FP64 arithmetic; STAG_F64X:
+ * double-float vectors) on the context's work vectors, which it first sets to
+ * zero, with CUDA events on the context's stream.  Algorithmic traffic: 4
+ * vectors read and 2 written, 288 bytes per even site.  Blocks; writes the
+ * mean milliseconds per launch to *ms_per_launch (host).  Errors: STAG_EINVAL,
+ * STAG_ENOMEM, STAG_ECUDA. */
+int stag_cg_update_time(stag_ctx ctx, int f64_arith, int nrep, double *ms_per_launch);
+
 /* Multi-vector operator (Sec. 4.3, NMULTI): out_k = D_{p,1-p} in_k for
  * k = 0..nrhs-1, with each link loaded once per site for a block of
  * rhs_block vectors (1, 2, 4, 8 or 16; 0 = autotuned, cached per context).
@@ -309,8 +330,9 @@ int stag_fermion_force(stag_ctx ctx, double *P, double *G, const double *X_even,
  * stag_fermion_force (overwritten).  n in [1, STAG_MAX_RHS].  Asynchronous. */
 int stag_fermion_force_multi(stag_ctx ctx, double *P, double *G, const double *X, const double *coeffs, int n);
 
-/* Right-hand sides per operator pass used by the last batched solve of this
- * context (the autotuner's choice when rhs_block was 0). */
+/* Right-hand sides per operator pass used by the last batched solve or
+ * stag_dslash_repeat_multi of this context (the autotuner's choice when
+ * rhs_block was 0). */
 int stag_last_rhs_block(stag_ctx ctx);
 
 /* ------------------------------------------------------------- utilities */

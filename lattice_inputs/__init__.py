@@ -54,6 +54,9 @@ WORKLOADS = [
     dict(name="32^3x16 smooth eps=0.3, m=0.005", dims=(32, 32, 32, 16), links="smooth", eps=0.3, mass=0.005),
     dict(name="24^3x8 smooth eps=0.3, m=0.01", dims=(24, 24, 24, 8), links="smooth", eps=0.3, mass=0.01),
     dict(name="64^3x16 smooth eps=0.3, m=0.01", dims=(64, 64, 64, 16), links="smooth", eps=0.3, mass=0.01),
+    # the lattices of the paper's Table 2 (32^4) and Table 1 (48^4)
+    dict(name="32^4 smooth eps=0.3, m=0.01", dims=(32, 32, 32, 32), links="smooth", eps=0.3, mass=0.01),
+    dict(name="48^4 smooth eps=0.3, m=0.01", dims=(48, 48, 48, 48), links="smooth", eps=0.3, mass=0.01),
 ]
 
 

@@ -87,6 +87,9 @@ def _declare(lib):
         "stag_dslash_prepare": ([P, P, I], I),
         "stag_dslash_repeat": ([P, I, I, I], I),
         "stag_dslash_result": ([P, P], I),
+        "stag_dslash_prepare_multi": ([P, P, I, I], I),
+        "stag_dslash_repeat_multi": ([P, I, I, I, I], I),
+        "stag_cg_update_time": ([P, I, I, P], I),
         "stag_solver_params_default": ([ctypes.POINTER(SolverParams)], None),
         "stag_cg_solve": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
         "stag_cg_solve_mixed": ([P, P, P, D, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)], I),
@@ -227,10 +230,30 @@ class Context:
         self._sync_stream()
         _check(self._lib.stag_dslash_repeat(self._h, int(prec), int(recon), int(nrep)))
 
-    def dslash_result(self, out):
-        """stag_dslash_result: the last repeat's output, converted to canonical complex128."""
+    def dslash_prepare_multi(self, inp, prec):
+        """stag_dslash_prepare_multi: convert the multi field inp (nrhs, V/2, 3) once into internal storage."""
         self._sync_stream()
-        _check(self._lib.stag_dslash_result(self._h, self._field(out, "out")))
+        nrhs = int(inp.shape[0])
+        _check(self._lib.stag_dslash_prepare_multi(self._h, self._field(inp, "in", nrhs), nrhs, int(prec)))
+
+    def dslash_repeat_multi(self, prec, recon, rhs_block=0, nrep=1):
+        """stag_dslash_repeat_multi: nrep multi-vector operator launches on the prepared fields."""
+        self._sync_stream()
+        _check(self._lib.stag_dslash_repeat_multi(self._h, int(prec), int(recon), int(rhs_block), int(nrep)))
+
+    def cg_update_time(self, f64_arith=F64X, nrep=10):
+        """stag_cg_update_time: mean milliseconds per launch of the fused CG vector update."""
+        self._sync_stream()
+        ms = ctypes.c_double()
+        _check(self._lib.stag_cg_update_time(self._h, int(f64_arith), int(nrep), ctypes.byref(ms)))
+        return ms.value
+
+    def dslash_result(self, out):
+        """stag_dslash_result: the last repeat's output, converted to canonical complex128
+        (out: (V/2, 3), or (nrhs, V/2, 3) after a multi prepare)."""
+        self._sync_stream()
+        n = int(out.shape[0]) if out.dim() == 3 else None
+        _check(self._lib.stag_dslash_result(self._h, self._field(out, "out", n)))
         return out
 
     def apply_M(self, out, inp, mass):

@@ -65,6 +65,7 @@ int check_half_field(const void* p, const char* what) { return check_dev_ptr(p, 
 
 static int ensure_lo_tmp(stag_ctx ctx, size_t bytes)
 {
+    ctx->prepared_prec = -1;   // every user of the scratch fields overwrites a prepared field
     if (ctx->tmp_lo_bytes >= bytes) return STAG_OK;
     if (ctx->tmp_lo_in) cudaFree(ctx->tmp_lo_in);
     if (ctx->tmp_lo_out) cudaFree(ctx->tmp_lo_out);
@@ -243,7 +244,7 @@ int stag_dslash_oe(stag_ctx ctx, double* out_odd, const double* in_even, int pre
     return dslash_entry(ctx, out_odd, in_even, prec, recon, 1);
 }
 
-int stag_dslash_prepare(stag_ctx ctx, const double* in, int prec)
+int stag_dslash_prepare_multi(stag_ctx ctx, const double* in, int nrhs, int prec)
 {
     STAG_TRY(check_ctx(ctx));
     STAG_TRY(check_half_field(in, "in"));
@@ -251,14 +252,52 @@ int stag_dslash_prepare(stag_ctx ctx, const double* in, int prec)
         set_error("unsupported prec %d", prec);
         return STAG_EUNSUPPORTED;
     }
+    if (nrhs < 1 || nrhs > STAG_MAX_RHS) {
+        set_error("nrhs must be in [1, %d]", STAG_MAX_RHS);
+        return STAG_EINVAL;
+    }
     const size_t bytes = lo_spinor_bytes(ctx->g, prec);
-    STAG_TRY(ensure_lo_tmp(ctx, bytes));
+    STAG_TRY(ensure_lo_tmp(ctx, bytes * nrhs));
     if (prec == STAG_F64)
-        STAG_CUDA_TRY(cudaMemcpyAsync(ctx->tmp_lo_in, in, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        STAG_CUDA_TRY(cudaMemcpyAsync(ctx->tmp_lo_in, in, bytes * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
     else
-        STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, 1, ctx->stream));
+        STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, nrhs, ctx->stream));
     ctx->prepared_prec = prec;
+    ctx->prepared_nrhs = nrhs;
     ctx->repeat_done = 0;
+    return STAG_OK;
+}
+
+int stag_dslash_prepare(stag_ctx ctx, const double* in, int prec)
+{
+    return stag_dslash_prepare_multi(ctx, in, 1, prec);
+}
+
+int stag_dslash_repeat_multi(stag_ctx ctx, int prec, int recon, int rhs_block, int nrep)
+{
+    STAG_TRY(check_ctx(ctx));
+    if (ctx->prepared_prec != prec || !ctx->tmp_lo_in) {
+        set_error("call stag_dslash_prepare_multi with this precision first");
+        return STAG_EINVAL;
+    }
+    if (nrep < 1 || recon != 18 && recon != 12 || (prec == STAG_F64X && recon != 18)) {
+        set_error("nrep must be >= 1 and recon 18 or 12");
+        return STAG_EINVAL;
+    }
+    if (rhs_block != 0 && rhs_block != 1 && rhs_block != 2 && rhs_block != 4 && rhs_block != 8 && rhs_block != 16) {
+        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
+        return STAG_EINVAL;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    int nb = rhs_block;
+    for (int k = 0; k < nrep; ++k)
+        STAG_TRY(multi_dslash_internal(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->prepared_nrhs,
+                                       rhs_block, &nb));
+    ctx->last_rhs_block = nb;
+    ctx->repeat_done = 1;
     return STAG_OK;
 }
 
@@ -266,23 +305,23 @@ int stag_dslash_result(stag_ctx ctx, double* out)
 {
     STAG_TRY(check_ctx(ctx));
     STAG_TRY(check_half_field(out, "out"));
-    if (!ctx->repeat_done) {
+    if (!ctx->repeat_done || ctx->prepared_prec < 0) {
         set_error("no stag_dslash_repeat since the last stag_dslash_prepare");
         return STAG_EINVAL;
     }
-    const int prec = ctx->prepared_prec;
+    const int prec = ctx->prepared_prec, n = ctx->prepared_nrhs;
     if (prec == STAG_F64)
-        STAG_CUDA_TRY(cudaMemcpyAsync(out, ctx->tmp_lo_out, lo_spinor_bytes(ctx->g, prec), cudaMemcpyDeviceToDevice,
-                                      ctx->stream));
+        STAG_CUDA_TRY(cudaMemcpyAsync(out, ctx->tmp_lo_out, lo_spinor_bytes(ctx->g, prec) * n,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
     else
-        STAG_TRY(convert_lo_to_f64(ctx, prec, ctx->tmp_lo_out, (double2*)out, 1, ctx->stream));
+        STAG_TRY(convert_lo_to_f64(ctx, prec, ctx->tmp_lo_out, (double2*)out, n, ctx->stream));
     return STAG_OK;
 }
 
 int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep)
 {
     STAG_TRY(check_ctx(ctx));
-    if (ctx->prepared_prec != prec || !ctx->tmp_lo_in) {
+    if (ctx->prepared_prec != prec || !ctx->tmp_lo_in || ctx->prepared_nrhs != 1) {
         set_error("call stag_dslash_prepare with this precision first");
         return STAG_EINVAL;
     }

@@ -630,6 +630,19 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
                               nb, nb_used);
 }
 
+// The multi operator on a precision's internal storage (as multi_dslash,
+// except that STAG_F64X reads and writes double-float vectors).
+int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs,
+                          int nb, int* nb_used)
+{
+    if (prec != STAG_F64X) return multi_dslash(ctx, prec, recon, par_out, out, in, nrhs, nb, nb_used);
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    return multi_dslash_tuned(ctx, "p3_r18_df", LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh},
+                              SpinorDF{(float4*)in}, SpinorDF{(float4*)out}, lo_spinor_bytes(ctx->g, prec), nrhs,
+                              par_out, nb, nb_used);
+}
+
 // ------------------------------------------------------------- slots
 
 int ensure_cg_f64(stag_ctx ctx);

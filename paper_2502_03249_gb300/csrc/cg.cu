@@ -354,6 +354,18 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
     return cg_solve_plan<F64Plan>(ctx, U, x_out, b_in, mass, sigma, prm, st, t0);
 }
 
+// Scalar record for timing the update kernel alone: never done (tol2 < 0,
+// maxiter at its largest), a fixed alpha.
+__global__ void k_update_time_init(CgScalars* sc)
+{
+    CgScalars s = {};
+    s.rr = 1.0;
+    s.alpha = 1e-3;
+    s.tol2 = -1.0;
+    s.maxiter = 0x7fffffff;
+    *sc = s;
+}
+
 void free_workspace(stag_ctx ctx)
 {
     Workspace* ws = ctx->ws;
@@ -379,6 +391,47 @@ int check_half_field(const void* p, const char* what);
 using namespace stag;
 
 extern "C" {
+
+int stag_cg_update_time(stag_ctx ctx, int f64_arith, int nrep, double* ms_per_launch)
+{
+    STAG_TRY(check_ctx(ctx));
+    if (nrep < 1 || !ms_per_launch || (f64_arith != STAG_F64 && f64_arith != STAG_F64X)) {
+        set_error("nrep must be >= 1, ms_per_launch non-NULL, f64_arith STAG_F64 or STAG_F64X");
+        return STAG_EINVAL;
+    }
+    STAG_TRY(ensure_cg_f64(ctx));
+    Workspace* ws = ctx->ws;
+    const int Vh = ctx->g.Vh, gb = nblk(Vh, BLAS_BS);
+    const size_t bytes = (size_t)3 * Vh * sizeof(double2);
+    for (double2* v : {ws->x, ws->r, ws->p, ws->Ap}) STAG_CUDA_TRY(cudaMemsetAsync(v, 0, bytes, ctx->stream));
+    k_update_time_init<<<1, 1, 0, ctx->stream>>>(ws->sc);
+    auto launch = [&]() {
+        if (f64_arith == STAG_F64X)
+            k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, ctx->stream>>>(Vh, DFPlan::v(ws->x), DFPlan::v(ws->r),
+                                                                   DFPlan::v(ws->p), DFPlan::v(ws->Ap), ws->sc,
+                                                                   ctx->partials, ctx->counters, 0, 0);
+        else
+            k_cg_update<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, ctx->stream>>>(
+                Vh, SpinorF64{ws->x}, SpinorF64{ws->r}, SpinorF64{ws->p}, SpinorF64{ws->Ap}, ws->sc, ctx->partials,
+                ctx->counters, 0, 0);
+    };
+    for (int k = 0; k < 2; ++k) launch();
+    cudaEvent_t e0, e1;
+    STAG_CUDA_TRY(cudaEventCreate(&e0));
+    STAG_CUDA_TRY(cudaEventCreate(&e1));
+    cudaEventRecord(e0, ctx->stream);
+    for (int k = 0; k < nrep; ++k) launch();
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    STAG_CUDA_TRY(e);
+    *ms_per_launch = (double)ms / nrep;
+    return STAG_OK;
+}
 
 void stag_solver_params_default(stag_solver_params* p)
 {

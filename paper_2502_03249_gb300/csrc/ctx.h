@@ -84,7 +84,8 @@ struct stag_ctx_s {
     stag::Workspace* ws;
     void* full_tmp;            // four half fields for the full-lattice solve
     int prepared_prec;         // storage of tmp_lo_in after stag_dslash_prepare (-1: none)
-    int repeat_done;           // tmp_lo_out holds a stag_dslash_repeat result of that field
+    int prepared_nrhs;         // fields prepared
+    int repeat_done;           // tmp_lo_out holds a stag_dslash_repeat result of those fields
     void* tune;                // autotuner cache (tune.cu)
     int last_rhs_block;        // right-hand sides per pass chosen by the last batched solve
 };
@@ -108,5 +109,7 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
                   cudaStream_t s);
 int launch_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
                            cudaStream_t s);
+int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs,
+                          int nb, int* nb_used);
 
 }  // namespace stag

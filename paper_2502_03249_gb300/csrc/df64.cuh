@@ -188,6 +188,10 @@ __device__ __forceinline__ DF df_fma(const DF& a, const DF& x, const DF& y)
 struct SpinorDF {
     typedef DF real;
     float4* p;
+    __host__ __device__ __forceinline__ SpinorDF at(int k, size_t stride) const
+    {
+        return SpinorDF{(float4*)((char*)p + (size_t)k * stride)};
+    }
     __device__ __forceinline__ Vec3<DF> load(int h) const
     {
         Vec3<DF> v;

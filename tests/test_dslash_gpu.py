@@ -234,3 +234,38 @@ def test_bare_kernel_path_matches_oracle(stag, dims, prec, recon):
     else:
         ref = orc.dslash_eo(dims, enc.recon12(U, enc.round_f16), enc.half_spinor(psi))
         assert rel(got, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("prec,recon,rhs_block", [(3, 18, 4), (3, 18, 1), (1, 12, 4), (0, 12, 2)])
+def test_bare_multi_kernel_path_matches_oracle(stag, prec, recon, rhs_block):
+    """The multi-vector operator the paper-comparable NMULTI scan times
+    (stag_dslash_prepare_multi / _repeat_multi on internal storage): each of 3
+    fields against the oracle, with a block of 4 (one lane masked), 2 or 1."""
+    dims = (10, 6, 4, 6)
+    U = li.random_links(dims, "smooth", eps=0.3, seed=301)
+    psi = li.gaussian_half(dims, seed=302, nvec=3)
+    ctx = make_ctx(stag, dims, U)
+    ctx.dslash_prepare_multi(dev(psi), prec)
+    ctx.dslash_repeat_multi(prec, recon, rhs_block, 2)
+    got = host(ctx.dslash_result(ctx.new_half(3)))
+    for k in range(3):
+        if prec == 3:
+            ref, bar = orc.dslash_eo(dims, U, psi[k]), 1e-12
+        elif prec == 1:
+            ref, bar = orc.dslash_eo(dims, enc.recon12(U, enc.round_f32), enc.round_f32(psi[k])), 1e-5
+        else:
+            ref, bar = orc.dslash_eo(dims, enc.recon12(U), psi[k]), 1e-12
+        assert rel(got[k], ref) <= bar
+    # a converting operator call discards the prepared fields
+    ctx.dslash_eo(ctx.new_half(), dev(psi[0]), 1, 12)
+    with pytest.raises(stag.StagError):
+        ctx.dslash_repeat_multi(prec, recon, rhs_block, 1)
+
+
+def test_cg_update_time(stag):
+    dims = (8, 8, 8, 8)
+    ctx = stag.Context(dims)
+    for arith in (0, 3):
+        assert 0.0 < ctx.cg_update_time(arith, nrep=3) < 100.0
+    with pytest.raises(stag.StagError):
+        ctx.cg_update_time(2, nrep=3)
