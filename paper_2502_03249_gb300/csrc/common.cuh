@@ -69,6 +69,33 @@ __device__ __forceinline__ void site_nbrs(const Geom& g, int p, int h, SiteNbrs&
     s.sb[3] = e3 ^ bb3 ^ SB;
 }
 
+// Forward neighbour (half index) and the sign bit of the forward hop (eta_mu
+// times the time-boundary sign) of half site h of parity p in direction mu,
+// the same values as site_nbrs for a runtime mu (no local array).
+__device__ __forceinline__ void fwd_nbr(const Geom& g, int p, int h, int mu, int& fw, uint32_t& sf)
+{
+    const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
+    const int r = h / g.Lxh;
+    const int xh = h - r * g.Lxh;
+    const int y = r % Ly;
+    const int zt = r / Ly;
+    const int z = zt % Lz;
+    const int t = zt / Lz;
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    const uint32_t SB = 0x80000000u;
+    if (mu == 0) {
+        fw = ((x + 1 == Lx) ? 0 : x + 1) / 2 + g.Lxh * r;
+        sf = 0u;
+        return;
+    }
+    const int c = (mu == 1) ? y : (mu == 2) ? z : t;
+    const int Lc = (mu == 1) ? Ly : (mu == 2) ? Lz : Lt;
+    const int st = (mu == 1) ? g.Lxh : (mu == 2) ? g.Lxh * Ly : g.Lxh * Ly * Lz;
+    fw = h + ((c + 1 == Lc) ? -(Lc - 1) * st : st);
+    const int ep = (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
+    sf = ((ep & 1) ? SB : 0u) ^ ((mu == 3 && t == Lt - 1) ? SB : 0u);
+}
+
 // ------------------------------------------------------- complex arithmetic
 
 template <typename T> struct Cplx { T re, im; };

@@ -41,20 +41,25 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
     const int t = (int)(r / g.L[2]);
     const int par = (x + y + z + t) & 1;
     const int h = (int)(i >> 1);
-    SiteNbrs s;
-    site_nbrs(g, par, h, s);
-    const int hf = s.fwd[mu];
+    int hf;
+    uint32_t sfb;
+    fwd_nbr(g, par, h, mu, hf, sfb);
     // eta_mu(x) times the forward boundary sign, as a double
-    const double eta = (s.sf[mu] ? -1.0 : 1.0);
+    const double eta = (sfb ? -1.0 : 1.0);
     // u, v and s of G = s u v^dagger
     const double2* up = par == 0 ? X + (size_t)h * 3 : Y + (size_t)h * 3;
     const double2* vp = par == 0 ? Y + (size_t)hf * 3 : X + (size_t)hf * 3;
     const double sg = (par == 0 ? 2.0 : -2.0) * eta * scale;
+    // u carries the factor s: G = u v^dagger, W = U G^dagger = (U v) u^dagger.
+    // GB300 runs FP64 at 1/64 of the FP32 rate and this kernel is bound by it,
+    // so the arithmetic is arranged to the minimum: scale factors folded into
+    // the vectors once, and only the upper triangle and the diagonal of the
+    // antihermitian P formed (P_ba = -conj(P_ab)).
     Cplx<double> u[3], v[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double2 q = __ldg(up + a), w = __ldg(vp + a);
-        u[a] = {q.x, q.y};
+        u[a] = {sg * q.x, sg * q.y};
         v[a] = {w.x, w.y};
     }
     double2* Gp = G ? G + (size_t)idx * 9 : nullptr;
@@ -63,10 +68,9 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                // s u_a conj(v_b)
-                const double re = u[a].re * v[b].re + u[a].im * v[b].im;
-                const double im = u[a].im * v[b].re - u[a].re * v[b].im;
-                double2 o = make_double2(sg * re, sg * im);
+                // u_a conj(v_b)
+                double2 o = make_double2(fma(u[a].re, v[b].re, u[a].im * v[b].im),
+                                         fma(u[a].im, v[b].re, -(u[a].re * v[b].im)));
                 if (accumulate) {
                     const double2 q = Gp[a * 3 + b];
                     o.x += q.x;
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
     }
     if (P) {
         const Mat3<double> Um = U.load(par, mu, h);
-        Cplx<double> w[3];   // U v
+        Cplx<double> w[3];   // (U v) / 2
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double re = 0.0, im = 0.0;
@@ -88,34 +92,36 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
                 im = fma(Um.m[a * 3 + c].re, v[c].im, im);
                 im = fma(Um.m[a * 3 + c].im, v[c].re, im);
             }
-            w[a] = {re, im};
+            w[a] = {0.5 * re, 0.5 * im};
         }
-        // W_ab = s w_a conj(u_b)
-        Cplx<double> W[9];
+        // P = (W - W^dagger)/2 - tr(W - W^dagger)/6 with W_ab = 2 w_a conj(u_b):
+        //   P_ab = w_a conj(u_b) - u_a conj(w_b),
+        //   P_aa = 2i Im(w_a conj(u_a)) - (2i/3) sum_c Im(w_c conj(u_c))
+        double d[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                W[a * 3 + b].re = sg * (w[a].re * u[b].re + w[a].im * u[b].im);
-                W[a * 3 + b].im = sg * (w[a].im * u[b].re - w[a].re * u[b].im);
-            }
-        // P = (W - W^dagger)/2 - tr(W - W^dagger)/6;  tr(W - W^dagger) = 2i Im tr W
-        const double trim = (W[0].im + W[4].im + W[8].im) / 3.0;
+        for (int a = 0; a < 3; ++a) d[a] = 2.0 * fma(w[a].im, u[a].re, -(w[a].re * u[a].im));
+        const double trim = (d[0] + d[1] + d[2]) * (1.0 / 3.0);
+        // off-diagonal (a, b) = (0, 1), (0, 2), (1, 2)
+        auto offd = [&](int a, int b) {
+            return Cplx<double>{fma(w[a].re, u[b].re, w[a].im * u[b].im) - fma(u[a].re, w[b].re, u[a].im * w[b].im),
+                                fma(w[a].im, u[b].re, -(w[a].re * u[b].im)) -
+                                    fma(u[a].im, w[b].re, -(u[a].re * w[b].im))};
+        };
+        const Cplx<double> p01 = offd(0, 1), p02 = offd(0, 2), p12 = offd(1, 2);
+        const Cplx<double> Pm[9] = {{0.0, d[0] - trim}, p01, p02,
+                                    {-p01.re, p01.im}, {0.0, d[1] - trim}, p12,
+                                    {-p02.re, p02.im}, {-p12.re, p12.im}, {0.0, d[2] - trim}};
         double2* Pp = P + (size_t)idx * 9;
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                double re = 0.5 * (W[a * 3 + b].re - W[b * 3 + a].re);
-                double im = 0.5 * (W[a * 3 + b].im + W[b * 3 + a].im);
-                if (a == b) im -= trim;
-                if (accumulate) {
-                    const double2 q = Pp[a * 3 + b];
-                    re += q.x;
-                    im += q.y;
-                }
-                Pp[a * 3 + b] = make_double2(re, im);
+        for (int k = 0; k < 9; ++k) {
+            double2 o = make_double2(Pm[k].re, Pm[k].im);
+            if (accumulate) {
+                const double2 q = Pp[k];
+                o.x += q.x;
+                o.y += q.y;
             }
+            Pp[k] = o;
+        }
     }
 }
 
@@ -171,8 +177,9 @@ int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2
     STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
     const Geom g = ctx->g;
     const LinkField<double2, 18> U{(const double2*)lk, g.Vh};
-    // Y = D_oe X into the context's odd temporary
-    STAG_TRY(launch_dslash(ctx, STAG_F64, 18, 1, ctx->tmp_odd, X, ctx->stream));
+    // Y = D_oe X into the context's odd temporary, with the double-float
+    // operator (~1e-14 relative; the IEEE-double one is FP64-bound on GB300)
+    STAG_TRY(launch_dslash(ctx, STAG_F64X, 18, 1, ctx->tmp_odd, X, ctx->stream));
     const long long n = 8LL * g.Vh;
     k_force<LinkField<double2, 18>><<<(unsigned)((n + F_BS - 1) / F_BS), F_BS, 0, ctx->stream>>>(
         g, U, X, ctx->tmp_odd, P, G, scale, accumulate);
