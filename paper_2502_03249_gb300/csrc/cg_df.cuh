@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(BS) k_dfcg_start(int Vh, const double2* b, Spi
 // Ap = (m^2 + sigma) p - D_eo t and the block partials of Re<p, Ap>; the last
 // block sets alpha (or flags a breakdown).
 template <class LF, int BS>
-__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_dfcg_Mp_dot(Geom g, LF U, SpinorDF t, SpinorDF p,
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfcg_Mp_dot(Geom g, LF U, SpinorDF t, SpinorDF p,
                                                                           SpinorDF Ap, CgScalars* sc, double* part,
                                                                           unsigned* cnt)
 {
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(BS) k_dfcg_p(int Vh, SpinorDF r, SpinorDF p, c
 // it, so that rr_true is the residual of the returned solution to double
 // rounding.  r is stored back as double-floats for a restart.
 template <class LF, int BS>
-__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_dfcg_true_resid(Geom g, LF U, SpinorDF t, SpinorDF x,
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfcg_true_resid(Geom g, LF U, SpinorDF t, SpinorDF x,
                                                                               const double2* b, SpinorDF r,
                                                                               CgScalars* sc, double* part,
                                                                               unsigned* cnt)

@@ -33,7 +33,7 @@ __device__ __forceinline__ double site_dot(const Vec3<T>& a, const Vec3<T>& b)
 }
 
 template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, S>::value)) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
 {
     if (sc->done) return;
     const int h = blockIdx.x * BS + threadIdx.x;
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_hop_guarded(Geom
 // SD is the storage view the operator reads t through (S itself, or a
 // double-float view of double storage); the epilogue runs in S's arithmetic.
 template <class LF, class SD, class S, int BS>
-__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_Mp_dot(Geom g, LF U, SD t, S p, S Ap, CgScalars* sc,
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SD>::value)) k_Mp_dot(Geom g, LF U, SD t, S p, S Ap, CgScalars* sc,
                                                double* part, unsigned* cnt)
 {
     __shared__ double red[BS / 32];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(BS) k_xpay_hop(Geom g, LF U, SD t, S x, S out,
 
 // out = D_{p,1-p} in; with guard set, only when a reliable update is due.
 template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_hop(Geom g, int p, LF U, S in, S out, const CgScalars* sc, int guard)
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, S>::value)) k_hop(Geom g, int p, LF U, S in, S out, const CgScalars* sc, int guard)
 {
     if (guard && !sc->reliable) return;
     const int h = blockIdx.x * BS + threadIdx.x;

@@ -7,7 +7,7 @@
 namespace stag {
 
 template <class LF, class SIn, class SOut, int BS>
-__global__ void __launch_bounds__(BS, OpMinBlocks<LF>::value) k_dslash(Geom g, int p, LF U, SIn in, SOut out)
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SIn>::value)) k_dslash(Geom g, int p, LF U, SIn in, SOut out)
 {
     const int h = blockIdx.x * BS + threadIdx.x;
     if (h >= g.Vh) return;

@@ -38,6 +38,8 @@ __device__ __forceinline__ Vec3<typename LF::real> dslash_site(const Geom& g, in
 // raises occupancy without spilling (measured 4 % and 7 % faster at 48^3 x 12).
 template <class LF> struct OpMinBlocks { static constexpr int value = 1; };
 template <int R> struct OpMinBlocks<LinkField<__half2, R>> { static constexpr int value = 8; };
+// the same for a link field and the spinor storage the operator reads
+template <class LF, class S> struct OpMinBlocksS { static constexpr int value = OpMinBlocks<LF>::value; };
 
 // Conversion of an operator result to the epilogue's arithmetic type (the
 // identity here; double-float results convert to double in df64.cuh).
