@@ -324,6 +324,20 @@ def profile_kernel(args, stag, torch):
         torch.cuda.synchronize()
         print(json.dumps({"profile_kernel": name, "workload": w3["name"], "solves": args.warmup + args.steps}))
         return 0
+    if parts[0] == "mixed":
+        # the 48^3 x 12 mixed-precision solve (inner F32 or F16, 12-real), host-driven
+        w2 = li.WORKLOADS[2]
+        dims2 = tuple(int(v) for v in dtxt.split("x")) if dtxt else w2["dims"]
+        ctx = stag.Context(dims2)
+        ctx.upload_gauge(li.random_links_torch(dims2, "smooth", w2["eps"], seed=li.workload_seed(2, 0)))
+        b = li.gaussian_half_torch(dims2, seed=li.workload_seed(2, 1))
+        x = ctx.new_half()
+        prec = {"f32": stag.F32, "f16": stag.F16}[parts[1]]
+        for _ in range(args.warmup + args.steps):
+            ctx.cg_solve_mixed(x, b, w2["mass"], tol=TOL, inner_prec=prec, inner_recon=int(parts[2]), use_graph=0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_kernel": name, "workload": w2["name"], "solves": args.warmup + args.steps}))
+        return 0
     if parts[0] == "cg":
         # whole solves, host-driven (ncu does not see the kernels of graphs with conditional nodes)
         arith = {"f64": F64_IEEE, "f64x": F64X}[parts[1]]
@@ -520,7 +534,8 @@ def main():
     ap.add_argument("--profile-kernel", default=None,
                     help="only run a few launches of one operator on the workload (for ncu): "
                          "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., or whole host-driven "
-                         "solves cg_f64 / cg_f64x, multi_f32_12 / multishift_f32_12 (32^3 x 16); optional @LXxLYxLZxLT")
+                         "solves cg_f64 / cg_f64x, multi_f32_12 / multishift_f32_12 (32^3 x 16), mixed_f16_12 / mixed_f32_12 "
+                         "(48^3 x 12); optional @LXxLYxLZxLT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
