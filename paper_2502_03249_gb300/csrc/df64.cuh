@@ -252,28 +252,6 @@ __device__ __forceinline__ double block_sum_df(DF v, double* smem)
     return s;
 }
 
-// Streaming loads for data read once per kernel: L2 evict-first policy (the
-// line is the first to go when the set needs room) and no L1 allocation.  A
-// half operator reads the whole gauge field (151 MB of double-float links at
-// 32^3 x 8, more than the 129 MB L2); loaded this way the links no longer
-// push the solver's 6 MB vectors out of L2 between the kernels of an
-// iteration (measured: CG iteration 76.5 -> 70.5 us at 32^3 x 8, 323 -> 310
-// us at 48^3 x 12).
-__device__ __forceinline__ unsigned long long l2_evict_first_policy()
-{
-    unsigned long long pol;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ float4 ld_stream(const float4* p, unsigned long long pol)
-{
-    float4 v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-        : "l"(p), "l"(pol));
-    return v;
-}
-
 // Links split at upload: per complex element a float4 (re_hi, re_lo, im_hi,
 // im_lo), same structure-of-arrays layout and byte count as the double copy.
 template <int RECON>
