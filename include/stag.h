@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define STAG_ABI_VERSION 1
+#define STAG_ABI_VERSION 2
 #define STAG_MAX_RHS 64   /* largest batch of right-hand sides or shifts */
 
 typedef struct stag_ctx_s *stag_ctx;
@@ -209,6 +209,14 @@ typedef struct {
     int f64_arith;         /* arithmetic of the double-precision operator passes (stag_cg_solve,
                               the reliable updates of the mixed solver): STAG_F64 (IEEE double)
                               or STAG_F64X (double-float) */
+    int temporal_gauge;    /* double-precision CG with f64_arith = STAG_F64X: 1 solves in temporal
+                              gauge (Sec. 4.3: the links of the time direction fixed to 1 except
+                              on the last slice, 6 link reads per site instead of 8), M' x' = g b
+                              with the gauge matrices g computed from the uploaded field, and
+                              returns x = g^dagger x'; the same system, the same residual norm.
+                              Needs unitary links (SU(3) or U(3): g U g^dagger is a gauge
+                              transformation only then).  0 (default): the links as uploaded.
+                              STAG_EINVAL with STAG_F64. */
 } stag_solver_params;
 
 typedef struct {

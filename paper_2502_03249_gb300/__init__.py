@@ -26,6 +26,7 @@ __all__ = [
 ]
 
 F64, F32, F16, F64X = 0, 1, 2, 3
+ABI_VERSION = 2   # include/stag.h STAG_ABI_VERSION: the struct layouts below
 RECON_18, RECON_12 = 18, 12
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 
@@ -55,7 +56,8 @@ class NotConverged(RuntimeError):
 class SolverParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("delta", ctypes.c_double), ("inner_prec", ctypes.c_int),
-                ("inner_recon", ctypes.c_int), ("rhs_block", ctypes.c_int), ("f64_arith", ctypes.c_int)]
+                ("inner_recon", ctypes.c_int), ("rhs_block", ctypes.c_int), ("f64_arith", ctypes.c_int),
+                ("temporal_gauge", ctypes.c_int)]
 
 
 class SolverStats(ctypes.Structure):
@@ -124,7 +126,11 @@ def load(path: str | None = None):
                 build()
             if not os.path.exists(p):
                 raise ImportError(f"libstag.so not found at {p}; run paper_2502_03249_gb300.build()")
-            _lib = _declare(ctypes.CDLL(p))
+            lib = _declare(ctypes.CDLL(p))
+            if lib.stag_abi_version() != ABI_VERSION:
+                raise ImportError(f"{p} has ABI version {lib.stag_abi_version()}, this binding {ABI_VERSION}: "
+                                  "rebuild with paper_2502_03249_gb300.build(force=True)")
+            _lib = lib
     return _lib
 
 

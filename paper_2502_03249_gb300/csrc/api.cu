@@ -195,6 +195,9 @@ int stag_destroy(stag_ctx ctx)
         if (ctx->links[s]) cudaFree(ctx->links[s]);
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->counters) cudaFree(ctx->counters);
+    if (ctx->tg_g) cudaFree(ctx->tg_g);
+    if (ctx->tg_links) cudaFree(ctx->tg_links);
+    if (ctx->tg_tmp) cudaFree(ctx->tg_tmp);
     if (ctx->tmp_odd) cudaFree(ctx->tmp_odd);
     if (ctx->tmp_lo_in) cudaFree(ctx->tmp_lo_in);
     if (ctx->tmp_lo_out) cudaFree(ctx->tmp_lo_out);

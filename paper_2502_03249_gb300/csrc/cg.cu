@@ -6,6 +6,7 @@
 #include <new>
 
 #include "cg_df.cuh"
+#include "tgauge.cuh"
 #include "workspace.h"
 
 namespace stag {
@@ -169,9 +170,10 @@ struct F64Plan {
     }
 };
 
-struct DFPlan {
-    typedef LinkFieldDF<18> LF;
-    static constexpr int slot = 1;
+template <class LFT, int SLOT>
+struct DFPlanT {
+    typedef LFT LF;
+    static constexpr int slot = SLOT;
     static SpinorDF v(double2* p) { return SpinorDF{reinterpret_cast<float4*>(p)}; }
     static int start(stag_ctx ctx, const double2* b_in, double mass, double sigma, double tol, int maxiter)
     {
@@ -216,6 +218,10 @@ struct DFPlan {
         return convert_lo_to_f64(ctx, STAG_F64X, ctx->ws->x, x_out, 1, ctx->stream);
     }
 };
+
+typedef DFPlanT<LinkFieldDF<18>, 1> DFPlan;
+// the same on temporal-gauge links (M' = g M g^dagger, see tgauge.cuh)
+typedef DFPlanT<LinkFieldTG, 2> DFPlanTG;
 
 // the graph  while (cond) { GRAPH_UNROLL CG iterations }, built once per context and plan
 template <class Plan>
@@ -338,6 +344,24 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
 {
     const auto t0 = std::chrono::steady_clock::now();
     STAG_TRY(ensure_cg_f64(ctx));
+    if (prm.f64_arith == STAG_F64X && prm.temporal_gauge) {
+        // M x = b as M' x' = g b, x = g^dagger x' (same residual norm: g is unitary)
+        const double2* G = nullptr;
+        const float4* lk = nullptr;
+        STAG_TRY(ensure_tg(ctx, &G, &lk));
+        if (!ctx->tg_tmp) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_tmp, (size_t)3 * ctx->g.Vh * sizeof(double2)));
+        STAG_TRY(tg_apply(ctx, G, b_in, ctx->tg_tmp, 0));
+        const LinkFieldTG U{lk, ctx->g.Vh, ctx->g.Vh / ctx->g.L[3], ctx->g.L[3]};
+        const int rc = cg_solve_plan<DFPlanTG>(ctx, U, x_out, ctx->tg_tmp, mass, sigma, prm, st, t0);
+        if (rc < 0) return rc;
+        STAG_TRY(tg_apply(ctx, G, x_out, x_out, 1));
+        STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        return rc;
+    }
+    if (prm.temporal_gauge) {
+        set_error("temporal_gauge needs f64_arith = STAG_F64X");
+        return STAG_EINVAL;
+    }
     if (prm.f64_arith == STAG_F64X) {
         const void* lk = nullptr;
         STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lk));
@@ -370,7 +394,7 @@ void free_workspace(stag_ctx ctx)
 {
     Workspace* ws = ctx->ws;
     if (!ws) return;
-    for (int i = 0; i < 2; ++i) free_graph_pair(ws->f64_graph[i], ws->f64_exec[i]);
+    for (int i = 0; i < 3; ++i) free_graph_pair(ws->f64_graph[i], ws->f64_exec[i]);
     free_mixed(ws);
     free_batches(ws);
     for (auto& m : ws->ms) m.release();
@@ -445,6 +469,7 @@ void stag_solver_params_default(stag_solver_params* p)
     p->inner_recon = STAG_RECON_12;
     p->rhs_block = 0;
     p->f64_arith = STAG_F64X;
+    p->temporal_gauge = 0;
 }
 
 int stag_cg_solve(stag_ctx ctx, double* x_even, const double* b_even, double mass, const stag_solver_params* params,

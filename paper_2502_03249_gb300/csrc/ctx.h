@@ -72,6 +72,10 @@ struct stag_ctx_s {
     void* links[8];            // link copies, index link_slot(prec, recon)
     size_t link_bytes[8];
     bool link_stale[8];        // derived copy older than the last upload (re-derived in place)
+    double2* tg_g;             // temporal gauge: g per site [par][V/2][9] (tgauge.cu)
+    float4* tg_links;          // temporal gauge: transformed double-float links
+    double2* tg_tmp;           // temporal gauge: g b for a solve
+    bool tg_stale;             // tg_g / tg_links older than the last upload
     // reduction scratch: partial sums (one double per block) and arrival counters
     double* partials;
     unsigned int* counters;    // 64 counters, each used by one reduction site
@@ -111,5 +115,7 @@ int launch_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void*
                            cudaStream_t s);
 int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs,
                           int nb, int* nb_used);
+int ensure_tg(stag_ctx ctx, const double2** G, const float4** links);
+int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int dagger);
 
 }  // namespace stag

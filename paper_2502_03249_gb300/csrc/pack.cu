@@ -93,6 +93,7 @@ int upload_gauge(stag_ctx ctx, const double* U, int on_device)
     // Derived copies are kept at their addresses and re-derived in place on
     // their next use: CUDA graphs captured by the solvers hold these pointers.
     for (int s = 1; s < 8; ++s) ctx->link_stale[s] = ctx->links[s] != nullptr;
+    ctx->tg_stale = true;
     if (!ctx->links[0]) {
         STAG_CUDA_TRY(cudaMalloc(&ctx->links[0], n * sizeof(double2)));
         ctx->link_bytes[0] = n * sizeof(double2);

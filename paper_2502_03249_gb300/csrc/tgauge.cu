@@ -1,0 +1,198 @@
+// tgauge.cu -- the temporal-gauge transform (see tgauge.cuh): the gauge
+// matrices g, the transformed double-float links, and g / g^dagger applied to
+// even-site vectors.  Computed in IEEE double from the internal F64/18 links
+// once per gauge upload, on first use.
+#include "ctx.h"
+#include "tgauge.cuh"
+
+namespace stag {
+
+__device__ __forceinline__ Cplx<double> cmul(Cplx<double> a, Cplx<double> b)
+{
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ Cplx<double> cmulc(Cplx<double> a, Cplx<double> b)   // a conj(b)
+{
+    return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -a.re * b.im)};
+}
+
+__device__ __forceinline__ Mat3<double> load_link64(const double2* L, int Vh, int par, int mu, int h)
+{
+    Mat3<double> U;
+    const double2* q = L + ((size_t)(par * 4 + mu) * 9) * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double2 v = q[(size_t)k * Vh];
+        U.m[k] = {v.x, v.y};
+    }
+    return U;
+}
+
+// C = A B
+__device__ __forceinline__ Mat3<double> mm(const Mat3<double>& A, const Mat3<double>& B)
+{
+    Mat3<double> C;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            Cplx<double> s = {0.0, 0.0};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const Cplx<double> p = cmul(A.m[a * 3 + c], B.m[c * 3 + b]);
+                s.re += p.re;
+                s.im += p.im;
+            }
+            C.m[a * 3 + b] = s;
+        }
+    return C;
+}
+
+// C = A B^dagger
+__device__ __forceinline__ Mat3<double> mmd(const Mat3<double>& A, const Mat3<double>& B)
+{
+    Mat3<double> C;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            Cplx<double> s = {0.0, 0.0};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const Cplx<double> p = cmulc(A.m[a * 3 + c], B.m[b * 3 + c]);
+                s.re += p.re;
+                s.im += p.im;
+            }
+            C.m[a * 3 + b] = s;
+        }
+    return C;
+}
+
+// g per site, one thread per spatial site walking up in time:
+// g(t = 0) = 1, g(t + 1) = g(t) U_t(t).  G: [par][V/2][9] complex128.
+__global__ void k_tg_gauge(Geom g, const double2* __restrict__ L, double2* __restrict__ G)
+{
+    const long long Vs = (long long)g.L[0] * g.L[1] * g.L[2];
+    const long long is = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (is >= Vs) return;
+    const int x = (int)(is % g.L[0]);
+    const int yz = (int)(is / g.L[0]);
+    const int y = yz % g.L[1], z = yz / g.L[1];
+    Mat3<double> cur;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) cur.m[k] = {(k % 4 == 0) ? 1.0 : 0.0, 0.0};
+    for (int t = 0; t < g.L[3]; ++t) {
+        const long long i = is + Vs * t;
+        const int par = (x + y + z + t) & 1;
+        const int h = (int)(i >> 1);
+        double2* dst = G + ((size_t)par * g.Vh + h) * 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dst[k] = make_double2(cur.m[k].re, cur.m[k].im);
+        if (t + 1 < g.L[3]) cur = mm(cur, load_link64(L, g.Vh, par, 3, h));
+    }
+}
+
+__device__ __forceinline__ Mat3<double> load_g(const double2* G, int Vh, int par, int h)
+{
+    Mat3<double> M;
+    const double2* q = G + ((size_t)par * Vh + h) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) M.m[k] = {q[k].x, q[k].y};
+    return M;
+}
+
+__device__ __forceinline__ void store_df(float4* q, size_t stride, const Mat3<double>& U)
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const DF re = split_double(U.m[k].re), im = split_double(U.m[k].im);
+        q[(size_t)k * stride] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+}
+
+// U'_mu(x) = g(x) U_mu(x) g(x + mu)^dagger for the spatial directions, and
+// U'_t(x) = g(x) U_t(x) on the last time slice; one thread per (par, h).
+__global__ void k_tg_links(Geom g, const double2* __restrict__ L, const double2* __restrict__ G,
+                           float4* __restrict__ out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2LL * g.Vh) return;
+    const int par = (int)(idx / g.Vh), h = (int)(idx - (long long)par * g.Vh);
+    SiteNbrs s;
+    site_nbrs(g, par, h, s);
+    const Mat3<double> gx = load_g(G, g.Vh, par, h);
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        const Mat3<double> U = load_link64(L, g.Vh, par, mu, h);
+        const Mat3<double> Up = mmd(mm(gx, U), load_g(G, g.Vh, 1 - par, s.fwd[mu]));
+        store_df(out + ((size_t)(par * 3 + mu) * 9) * g.Vh + h, g.Vh, Up);
+    }
+    const int Vsh = g.Vh / g.L[3];
+    const int t = h / Vsh;
+    if (t == g.L[3] - 1)
+        store_df(out + (size_t)54 * g.Vh + ((size_t)par * 9) * Vsh + (h - t * Vsh), Vsh,
+                 mm(gx, load_link64(L, g.Vh, par, 3, h)));
+}
+
+// out = g v (dagger = 0) or g^dagger v (dagger = 1) on even sites; in place allowed.
+__global__ void k_tg_apply(int Vh, const double2* __restrict__ G, const double2* in, double2* out, int dagger)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const Mat3<double> M = load_g(G, Vh, 0, h);
+    Cplx<double> v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double2 q = in[(size_t)h * 3 + c];
+        v[c] = {q.x, q.y};
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Cplx<double> s = {0.0, 0.0};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            // (g v)_a = g_ac v_c ; (g^dagger v)_a = conj(g_ca) v_c
+            const Cplx<double> p = dagger ? cmulc(v[c], M.m[c * 3 + a]) : cmul(M.m[a * 3 + c], v[c]);
+            s.re += p.re;
+            s.im += p.im;
+        }
+        out[(size_t)h * 3 + a] = make_double2(s.re, s.im);
+    }
+}
+
+// The gauge matrices and the temporal-gauge links for the current gauge
+// field, computed on first use after an upload (kept at their addresses).
+int ensure_tg(stag_ctx ctx, const double2** G, const float4** links)
+{
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    const Geom g = ctx->g;
+    if (!ctx->tg_g || ctx->tg_stale) {
+        const size_t gbytes = (size_t)2 * g.Vh * 9 * sizeof(double2);
+        const size_t lbytes = ((size_t)54 * g.Vh + (size_t)18 * (g.Vh / g.L[3])) * sizeof(float4);
+        if (!ctx->tg_g) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_g, gbytes));
+        if (!ctx->tg_links) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_links, lbytes));
+        const double2* L = (const double2*)ctx->links[0];
+        const long long Vs = (long long)g.L[0] * g.L[1] * g.L[2];
+        k_tg_gauge<<<(unsigned)((Vs + 127) / 128), 128, 0, ctx->stream>>>(g, L, ctx->tg_g);
+        const long long n = 2LL * g.Vh;
+        k_tg_links<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, L, ctx->tg_g, ctx->tg_links);
+        STAG_CUDA_TRY(cudaGetLastError());
+        ctx->tg_stale = false;
+    }
+    *G = ctx->tg_g;
+    *links = ctx->tg_links;
+    return STAG_OK;
+}
+
+int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int dagger)
+{
+    const int Vh = ctx->g.Vh;
+    k_tg_apply<<<(Vh + 255) / 256, 256, 0, ctx->stream>>>(Vh, G, in, out, dagger);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+}  // namespace stag

@@ -74,8 +74,8 @@ struct Workspace {
     CgScalars* sc = nullptr;        // device scalar records
     CgScalars* sc_host = nullptr;   // pinned host mirror for the final read
     bool f64_ready = false;
-    cudaGraph_t f64_graph[2] = {nullptr, nullptr};       // [IEEE double, double-float]
-    cudaGraphExec_t f64_exec[2] = {nullptr, nullptr};
+    cudaGraph_t f64_graph[3] = {nullptr, nullptr, nullptr};   // [IEEE double, double-float, temporal gauge]
+    cudaGraphExec_t f64_exec[3] = {nullptr, nullptr, nullptr};
     MixedSlot mixed[2][2];          // [F32, F16][18, 12]
     BatchSlot batch[3][2];          // [F64, F32, F16][18, 12]
     MsSlot ms[2];                   // multi-shift [F64, F32]

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_strerror(lib):
-    assert lib.stag_abi_version() == 1
+    assert lib.stag_abi_version() == 2
     for code in (0, 1, 2, -1, -2, -3, -4, -5, -6):
         assert len(lib.stag_strerror(code)) > 0
     assert lib.stag_strerror(12345) == b"unknown status"
@@ -70,4 +70,4 @@ def test_solver_param_defaults(lib):
     lib.stag_solver_params_default(ctypes.byref(p))
     assert p.tol == 1e-10 and p.maxiter == 100000 and p.use_graph == 1
     assert p.inner_prec == stag.F32 and p.inner_recon == 12 and p.delta == 0.1
-    assert p.f64_arith == stag.F64X
+    assert p.f64_arith == stag.F64X and p.temporal_gauge == 0
