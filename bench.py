@@ -339,12 +339,14 @@ def profile_kernel(args, stag, torch):
         print(json.dumps({"profile_kernel": name, "workload": w2["name"], "solves": args.warmup + args.steps}))
         return 0
     if parts[0] == "cg":
-        # whole solves, host-driven (ncu does not see the kernels of graphs with conditional nodes)
+        # whole solves, host-driven (ncu does not see the kernels of graphs with conditional nodes);
+        # cg_f64x_tg: in temporal gauge
         arith = {"f64": F64_IEEE, "f64x": F64X}[parts[1]]
+        tg = 1 if len(parts) > 2 and parts[2] == "tg" else 0
         b = torch.from_numpy(li.gaussian_half(dims, seed=li.workload_seed(WORKLOAD_INDEX, 1))).cuda()
         x = ctx.new_half()
         for _ in range(args.warmup + args.steps):
-            ctx.cg_solve(x, b, w["mass"], tol=TOL, use_graph=0, f64_arith=arith)
+            ctx.cg_solve(x, b, w["mass"], tol=TOL, use_graph=0, f64_arith=arith, temporal_gauge=tg)
         torch.cuda.synchronize()
         print(json.dumps({"profile_kernel": name, "workload": w["name"], "solves": args.warmup + args.steps}))
         return 0
