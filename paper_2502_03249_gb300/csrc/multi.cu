@@ -1,0 +1,157 @@
+// multi.cu -- the multi-vector operator (Sec. 4.3, NMULTI): each link loaded
+// once per site for a block of right-hand sides, the block chosen by the
+// autotuner; used by the batched solvers, stag_dslash_multi and the
+// measurement entry points.
+#include "batched_impl.cuh"
+
+namespace stag {
+
+// Multi operator pass for the autotuner and the public multi Dslash.
+template <class LF, class S, int NB>
+__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_multi_dslash(Geom g, int p, LF U, S in,
+                                                                                      S out, size_t stride, int nrhs)
+{
+    const int k0 = blockIdx.y * NB;
+    unsigned mask = 0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+        if (k0 + k < nrhs) mask |= 1u << k;
+    const int h = blockIdx.x * BBS + threadIdx.x;
+    if (h >= g.Vh) return;
+    Vec3<typename LF::real> acc[NB];
+    dslash_site_multi<LF, S, NB>(g, p, h, U, in, stride, k0, mask, acc);
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+        if (mask & (1u << k)) out.at(k0 + k, stride).store(h, acc[k]);
+}
+
+template <class LF, class S>
+int launch_multi_dslash_nb(stag_ctx ctx, int nb, const LF& U, const S& in, const S& out, size_t stride, int nrhs,
+                           int p, cudaStream_t s)
+{
+    const int gx = (ctx->g.Vh + BBS - 1) / BBS;
+    const dim3 grid(gx, (nrhs + nb - 1) / nb);
+    switch (nb) {
+    case 1: k_multi_dslash<LF, S, 1><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 2: k_multi_dslash<LF, S, 2><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 4: k_multi_dslash<LF, S, 4><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 8: k_multi_dslash<LF, S, 8><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    case 16: k_multi_dslash<LF, S, 16><<<grid, BBS, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs); break;
+    default: set_error("unsupported rhs block %d", nb); return STAG_EINVAL;
+    }
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+// Apply the multi Dslash on internal-storage multi fields; nb = 0 asks the
+// autotuner (timed on these buffers, cached per context and shape).
+template <class LF, class S>
+static int multi_dslash_tuned(stag_ctx ctx, const char* tag, const LF& U, const S& in, const S& out, size_t stride,
+                              int nrhs, int p, int nb, int* nb_used)
+{
+    if (nb == 0) {
+        char key[128];
+        snprintf(key, sizeof(key), "multi_dslash/%s/nrhs%d", tag, nrhs);
+        STAG_TRY(tune_choice(ctx, key, {1, 2, 4, 8, 16}, nrhs, &nb, [&](int c) {
+            return launch_multi_dslash_nb(ctx, c, U, in, out, stride, nrhs, p, ctx->stream);
+        }));
+    }
+    if (nb_used) *nb_used = nb;
+    return launch_multi_dslash_nb(ctx, nb, U, in, out, stride, nrhs, p, ctx->stream);
+}
+
+int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs, int nb,
+                 int* nb_used)
+{
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    const int Vh = ctx->g.Vh;
+    const size_t stride = lo_spinor_bytes(ctx->g, prec);
+    char tag[32];
+    snprintf(tag, sizeof(tag), "p%d_r%d", prec, recon);
+    if (prec == STAG_F64) {
+        SpinorF64 si{(double2*)in}, so{(double2*)out};
+        if (recon == 18)
+            return multi_dslash_tuned(ctx, tag, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+                                      par_out, nb, nb_used);
+        return multi_dslash_tuned(ctx, tag, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+                                  par_out, nb, nb_used);
+    }
+    if (prec == STAG_F64X) {
+        SpinorF64asDF si{(double2*)in}, so{(double2*)out};
+        return multi_dslash_tuned(ctx, tag, LinkFieldDF<18>{(const float4*)lk, Vh}, si, so, stride, nrhs, par_out, nb,
+                                  nb_used);
+    }
+    if (prec == STAG_F32) {
+        SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
+        if (recon == 18)
+            return multi_dslash_tuned(ctx, tag, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+                                      par_out, nb, nb_used);
+        return multi_dslash_tuned(ctx, tag, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+                                  par_out, nb, nb_used);
+    }
+    SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
+    if (recon == 18)
+        return multi_dslash_tuned(ctx, tag, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, stride, nrhs,
+                                  par_out, nb, nb_used);
+    return multi_dslash_tuned(ctx, tag, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, stride, nrhs, par_out,
+                              nb, nb_used);
+}
+
+// The multi operator on a precision's internal storage (as multi_dslash,
+// except that STAG_F64X reads and writes double-float vectors).
+int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs,
+                          int nb, int* nb_used)
+{
+    if (prec != STAG_F64X) return multi_dslash(ctx, prec, recon, par_out, out, in, nrhs, nb, nb_used);
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    return multi_dslash_tuned(ctx, "p3_r18_df", LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh},
+                              SpinorDF{(float4*)in}, SpinorDF{(float4*)out}, lo_spinor_bytes(ctx->g, prec), nrhs,
+                              par_out, nb, nb_used);
+}
+
+int check_ctx(stag_ctx ctx);
+int check_half_field(const void* p, const char* what);
+
+}  // namespace stag
+
+using namespace stag;
+
+extern "C" {
+
+int stag_dslash_multi(stag_ctx ctx, double* out, const double* in, int nrhs, int out_parity, int prec, int recon,
+                      int rhs_block)
+{
+    STAG_TRY(check_ctx(ctx));
+    STAG_TRY(check_half_field(out, "out"));
+    STAG_TRY(check_half_field(in, "in"));
+    if (out == in) {
+        set_error("out and in must not alias");
+        return STAG_EINVAL;
+    }
+    if (nrhs < 1 || nrhs > STAG_MAX_RHS || (out_parity != 0 && out_parity != 1)) {
+        set_error("nrhs must be in [1, %d] and out_parity 0 or 1", STAG_MAX_RHS);
+        return STAG_EINVAL;
+    }
+    if (rhs_block != 0 && rhs_block != 1 && rhs_block != 2 && rhs_block != 4 && rhs_block != 8 && rhs_block != 16) {
+        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
+        return STAG_EINVAL;
+    }
+    if (prec < STAG_F64 || prec > STAG_F64X || (recon != 18 && recon != 12) || (prec == STAG_F64X && recon != 18)) {
+        set_error("unsupported prec %d / recon %d", prec, recon);
+        return STAG_EUNSUPPORTED;
+    }
+    if (!ctx->have_gauge) {
+        set_error("no gauge field uploaded");
+        return STAG_ENOGAUGE;
+    }
+    if (prec == STAG_F64 || prec == STAG_F64X) return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr);
+    const size_t lo = lo_spinor_bytes(ctx->g, prec) * nrhs;
+    STAG_TRY(ensure_lo_tmp_public(ctx, lo));
+    STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, nrhs, ctx->stream));
+    STAG_TRY(multi_dslash(ctx, prec, recon, out_parity, ctx->tmp_lo_out, ctx->tmp_lo_in, nrhs, rhs_block, nullptr));
+    return convert_lo_to_f64(ctx, prec, ctx->tmp_lo_out, (double2*)out, nrhs, ctx->stream);
+}
+
+}  // extern "C"
