@@ -230,16 +230,17 @@ CG_GRAPH_UNROLL = 4     # CG iterations per body of the solver graph's while loo
 CG_CHECK_EVERY = 25     # host-driven loop: iterations between convergence reads
 
 
-def cg_kernel_launches(st, use_graph):
+def cg_kernel_launches(st, use_graph, arith=0):
     """Kernels one double-precision CG solve launches: the start kernel, four
     per iteration slot (whole graph bodies, or whole host-loop batches), the
-    two true-residual kernels per pass and one restart kernel per restart.
+    two true-residual kernels per pass and one restart kernel per restart; the
+    double-float solver converts its solution back to double with one more.
     Exact when the solve needed no restart (each pass's iterations are not
     reported separately)."""
     per = CG_GRAPH_UNROLL if use_graph else CG_CHECK_EVERY
     passes = st["restarts"] + 1
     slots = per * max(passes, math.ceil(max(st["iters"], 1) / per))
-    return 1 + 4 * slots + 2 * passes + st["restarts"]
+    return 1 + 4 * slots + 2 * passes + st["restarts"] + (1 if arith == F64X else 0)
 
 
 class L2Flush:
@@ -600,7 +601,7 @@ def main():
     ms_per_step = t_sum / args.steps
     half_per_step = statistics.mean(half_dslash(s) for s in stats)
     value = weak_scaling_value(ws, Vh, half_per_step, ms_per_step)
-    launches = sum(cg_kernel_launches(s, ug) for s in stats)
+    launches = sum(cg_kernel_launches(s, ug, arith) for s in stats)
     clocks = clk.summary()
 
     # ---- the same solve with IEEE-double operator passes

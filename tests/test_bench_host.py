@@ -87,3 +87,6 @@ def test_cg_kernel_launch_count():
     assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 0) == 1 + 4 * 100 + 2
     # a restart adds a pass: its residual kernels and the restart kernel
     assert bench.cg_kernel_launches({"iters": 2, "restarts": 1}, 1) == 1 + 4 * 8 + 4 + 1
+
+    # the double-float solver's final conversion kernel
+    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3) == 1 + 4 * 80 + 2 + 1
