@@ -68,17 +68,20 @@ def test_cg_4x4_workload(stag, use_graph, arith):
     assert abs(st["iters"] - it_cpu) <= max(3, it_cpu // 20)
 
 
-@pytest.mark.parametrize("arith", [0, 3])
-def test_graph_and_host_loop_identical(stag, arith):
+@pytest.mark.parametrize("arith,tol", [(0, 1e-11), (3, 1e-10)])
+def test_graph_and_host_loop_identical(stag, arith, tol):
+    """Graph and host-driven loops give the same solve bit for bit.  The
+    double-float solve uses tol 1e-10: its residual floor at m = 0.05 is
+    ~4e-12 (1e-12 (0.1 / m)^2), too close to 1e-11 for a stable stopping point."""
     dims, mass = (6, 4, 2, 10), 0.05
     ctx, U = setup(stag, dims, seed=311)
     b = dev(li.gaussian_half(dims, seed=312))
     x1, x2 = ctx.new_half(), ctx.new_half()
-    s1 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1, f64_arith=arith)
-    s2 = ctx.cg_solve(x2, b, mass, tol=1e-11, use_graph=0, check_every=7, f64_arith=arith)
+    s1 = ctx.cg_solve(x1, b, mass, tol=tol, use_graph=1, f64_arith=arith)
+    s2 = ctx.cg_solve(x2, b, mass, tol=tol, use_graph=0, check_every=7, f64_arith=arith)
     assert s1["iters"] == s2["iters"]
     assert bool((x1 == x2).all())      # deterministic reductions: bit for bit
-    s3 = ctx.cg_solve(x1, b, mass, tol=1e-11, use_graph=1, f64_arith=arith)   # graph reused
+    s3 = ctx.cg_solve(x1, b, mass, tol=tol, use_graph=1, f64_arith=arith)   # graph reused
     assert s3["iters"] == s1["iters"] and bool((x1 == x2).all())
 
 
@@ -167,3 +170,4 @@ def test_cg_edge_cases(stag):
     # the context still solves afterwards
     st = ctx.cg_solve(x, b, 0.1)
     assert st["status"] == 0
+
