@@ -92,35 +92,59 @@ def fp64_peak_gflops(sm_mhz: float = 2070.0) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling during the timed region.
+
+    A reader thread timestamps every sample; entering waits (up to 10 s) for
+    the first sample so that the sampler is running when the timed region
+    starts, and only samples taken between entering and leaving (plus one
+    interval) are summarised."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.samples = []          # (perf_counter time, csv line)
+        self.lines = []
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            if ln.strip():
+                self.samples.append((time.perf_counter(), ln))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+        if self.proc is not None:
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            t_end = time.perf_counter() + 10.0
+            while not self.samples and time.perf_counter() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
+        self.t1 = time.perf_counter()
         if self.proc is not None:
+            time.sleep(self.INTERVAL_MS * 1e-3)
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+                self.proc.wait()
+            self.thread.join(timeout=5)
+        hi = self.t1 + self.INTERVAL_MS * 1e-3
+        self.lines = [ln for t, ln in self.samples if self.t0 <= t <= hi]
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -200,12 +224,23 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w["name"], "dims": list(dims), "mass": mass},
+        "data": "synthetic", "config": headline_config(w),
         "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def headline_config(w):
+    """The benchmark step's workload, the same dict in both arms' lines."""
+    return {
+        "workload": w["name"] + ", double-precision CG to true residual 1e-10 (one solve per step)",
+        "dims": list(w["dims"]), "mass": w["mass"], "links": "exp(0.3 i H), 18-real double", "tol": TOL,
+        "l2": "GPU arm: flushed (512 MB write, then 512 MB read) before every step; working set 151 MB links "
+              "+ 6 MB per vector",
+        "value_definition": "570 flop x V/2 x half-Dslash applications per solve / solve time",
+    }
 
 
 def cpu_baseline_sample(dims, U, b, mass, Vh, budget_s=12.0):
@@ -230,17 +265,29 @@ CG_GRAPH_UNROLL = 4     # CG iterations per body of the solver graph's while loo
 CG_CHECK_EVERY = 25     # host-driven loop: iterations between convergence reads
 
 
-def cg_kernel_launches(st, use_graph, arith=0):
+def cg_df_dir(vh, l2_bytes):
+    """Whether the double-float CG applies p = r + beta p inside its operator
+    passes (three launches per iteration): the library's rule, five 48-byte
+    vectors per site within half of L2, unless STAG_CG_DIR forces it."""
+    e = os.environ.get("STAG_CG_DIR", "")
+    if e[:1] in ("0", "1"):
+        return e[:1] == "1"
+    return 5 * 48 * vh <= 0.5 * l2_bytes
+
+
+def cg_kernel_launches(st, use_graph, arith=0, df_dir=True):
     """Kernels one double-precision CG solve launches: the start kernel, four
-    per iteration slot (whole graph bodies, or whole host-loop batches), the
-    two true-residual kernels per pass and one restart kernel per restart; the
-    double-float solver converts its solution back to double with one more.
-    Exact when the solve needed no restart (each pass's iterations are not
-    reported separately)."""
+    per iteration slot (whole graph bodies, or whole host-loop batches; three
+    when the double-float solver applies p = r + beta p inside its operator
+    passes, df_dir), the two true-residual kernels per pass and one restart
+    kernel per restart; the double-float solver converts its solution back to
+    double with one more.  Exact when the solve needed no restart (each pass's
+    iterations are not reported separately)."""
     per = CG_GRAPH_UNROLL if use_graph else CG_CHECK_EVERY
     passes = st["restarts"] + 1
     slots = per * max(passes, math.ceil(max(st["iters"], 1) / per))
-    return 1 + 4 * slots + 2 * passes + st["restarts"] + (1 if arith == F64X else 0)
+    per_iter = 3 if (arith == F64X and df_dir) else 4
+    return 1 + per_iter * slots + 2 * passes + st["restarts"] + (1 if arith == F64X else 0)
 
 
 class L2Flush:
@@ -525,7 +572,7 @@ def section_force(stag, torch, timer, hbm):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -601,7 +648,8 @@ def main():
     ms_per_step = t_sum / args.steps
     half_per_step = statistics.mean(half_dslash(s) for s in stats)
     value = weak_scaling_value(ws, Vh, half_per_step, ms_per_step)
-    launches = sum(cg_kernel_launches(s, ug, arith) for s in stats)
+    df_dir = cg_df_dir(Vh, getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 126 << 20))
+    launches = sum(cg_kernel_launches(s, ug, arith, df_dir) for s in stats)
     clocks = clk.summary()
 
     # ---- the same solve with IEEE-double operator passes
@@ -697,15 +745,10 @@ def main():
         "vs_baseline": None,
         "dtype": "f64 storage; operator in double-float (f32x2)" if arith == F64X else "f64",
         "data": "synthetic",
-        "config": {
-            "workload": w["name"] + ", double-precision CG to true residual 1e-10 (one solve per step)",
-            "dims": list(dims), "mass": mass, "links": "exp(0.3 i H), 18-real double", "tol": TOL,
-            "f64_arith": "double-float (STAG_F64X)" if arith == F64X else "IEEE double (STAG_F64)",
-            "l2": "flushed (512 MB write, then 512 MB read) before every step; working set 151 MB links + 6 MB per vector",
-            "value_definition": "570 flop x V/2 x half-Dslash applications per solve / solve time",
-        },
+        "config": headline_config(w),
         "cg": {"time_to_solution_ms": ms_per_step, "iters": last["iters"], "restarts": last["restarts"],
-               "true_rel_residual": last["true_rel_residual"], "half_dslash_per_solve": half_per_step},
+               "true_rel_residual": last["true_rel_residual"], "half_dslash_per_solve": half_per_step,
+               "f64_arith": "double-float (STAG_F64X)" if arith == F64X else "IEEE double (STAG_F64)"},
         "cg_ieee_f64": {"time_to_solution_ms": ms_ieee, "iters": st_ieee["iters"],
                         "true_rel_residual": st_ieee["true_rel_residual"]},
         "cg_temporal_gauge": None if st_tg is None else {

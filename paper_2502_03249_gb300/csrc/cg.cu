@@ -3,6 +3,7 @@
 // iteration running inside one CUDA graph whose while-loop condition is
 // cleared on the device, so no host round trip happens per iteration.
 #include <chrono>
+#include <cstdlib>
 #include <new>
 
 #include "cg_df.cuh"
@@ -80,7 +81,8 @@ __global__ void __launch_bounds__(BS) k_cg_start_f64(int Vh, const double2* b, d
     }
 }
 
-// Restart from the true residual now held in r: p = r, rr = rr_true.
+// Restart from the true residual now held in r: p = r, rr = rr_true, beta = 0
+// (the double-float iteration applies p = r + beta p when it next reads p).
 template <int BS>
 __global__ void __launch_bounds__(BS) k_cg_restart_f64(int Vh, const double2* r, double2* p, CgScalars* sc)
 {
@@ -88,6 +90,7 @@ __global__ void __launch_bounds__(BS) k_cg_restart_f64(int Vh, const double2* r,
     if (i < 3LL * Vh) p[i] = r[i];
     if (i == 0) {
         sc->rr = sc->rr_true;
+        sc->beta = 0.0;
         sc->done = 0;
         sc->status = 0;
     }
@@ -170,6 +173,27 @@ struct F64Plan {
     }
 };
 
+// Whether the double-float CG applies p = r + beta p inside its operator
+// passes: when its five vectors (x r p Ap t, 48 bytes per site each) fit in
+// half of L2, where the hop's second neighbour gather hits L2 (32^3 x 8: 5.62
+// against 5.72 ms per solve); on larger lattices the separate pass is faster
+// (48^3 x 12: 29.7 against 30.7 ms).  Environment STAG_CG_DIR=0 or 1 forces
+// either arrangement (the two give the same bits).
+static int decide_df_dir(stag_ctx ctx)
+{
+    Workspace* ws = ctx->ws;
+    if (ws->df_dir >= 0) return STAG_OK;
+    const char* e = getenv("STAG_CG_DIR");
+    if (e && (e[0] == '0' || e[0] == '1')) {
+        ws->df_dir = e[0] - '0';
+        return STAG_OK;
+    }
+    int l2 = 0;
+    STAG_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device));
+    ws->df_dir = (5.0 * 48.0 * ctx->g.Vh <= 0.5 * (double)l2) ? 1 : 0;
+    return STAG_OK;
+}
+
 template <class LFT, int SLOT>
 struct DFPlanT {
     typedef LFT LF;
@@ -179,6 +203,7 @@ struct DFPlanT {
     {
         Workspace* ws = ctx->ws;
         const int Vh = ctx->g.Vh;
+        STAG_TRY(decide_df_dir(ctx));
         // b stays double: the true residual is formed against it
         STAG_CUDA_TRY(cudaMemcpyAsync(ws->b, b_in, (size_t)3 * Vh * sizeof(double2), cudaMemcpyDeviceToDevice,
                                       ctx->stream));
@@ -193,12 +218,20 @@ struct DFPlanT {
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
         const int gh = nblk(g.Vh, HOP_BS), gb = nblk(g.Vh, BLAS_BS);
-        k_hop_guarded<LF, SpinorDF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, v(ws->p), v(ws->t), ws->sc);
-        k_dfcg_Mp_dot<LF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->p), v(ws->Ap), ws->sc, ctx->partials,
-                                                        ctx->counters);
-        k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), ws->sc,
-                                                      ctx->partials, ctx->counters, cond, use_cond);
-        k_dfcg_p<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->r), v(ws->p), ws->sc);
+        if (ws->df_dir == 1) {
+            k_dfcg_hop<LF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->r), v(ws->p), v(ws->t), ws->sc);
+            k_dfcg_Mp_dot<LF, HOP_BS, true><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->r), v(ws->p), v(ws->Ap),
+                                                                  ws->sc, ctx->partials, ctx->counters);
+            k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), ws->sc,
+                                                          ctx->partials, ctx->counters, cond, use_cond);
+        } else {
+            k_hop_guarded<LF, SpinorDF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, v(ws->p), v(ws->t), ws->sc);
+            k_dfcg_Mp_dot<LF, HOP_BS, false><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->r), v(ws->p), v(ws->Ap),
+                                                                   ws->sc, ctx->partials, ctx->counters);
+            k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), ws->sc,
+                                                          ctx->partials, ctx->counters, cond, use_cond);
+            k_dfcg_p<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->r), v(ws->p), ws->sc);
+        }
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }

@@ -1,13 +1,20 @@
 // cg_df.cuh -- the conjugate-gradient iteration on M = m^2 - D_eo D_oe (+ sigma)
 // with the Krylov vectors x, r, p, Ap and t = D_oe p held as double-floats
-// (SpinorDF): the same four launches per iteration as cg_kernels.cuh,
+// (SpinorDF): the steps of cg_kernels.cuh,
 //   hop     t  = D_oe p
 //   Mp_dot  Ap = (m^2 + sigma) p - D_eo t,  pAp = Re<p,Ap>,  alpha = rr / pAp
 //   update  x += alpha p, r -= alpha Ap,    rr' = |r|^2,     beta = rr'/rr
 //   p       p  = r + beta p
-// but every per-site operation runs in double-float arithmetic on the FP32
-// pipe (GB300 executes FP64 at 1/64 of the FP32 rate).  The scalars alpha,
-// beta and the reductions' results stay double in the CgScalars record.
+// in four launches, or in three when the solver's vectors fit in L2: then the
+// direction update p = r + beta p of one iteration is applied where the next
+// iteration first reads p (the hop reads r and p at its neighbours through
+// SpinorDFDir, Mp_dot forms and stores p at its own site; bit for bit the
+// values of the separate pass).  On larger lattices the second neighbour
+// gather costs more than the pass it saves.  Every per-site operation
+// runs in double-float arithmetic on the FP32 pipe (GB300 executes FP64 at
+// 1/64 of the FP32 rate).  The scalars alpha, beta and the reductions'
+// results stay double in the CgScalars record; beta = 0 after a (re)start,
+// where p already holds r.
 #pragma once
 
 #include "cg_kernels.cuh"
@@ -61,12 +68,45 @@ __global__ void __launch_bounds__(BS) k_dfcg_start(int Vh, const double2* b, Spi
     }
 }
 
-// Ap = (m^2 + sigma) p - D_eo t and the block partials of Re<p, Ap>; the last
-// block sets alpha (or flags a breakdown).
+// The search direction as the first operator pass of an iteration reads it:
+// r + beta p, formed at load time from the stored r and p with the
+// previous iteration's beta (bit for bit the value Mp_dot then stores).
+struct SpinorDFDir {
+    typedef DF real;
+    SpinorDF r, p;
+    DF beta;
+    __device__ __forceinline__ Vec3<DF> load(int h) const
+    {
+        const Vec3<DF> rv = r.load(h), pv = p.load(h);
+        Vec3<DF> o;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.c[c].re = df_fma(beta, pv.c[c].re, rv.c[c].re);
+            o.c[c].im = df_fma(beta, pv.c[c].im, rv.c[c].im);
+        }
+        return o;
+    }
+};
+
+// t = D_oe (r + beta p) on odd sites (p itself is updated by Mp_dot).
 template <class LF, int BS>
-__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfcg_Mp_dot(Geom g, LF U, SpinorDF t, SpinorDF p,
-                                                                          SpinorDF Ap, CgScalars* sc, double* part,
-                                                                          unsigned* cnt)
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfcg_hop(Geom g, LF U, SpinorDF r,
+                                                                                       SpinorDF p, SpinorDF t,
+                                                                                       const CgScalars* sc)
+{
+    if (sc->done) return;
+    const int h = blockIdx.x * BS + threadIdx.x;
+    if (h >= g.Vh) return;
+    const SpinorDFDir in{r, p, split_double(sc->beta)};
+    t.store(h, dslash_site(g, 1, h, U, in));
+}
+
+// DIR: p = r + beta p (stored) first.  Ap = (m^2 + sigma) p - D_eo t and the
+// block partials of Re<p, Ap>; the last block sets alpha (or flags a breakdown).
+template <class LF, int BS, bool DIR>
+__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfcg_Mp_dot(Geom g, LF U, SpinorDF t, SpinorDF r,
+                                                                          SpinorDF p, SpinorDF Ap, CgScalars* sc,
+                                                                          double* part, unsigned* cnt)
 {
     __shared__ double red[BS / 32];
     __shared__ bool last;
@@ -76,7 +116,13 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfc
     DF d(0);
     if (h < g.Vh) {
         const Vec3<DF> Dt = dslash_site(g, 0, h, U, t);
-        const Vec3<DF> pv = p.load(h);
+        Vec3<DF> pv;
+        if (DIR) {
+            pv = SpinorDFDir{r, p, split_double(sc->beta)}.load(h);
+            p.store(h, pv);
+        } else {
+            pv = p.load(h);
+        }
         Vec3<DF> a;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -151,6 +197,7 @@ __global__ void __launch_bounds__(BS) k_dfcg_update(int Vh, SpinorDF x, SpinorDF
     }
 }
 
+// p = r + beta p as a pass of its own (the four-launch iteration)
 template <int BS>
 __global__ void __launch_bounds__(BS) k_dfcg_p(int Vh, SpinorDF r, SpinorDF p, const CgScalars* sc)
 {

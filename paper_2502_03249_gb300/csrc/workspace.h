@@ -76,6 +76,9 @@ struct Workspace {
     bool f64_ready = false;
     cudaGraph_t f64_graph[3] = {nullptr, nullptr, nullptr};   // [IEEE double, double-float, temporal gauge]
     cudaGraphExec_t f64_exec[3] = {nullptr, nullptr, nullptr};
+    // double-float CG: 1 applies p = r + beta p inside the operator passes
+    // (three launches per iteration), 0 as a pass of its own; -1 undecided
+    int df_dir = -1;
     MixedSlot mixed[2][2];          // [F32, F16][18, 12]
     BatchSlot batch[3][2];          // [F64, F32, F16][18, 12]
     MsSlot ms[2];                   // multi-shift [F64, F32]

@@ -88,5 +88,45 @@ def test_cg_kernel_launch_count():
     # a restart adds a pass: its residual kernels and the restart kernel
     assert bench.cg_kernel_launches({"iters": 2, "restarts": 1}, 1) == 1 + 4 * 8 + 4 + 1
 
-    # the double-float solver's final conversion kernel
-    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3) == 1 + 4 * 80 + 2 + 1
+    # the double-float solver: three kernels per iteration (four with the
+    # direction update as a pass of its own) and its final conversion kernel
+    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3) == 1 + 3 * 80 + 2 + 1
+    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3, False) == 1 + 4 * 80 + 2 + 1
+
+
+def test_cg_direction_update_rule(monkeypatch):
+    import bench
+    l2 = 126 << 20
+    monkeypatch.delenv("STAG_CG_DIR", raising=False)
+    assert bench.cg_df_dir(32 * 32 * 32 * 8 // 2, l2)          # 31.5 MB of vectors
+    assert not bench.cg_df_dir(48 * 48 * 48 * 12 // 2, l2)     # 159 MB
+    monkeypatch.setenv("STAG_CG_DIR", "0")
+    assert not bench.cg_df_dir(128, l2)
+    monkeypatch.setenv("STAG_CG_DIR", "1")
+    assert bench.cg_df_dir(48 * 48 * 48 * 12 // 2, l2)
+
+
+def test_clock_sampler_keeps_samples_of_the_timed_window(tmp_path, monkeypatch):
+    """The sampler waits for its first sample before the timed region and keeps
+    only the samples taken inside it (a fake nvidia-smi on PATH, no GPU)."""
+    import time
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/usr/bin/env python3\n"
+                    "import sys, time\n"
+                    "time.sleep(0.3)\n"
+                    "k = 0\n"
+                    "while True:\n"
+                    "    act = 'Active' if k == 3 else 'Not Active'\n"
+                    "    print(f'0, {1900 + k}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {act}', flush=True)\n"
+                    "    k += 1\n"
+                    "    time.sleep(0.05)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    with bench.ClockSampler(0) as clk:
+        assert clk.samples, "entering waits for the first sample"
+        time.sleep(0.4)
+    s = clk.summary()
+    assert s["samples"] >= 4
+    assert s["sm_max_mhz"] == 2070.0 and 1900.0 <= s["sm_mhz"] <= 1930.0
+    assert s["reasons"] == ["sw_power_cap"]

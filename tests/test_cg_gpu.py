@@ -171,3 +171,35 @@ def test_cg_edge_cases(stag):
     st = ctx.cg_solve(x, b, 0.1)
     assert st["status"] == 0
 
+
+
+@pytest.mark.parametrize("tol", [1e-10, 1e-17])
+@pytest.mark.parametrize("tg", [0, 1])
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_direction_update_arrangements_identical(stag, monkeypatch, use_graph, tg, tol):
+    """The double-float CG applies p = r + beta p either as a pass of its own
+    (STAG_CG_DIR=0) or inside the next iteration's operator passes (1, the
+    choice on lattices whose solver vectors fit in L2): the same arithmetic,
+    so the same iterations and the same solution bit for bit.  tol 1e-17 lies
+    below the rounding floor: the solve restarts from the true residual until
+    a restart no longer halves it, which checks that both arrangements begin
+    a restart with p = r."""
+    dims, mass = (10, 6, 4, 6), 0.05
+    U = li.random_links(dims, "smooth", eps=0.3, seed=361)
+    b = li.gaussian_half(dims, seed=362)
+    out = {}
+    for setting in ("0", "1"):
+        monkeypatch.setenv("STAG_CG_DIR", setting)
+        ctx = stag.Context(dims)
+        ctx.upload_gauge(dev(U))
+        x = ctx.new_half()
+        st = ctx.cg_solve(x, dev(b), mass, tol=tol, use_graph=use_graph, temporal_gauge=tg, raise_on_fail=False)
+        if tol >= 1e-10:
+            assert st["status"] == 0
+            assert orc.true_residual(dims, U, mass, host(x), b) <= tol
+        else:
+            assert st["status"] == 1 and st["restarts"] >= 1 and st["true_rel_residual"] < 1e-11
+        out[setting] = (st["iters"], st["restarts"], host(x))
+        ctx.close()
+    assert out["0"][:2] == out["1"][:2]
+    assert np.array_equal(out["0"][2], out["1"][2])
