@@ -169,10 +169,10 @@ int stag_dslash_multi(stag_ctx ctx, double *out, const double *in, int nrhs, int
 int stag_apply_M(stag_ctx ctx, double *out_even, const double *in_even, double mass);
 
 /* Allocation-free variant of stag_apply_M, for callers that cannot allocate
- * device memory: code running while a stream is captured into a CUDA graph
- * (cudaMalloc and cudaFree are not capturable, and cudaFree synchronises the
- * device), latency-critical loops that cannot absorb that synchronisation,
- * and hosts that keep every device byte in their own pre-sized arena.  It
+ * device memory: hosts that own every device byte through their own pre-sized
+ * arena or caching allocator and forbid libraries to call cudaMalloc behind
+ * it, and latency-critical loops that cannot absorb the device-wide
+ * synchronisation cudaFree implies (and the latency of cudaMalloc).  It
  * needs no context: the gauge field is read straight from the caller's
  * canonical buffer, and the odd-site intermediate D_oe in lives in a static
  * device array of STAG_NOALLOC_MAX_VH x 3 complex doubles (6 MiB) that every

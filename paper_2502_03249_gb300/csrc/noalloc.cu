@@ -3,11 +3,10 @@
 //
 // stag_apply_M needs an odd-parity intermediate t = D_oe in; a context
 // allocates it with cudaMalloc when it is created.  Some callers cannot do
-// that: code that runs while a stream is being captured into a CUDA graph
-// (cudaMalloc/cudaFree are not capturable and cudaFree synchronises the
-// device), latency-critical loops where an allocation's implicit device
-// synchronisation is not acceptable, and hosts that must keep every device
-// byte inside their own pre-sized memory arena.  For them this variant takes
+// that: hosts that own every device byte through their own pre-sized arena
+// or caching allocator and forbid a library to allocate behind it, and
+// latency-critical loops that cannot absorb the device-wide synchronisation
+// cudaFree implies (or the latency of cudaMalloc).  For them this variant takes
 // the gauge field straight from the caller's canonical buffer (no context, no
 // internal link copy) and keeps the intermediate in a fixed, statically sized
 // device array that is part of the loaded library image.

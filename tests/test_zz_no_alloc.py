@@ -1,10 +1,10 @@
 """The allocation-free operator entry point, stag_apply_M_noalloc.
 
 Some callers cannot allocate device memory at the point where they apply the
-operator: code running while a stream is being captured into a CUDA graph
-(allocation calls are not capturable and freeing synchronises the device),
-latency-critical loops that cannot absorb that synchronisation, and hosts
-that must keep every device byte in their own pre-sized arena.  For them the
+operator: hosts that own all device memory through their own pre-sized arena
+or caching allocator and forbid a library to call cudaMalloc behind it, and
+latency-critical loops that cannot absorb the device-wide synchronisation
+cudaFree implies.  For them the
 library offers stag_apply_M_noalloc, which keeps its intermediate field in a
 fixed static device array.  It must give the same result as stag_apply_M (the
 context-based entry point), within the double-precision tolerance used for
