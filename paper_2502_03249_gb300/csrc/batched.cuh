@@ -15,6 +15,14 @@ namespace stag {
 template <class LF, int NB> struct MultiMinBlocks {
     static constexpr int value = NB == 1 ? OpMinBlocks<LF>::value : 4;
 };
+// The operator pass with the Ap / <p, Ap> epilogue on float arithmetic: up to
+// 8 right-hand sides it fits 5 blocks per SM (96 registers) without spilling,
+// one block more than the general bound (at which it took 127 registers); 16
+// right-hand sides, or double arithmetic, would spill.
+template <class LF, int NB> struct MultiMpMinBlocks {
+    static constexpr int value = (NB > 1 && NB <= 8 && sizeof(typename LF::real) == 4)
+                                     ? 5 : MultiMinBlocks<LF, NB>::value;
+};
 
 // acc[k] = (D_{p,1-p} in_{k0+k})_h for the k with bit k of mask set.
 // in.at(j, stride) is field j of the multi field.
