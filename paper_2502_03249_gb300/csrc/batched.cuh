@@ -9,19 +9,16 @@
 namespace stag {
 
 // Minimum resident blocks of 128 threads for a batched operator kernel: the
-// single-RHS bound of the link field for NB = 1, else 4 (at most 128
-// registers per thread; unbounded, the compiler takes up to 222 for NB = 8
-// and runs 2 blocks per SM).
+// single-RHS bound of the link field for NB = 1; on float arithmetic 7 for up
+// to 4 right-hand sides per block (72 registers) and 6 for 8 (80 registers,
+// a few dozen bytes of spill), which the latency-bound multi-vector passes
+// need more than registers (32^3 x 16, 16 RHS: 105.1 -> 99.7 ms, the
+// autotuner now choosing blocks of 4; at 4 and 5 blocks per SM the kernels
+// took 96-127 registers); else 4 (at most 128 registers; unbounded, the
+// compiler takes up to 222 for NB = 8 and runs 2 blocks per SM).
 template <class LF, int NB> struct MultiMinBlocks {
-    static constexpr int value = NB == 1 ? OpMinBlocks<LF>::value : 4;
-};
-// The operator pass with the Ap / <p, Ap> epilogue on float arithmetic: up to
-// 8 right-hand sides it fits 5 blocks per SM (96 registers) without spilling,
-// one block more than the general bound (at which it took 127 registers); 16
-// right-hand sides, or double arithmetic, would spill.
-template <class LF, int NB> struct MultiMpMinBlocks {
-    static constexpr int value = (NB > 1 && NB <= 8 && sizeof(typename LF::real) == 4)
-                                     ? 5 : MultiMinBlocks<LF, NB>::value;
+    static constexpr int value = NB == 1 ? OpMinBlocks<LF>::value
+                                         : (sizeof(typename LF::real) != 4 ? 4 : (NB <= 4 ? 7 : (NB <= 8 ? 6 : 4)));
 };
 
 // acc[k] = (D_{p,1-p} in_{k0+k})_h for the k with bit k of mask set.

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_hop(
 
 // Ap_k = (m^2 + sigma_k) p_k - D_eo t_k, pAp_k, alpha_k = rr_k / pAp_k.
 template <class LF, class S, int NB>
-__global__ void __launch_bounds__(BBS, (MultiMpMinBlocks<LF, NB>::value)) k_b_Mp_dot(Geom g, LF U, S t, S p, S Ap,
+__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_Mp_dot(Geom g, LF U, S t, S p, S Ap,
                                                                                   size_t stride, BatchScal bs)
 {
     __shared__ double red[(BBS / 32) * (NB > 1 ? NB : 1)];
