@@ -130,3 +130,25 @@ def test_clock_sampler_keeps_samples_of_the_timed_window(tmp_path, monkeypatch):
     assert s["samples"] >= 4
     assert s["sm_max_mhz"] == 2070.0 and 1900.0 <= s["sm_mhz"] <= 1930.0
     assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_reference_arm_line(tmp_path):
+    """`bench.py --impl reference` times the CPU oracle on the benchmark's
+    workload and prints one JSON line with the keys the harness reads, the
+    same metric, unit and config as the GPU arm."""
+    import json
+    import subprocess
+    import sys
+    import bench
+    import lattice_inputs as li
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=str(tmp_path))
+    assert p.returncode == 0, p.stderr
+    line = json.loads(p.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GFLOP/s"
+    assert line["higher_is_better"] is True and line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3
+    assert line["config"] == bench.headline_config(li.WORKLOADS[bench.WORKLOAD_INDEX])
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
