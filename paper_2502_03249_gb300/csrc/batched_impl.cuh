@@ -149,21 +149,27 @@ __global__ void __launch_bounds__(BBS) k_b_init(int Vh, const double2* b, const 
 
 // ------------------------------------------------------- operator passes
 
-// t_k = D_oe p_k for the systems selected by MODE (0: active, 1: updating).
+// t_k = D_oe p_k for the systems selected by MODE.  MODE 0 (active systems,
+// the iteration): grid (gx, nrhs / NB), row y takes systems y NB ... .  MODE 1
+// (systems due a reliable update, usually one or two): grid (gx, 1), every
+// block loops over the groups of NB systems and skips those with none due, so
+// no block is launched for systems that have nothing to do.
 template <class LF, class S, int NB, int MODE>
 __global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_hop(Geom g, LF U, S in, S out,
                                                                                size_t stride, BatchScal bs)
 {
-    const int k0 = blockIdx.y * NB;
-    const unsigned mask = MODE == 0 ? mask_active<NB>(bs, k0) : mask_updating<NB>(bs, k0);
-    if (!mask) return;
     const int h = blockIdx.x * BBS + threadIdx.x;
     if (h >= g.Vh) return;
-    Vec3<typename LF::real> acc[NB];
-    dslash_site_multi<LF, S, NB>(g, 1, h, U, in, stride, k0, mask, acc);
+    const int kbeg = MODE == 0 ? blockIdx.y * NB : 0, kend = MODE == 0 ? kbeg + NB : bs.nrhs;
+    for (int k0 = kbeg; k0 < kend; k0 += NB) {
+        const unsigned mask = MODE == 0 ? mask_active<NB>(bs, k0) : mask_updating<NB>(bs, k0);
+        if (!mask) continue;
+        Vec3<typename LF::real> acc[NB];
+        dslash_site_multi<LF, S, NB>(g, 1, h, U, in, stride, k0, mask, acc);
 #pragma unroll
-    for (int k = 0; k < NB; ++k)
-        if (mask & (1u << k)) out.at(k0 + k, stride).store(h, acc[k]);
+        for (int k = 0; k < NB; ++k)
+            if (mask & (1u << k)) out.at(k0 + k, stride).store(h, acc[k]);
+    }
 }
 
 // Ap_k = (m^2 + sigma_k) p_k - D_eo t_k, pAp_k, alpha_k = rr_k / pAp_k.
@@ -295,40 +301,40 @@ __global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride
     }
 }
 
-// x_hi_k += xlo_k, xlo_k = 0 for systems due a reliable update.  grid (gx, nrhs).
+// x_hi_k += xlo_k, xlo_k = 0 for systems due a reliable update.  grid (gx, 1):
+// each block loops over the systems and skips those not due.
 template <class SX>
 __global__ void __launch_bounds__(BBS) k_b_accum_x(int Vh, double2* x_hi, SX xlo, size_t sx_stride, BatchScal bs)
 {
-    const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
-    if (!updating(bs.sc[k]) || h >= Vh) return;
-    const SX xk = xlo.at(k, sx_stride);
-    const Vec3<typename SX::real> v = xk.load_rw(h);
-    Vec3<typename SX::real> z;
-    const size_t o = ((size_t)k * Vh + h) * 3;
+    const int h = blockIdx.x * BBS + threadIdx.x;
+    if (h >= Vh) return;
+    for (int k = 0; k < bs.nrhs; ++k) {
+        if (!updating(bs.sc[k])) continue;
+        const SX xk = xlo.at(k, sx_stride);
+        const Vec3<typename SX::real> v = xk.load_rw(h);
+        Vec3<typename SX::real> z;
+        const size_t o = ((size_t)k * Vh + h) * 3;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double2 xv = x_hi[o + c];
-        xv.x += (double)v.c[c].re;
-        xv.y += (double)v.c[c].im;
-        x_hi[o + c] = xv;
-        z.c[c].re = z.c[c].im = 0;
+        for (int c = 0; c < 3; ++c) {
+            double2 xv = x_hi[o + c];
+            xv.x += (double)v.c[c].re;
+            xv.y += (double)v.c[c].im;
+            x_hi[o + c] = xv;
+            z.c[c].re = z.c[c].im = 0;
+        }
+        xk.store(h, z);
     }
-    xk.store(h, z);
 }
 
-// r_hi_k = b_k - (m^2 + sigma_k) x_hi_k + D_eo t_k, rr_true_k (double) for updating systems.
-// The operator pass runs in LF's arithmetic (IEEE double, or double-float on
-// the same double vectors through SD), the epilogue in double.
+// One group of NB systems of k_b_resid64 (below).
 template <class LF, class SD, int NB>
-__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_resid64(Geom g, LF U, const double2* t,
-                                                                                        const double2* x_hi,
-                                                                                        const double2* b, double2* r_hi,
-                                                                                        BatchScal bs)
+__device__ __forceinline__ void resid64_group(const Geom& g, const LF& U, const double2* t, const double2* x_hi,
+                                              const double2* b, double2* r_hi, const BatchScal& bs, int k0,
+                                              double* red, unsigned* lastm_p)
 {
-    __shared__ double red[(BBS / 32) * (NB > 1 ? NB : 1)];
-    __shared__ unsigned lastm;
-    const int k0 = blockIdx.y * NB;
+    unsigned& lastm = *lastm_p;
     const unsigned mask = mask_updating<NB>(bs, k0);
+    if (!mask) return;   // uniform over the block
     const int h = blockIdx.x * BBS + threadIdx.x;
     const size_t stride = (size_t)g.Vh * 3 * sizeof(double2);
     double d[NB];
@@ -368,17 +374,36 @@ __global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_resi
     }
 }
 
+// r_hi_k = b_k - (m^2 + sigma_k) x_hi_k + D_eo t_k, rr_true_k (double) for updating systems.
+// The operator pass runs in LF's arithmetic (IEEE double, or double-float on
+// the same double vectors through SD), the epilogue in double.  grid (gx, 1):
+// each block loops over the groups of NB systems and skips those with none
+// due; every system due gets one partial from every block and is finished by
+// its own last block, as in the iteration's reductions.
+template <class LF, class SD, int NB>
+__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_resid64(Geom g, LF U, const double2* t,
+                                                                                        const double2* x_hi,
+                                                                                        const double2* b, double2* r_hi,
+                                                                                        BatchScal bs)
+{
+    __shared__ double red[(BBS / 32) * (NB > 1 ? NB : 1)];
+    __shared__ unsigned lastm;
+    for (int k0 = 0; k0 < bs.nrhs; k0 += NB)
+        resid64_group<LF, SD, NB>(g, U, t, x_hi, b, r_hi, bs, k0, red, &lastm);
+}
+
 // r_k = lo(r_hi_k) (and p_k = r_k at the start); then, in the last block,
 // restart each updated system's recurrence from its true residual and decide
-// convergence.  grid (gx, nrhs).
+// convergence.  grid (gx, 1): each block loops over the systems due.
 template <class S>
 __global__ void __launch_bounds__(BBS) k_b_finish(int Vh, const double2* r_hi, S r, S p, size_t stride, BatchScal bs,
                                                   int start, cudaGraphConditionalHandle wh, int use_cond)
 {
     __shared__ bool last;
     typedef typename S::real real;
-    const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
-    if (updating(bs.sc[k]) && h < Vh) {
+    const int h = blockIdx.x * BBS + threadIdx.x;
+    for (int k = 0; k < bs.nrhs && h < Vh; ++k) {
+        if (!updating(bs.sc[k])) continue;
         Vec3<real> v;
         const size_t o = ((size_t)k * Vh + h) * 3;
 #pragma unroll
@@ -456,12 +481,12 @@ struct BatchPlan {
     {
         const Geom g = ctx->g;
         const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
-        const dim3 gb(m.gx, m.nrhs), g64(m.gx, (m.nrhs + NB64 - 1) / NB64);
+        const dim3 gb(m.gx, m.nrhs), g1(m.gx, 1);
         k_b_init<SX><<<gb, BBS, 0, s>>>(g.Vh, m.b, x0, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs, tol, maxiter,
                                         mass * mass, shifts_dev, delta);
-        k_b_hop<LF64, SD64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
-        k_b_resid64<LF64, SD64, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
-        k_b_finish<S><<<gb, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 1, 0, 0);
+        k_b_hop<LF64, SD64, NB64, 1><<<g1, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
+        k_b_resid64<LF64, SD64, NB64><<<g1, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+        k_b_finish<S><<<g1, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 1, 0, 0);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
@@ -482,11 +507,12 @@ struct BatchPlan {
     {
         const Geom g = ctx->g;
         const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
-        const dim3 gb(m.gx, m.nrhs), g64(m.gx, (m.nrhs + NB64 - 1) / NB64);
-        k_b_accum_x<SX><<<gb, BBS, 0, s>>>(g.Vh, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs);
-        k_b_hop<LF64, SD64, NB64, 1><<<g64, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
-        k_b_resid64<LF64, SD64, NB64><<<g64, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
-        k_b_finish<S><<<gb, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 0,
+        // one grid row: the blocks loop over the (usually one or two) systems due
+        const dim3 g1(m.gx, 1);
+        k_b_accum_x<SX><<<g1, BBS, 0, s>>>(g.Vh, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs);
+        k_b_hop<LF64, SD64, NB64, 1><<<g1, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
+        k_b_resid64<LF64, SD64, NB64><<<g1, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+        k_b_finish<S><<<g1, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 0,
                                          lg ? lg->w : 0, use_cond);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;

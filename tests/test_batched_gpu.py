@@ -128,3 +128,27 @@ def test_batched_edge_cases(stag):
                                    ctypes.c_double(0.1), None, None) == -1
     with pytest.raises(stag.StagError):
         ctx.cg_solve_multi(X, dev(B), 0.1, rhs_block=3)
+
+
+@pytest.mark.parametrize("prec,f64_arith", [(1, 3), (2, 3), (1, 0)])
+def test_batched_graph_and_host_loop_identical(stag, prec, f64_arith):
+    """The graph (reliable updates inside a device-side if) and the host-driven
+    loop (the reliable-update kernels launched every iteration, doing work only
+    for the systems due) run the same kernels: the same iterations, reliable
+    updates and solutions bit for bit, every system at the oracle's residual."""
+    dims, mass, nrhs = (10, 6, 4, 6), 0.05, 5
+    U = li.random_links(dims, "smooth", eps=0.3, seed=541)
+    B = li.gaussian_half(dims, seed=542, nvec=nrhs)
+    B[3] *= 1e-4
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(dev(U))
+    out = {}
+    for ug in (1, 0):
+        X = ctx.new_half(nrhs)
+        st = ctx.cg_solve_multi(X, dev(B), mass, tol=1e-10, inner_prec=prec, inner_recon=12, rhs_block=4,
+                                use_graph=ug, f64_arith=f64_arith)
+        out[ug] = ([(s["iters"], s["reliable_updates"]) for s in st], host(X))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
+    for k in range(nrhs):
+        assert orc.true_residual(dims, U, mass, out[1][1][k], B[k]) <= 1e-10
