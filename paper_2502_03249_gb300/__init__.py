@@ -23,12 +23,14 @@ import threading
 __all__ = [
     "F64", "F32", "F16", "F64X", "RECON_18", "RECON_12", "StagError", "NotConverged",
     "load", "build", "Context", "SolverParams", "SolverStats", "StaggeredAction", "fermion_force",
+    "apply_M_noalloc", "NOALLOC_MAX_VH",
 ]
 
 F64, F32, F16, F64X = 0, 1, 2, 3
 ABI_VERSION = 2   # include/stag.h STAG_ABI_VERSION: the struct layouts below
 RECON_18, RECON_12 = 18, 12
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+NOALLOC_MAX_VH = 1 << 17   # include/stag.h STAG_NOALLOC_MAX_VH
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libstag.so")
@@ -108,6 +110,7 @@ def _declare(lib):
         "stag_strerror": ([I], ctypes.c_char_p),
         "stag_last_error": ([], ctypes.c_char_p),
         "stag_abi_version": ([], I),
+        "stag_apply_M_noalloc": ([ctypes.POINTER(I), P, P, P, D, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -476,3 +479,23 @@ def fermion_force(U, phi, lattice, mass, **params):
     P = torch.empty_like(U)
     lattice.fermion_force(X, P=P)
     return P
+
+
+def apply_M_noalloc(dims, U, out, inp, mass, stream=None):
+    """stag_apply_M_noalloc: out = m^2 inp - D_eo D_oe inp without any device
+    allocation, for callers whose device memory is owned by their own arena.
+    No context: U is the canonical (V,4,3,3) complex128 gauge field, out and inp
+    are (V/2,3) complex128 even-site fields, all on the current CUDA device;
+    V/2 <= NOALLOC_MAX_VH.  The intermediate lives in one static device array
+    shared by every call: calls that overlap on the device must be serialised.
+    Enqueued on `stream` (default: torch's current stream)."""
+    torch = _torch()
+    lib = load()
+    d = (ctypes.c_int * 4)(*(int(v) for v in dims))
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    for t, what in ((U, "U"), (out, "out"), (inp, "inp")):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise StagError(-1, f"{what} must be a contiguous complex128 CUDA tensor")
+    _check(lib.stag_apply_M_noalloc(d, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(inp.data_ptr()), float(mass), ctypes.c_void_p(s)))
+    return out

@@ -71,3 +71,18 @@ def test_solver_param_defaults(lib):
     assert p.tol == 1e-10 and p.maxiter == 100000 and p.use_graph == 1
     assert p.inner_prec == stag.F32 and p.inner_recon == 12 and p.delta == 0.1
     assert p.f64_arith == stag.F64X and p.temporal_gauge == 0
+
+
+def test_noalloc_rejects_bad_geometry_without_device(lib):
+    """The allocation-free operator checks extents and its static limit before
+    any CUDA call."""
+    import paper_2502_03249_gb300 as stag
+    d = (ctypes.c_int * 4)(4, 4, 3, 4)
+    assert lib.stag_apply_M_noalloc(d, None, None, None, 0.1, None) == -2
+    d = (ctypes.c_int * 4)(64, 64, 64, 16)   # V/2 = 2^21
+    assert lib.stag_apply_M_noalloc(d, None, None, None, 0.1, None) == -1
+    assert b"static scratch limit" in lib.stag_last_error()
+    assert lib.stag_apply_M_noalloc(None, None, None, None, 0.1, None) == -1
+    assert stag.NOALLOC_MAX_VH == 1 << 17
+    hdr = open(HEADER).read()
+    assert "#define STAG_NOALLOC_MAX_VH (1 << 17)" in hdr

@@ -203,3 +203,21 @@ def test_direction_update_arrangements_identical(stag, monkeypatch, use_graph, t
         ctx.close()
     assert out["0"][:2] == out["1"][:2]
     assert np.array_equal(out["0"][2], out["1"][2])
+
+
+def test_apply_M_noalloc_binding(stag):
+    """The Python wrapper of the allocation-free operator: equal to the
+    context's M to the operator bar, bad tensors rejected before the call."""
+    import torch
+    dims, mass = (6, 4, 2, 10), 0.2
+    U = li.random_links(dims, "haar", seed=381)
+    ctx, _ = setup(stag, dims, seed=381)
+    psi = dev(li.gaussian_half(dims, seed=382))
+    ref = ctx.new_half()
+    ctx.apply_M(ref, psi, mass)
+    out = torch.empty_like(psi)
+    stag.apply_M_noalloc(dims, dev(U), out, psi, mass)
+    torch.cuda.synchronize()
+    assert rel(host(out), host(ref)) <= 1e-12
+    with pytest.raises(stag.StagError):
+        stag.apply_M_noalloc(dims, dev(U), out.to(torch.complex64), psi, mass)
