@@ -186,7 +186,10 @@ int stag_apply_M(stag_ctx ctx, double *out_even, const double *in_even, double m
  * Result: out_even = m^2 in_even - D_eo D_oe in_even, the same arithmetic as
  * stag_apply_M.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture begins.  All calls share the one array:
+ * call before any stream capture begins.  The address is cached for the life
+ * of the device's primary context: resetting the device (cudaDeviceReset)
+ * between calls is not supported.  U, out_even and in_even must be memory of
+ * the current device (STAG_EINVAL otherwise).  All calls share the one array:
  * calls that overlap on the GPU (other streams, other host threads) race on
  * it and must be serialised by the caller.  Nothing in it needs clearing
  * between calls (every element is written before it is read). */

@@ -491,11 +491,21 @@ def apply_M_noalloc(dims, U, out, inp, mass, stream=None):
     Enqueued on `stream` (default: torch's current stream)."""
     torch = _torch()
     lib = load()
-    d = (ctypes.c_int * 4)(*(int(v) for v in dims))
+    dims = tuple(int(v) for v in dims)
+    if len(dims) != 4 or any(v < 2 or v % 2 for v in dims):
+        raise StagError(-2, f"lattice extents must be four even integers >= 2, got {dims}")
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    d = (ctypes.c_int * 4)(*dims)
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-    for t, what in ((U, "U"), (out, "out"), (inp, "inp")):
-        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+    cur = torch.cuda.current_device()
+    for t, what, shape in ((U, "U", (V, 4, 3, 3)), (out, "out", (V // 2, 3)), (inp, "inp", (V // 2, 3))):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda or \
+                not t.is_contiguous():
             raise StagError(-1, f"{what} must be a contiguous complex128 CUDA tensor")
+        if tuple(t.shape) != shape:
+            raise StagError(-1, f"{what} must have shape {shape} for dims {dims}, got {tuple(t.shape)}")
+        if t.device.index != cur:
+            raise StagError(-1, f"{what} is on cuda:{t.device.index}, but cuda:{cur} is current")
     _check(lib.stag_apply_M_noalloc(d, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                     ctypes.c_void_p(inp.data_ptr()), float(mass), ctypes.c_void_p(s)))
     return out

@@ -53,7 +53,9 @@ struct LinkCanonicalF64 {
 
 // Device address of g_noalloc_odd, looked up once per device with that
 // device current (the host-side symbol is only a stand-in, not a device
-// address).
+// address).  The address is cached for the life of the device's primary
+// context: a cudaDeviceReset between calls (which unloads the module and may
+// reload it elsewhere) is not supported.
 static int noalloc_scratch(double2** out)
 {
     static std::mutex mu;
@@ -78,7 +80,10 @@ static int noalloc_scratch(double2** out)
     return STAG_OK;
 }
 
-static int check_device_buffer(const void* p, const char* what)
+// A buffer the kernels may dereference: device (or managed) memory of the
+// current device.  Memory of another GPU is rejected: the kernels would reach
+// it through the unified address space without peer access and fault.
+static int check_device_buffer(const void* p, const char* what, int dev)
 {
     if (!p || ((uintptr_t)p & 15u)) {
         set_error("%s is NULL or not 16-byte aligned", what);
@@ -92,6 +97,10 @@ static int check_device_buffer(const void* p, const char* what)
     }
     if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
         set_error("%s is not device memory", what);
+        return STAG_EINVAL;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) {
+        set_error("%s lives on device %d, but device %d is current", what, a.device, dev);
         return STAG_EINVAL;
     }
     return STAG_OK;
@@ -108,23 +117,26 @@ extern "C" int stag_apply_M_noalloc(const int dims[4], const double* U, double* 
         set_error("dims is NULL");
         return STAG_EINVAL;
     }
-    long long V = 1;
-    for (int mu = 0; mu < 4; ++mu) {
+    for (int mu = 0; mu < 4; ++mu)
         if (dims[mu] < 2 || dims[mu] % 2) {
             set_error("extent %d of direction %d is not even and >= 2", dims[mu], mu);
             return STAG_EGEOM;
         }
-        V *= dims[mu];
-    }
+    // The product stops growing once it passes the limit, so every partial
+    // product stays below 2^18 * 2^31 and cannot overflow.
+    long long V = 1;
+    for (int mu = 0; mu < 4 && V <= 2LL * STAG_NOALLOC_MAX_VH; ++mu) V *= dims[mu];
     if (V / 2 > STAG_NOALLOC_MAX_VH) {
-        set_error("stag_apply_M_noalloc: V/2 = %lld sites exceeds the static scratch limit of %d sites "
+        set_error("stag_apply_M_noalloc: the lattice exceeds the static scratch limit of %d sites "
                   "(V <= %d); use a context and stag_apply_M instead",
-                  V / 2, STAG_NOALLOC_MAX_VH, 2 * STAG_NOALLOC_MAX_VH);
+                  STAG_NOALLOC_MAX_VH, 2 * STAG_NOALLOC_MAX_VH);
         return STAG_EINVAL;
     }
-    STAG_TRY(check_device_buffer(U, "U"));
-    STAG_TRY(check_device_buffer(out_even, "out_even"));
-    STAG_TRY(check_device_buffer(in_even, "in_even"));
+    int dev = 0;
+    STAG_CUDA_TRY(cudaGetDevice(&dev));
+    STAG_TRY(check_device_buffer(U, "U", dev));
+    STAG_TRY(check_device_buffer(out_even, "out_even", dev));
+    STAG_TRY(check_device_buffer(in_even, "in_even", dev));
     if (out_even == in_even) {
         set_error("out and in must not alias");
         return STAG_EINVAL;

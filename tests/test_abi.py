@@ -83,6 +83,12 @@ def test_noalloc_rejects_bad_geometry_without_device(lib):
     assert lib.stag_apply_M_noalloc(d, None, None, None, 0.1, None) == -1
     assert b"static scratch limit" in lib.stag_last_error()
     assert lib.stag_apply_M_noalloc(None, None, None, None, 0.1, None) == -1
+    # extents whose product overflows a 64-bit integer are refused, not wrapped
+    huge = (ctypes.c_int * 4)(1 << 16, 1 << 16, 1 << 16, (1 << 15) + 2)
+    assert lib.stag_apply_M_noalloc(huge, None, None, None, 0.1, None) == -1
+    assert b"static scratch limit" in lib.stag_last_error()
+    huge = (ctypes.c_int * 4)(2147483646, 2147483646, 2147483646, 2147483646)
+    assert lib.stag_apply_M_noalloc(huge, None, None, None, 0.1, None) == -1
     assert stag.NOALLOC_MAX_VH == 1 << 17
     hdr = open(HEADER).read()
     assert "#define STAG_NOALLOC_MAX_VH (1 << 17)" in hdr

@@ -221,3 +221,13 @@ def test_apply_M_noalloc_binding(stag):
     assert rel(host(out), host(ref)) <= 1e-12
     with pytest.raises(stag.StagError):
         stag.apply_M_noalloc(dims, dev(U), out.to(torch.complex64), psi, mass)
+    # shapes that do not match dims are refused on the host, before any launch
+    Ud = dev(U)
+    with pytest.raises(stag.StagError, match="shape"):
+        stag.apply_M_noalloc(dims, Ud[: Ud.shape[0] // 2], out, psi, mass)
+    with pytest.raises(stag.StagError, match="shape"):
+        stag.apply_M_noalloc(dims, Ud, out[:-1], psi[:-1], mass)
+    with pytest.raises(stag.StagError, match="shape"):
+        stag.apply_M_noalloc((6, 4, 2, 12), Ud, out, psi, mass)
+    with pytest.raises(stag.StagError):
+        stag.apply_M_noalloc((6, 4, 3, 10), Ud, out, psi, mass)

@@ -20,6 +20,7 @@ import numpy as np
 import pytest
 
 import lattice_inputs as li
+import oracle as orc
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +55,12 @@ def test_noalloc_matches_apply_M_on_two_calls_in_a_row(stag):
         o, r = out.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(o))
         assert np.linalg.norm(o - r) <= 1e-12 * np.linalg.norm(r)
+        # and directly against the CPU oracle's M on the same host data (the
+        # links are read from the canonical layout here, so an index mistake
+        # shared with the context's own link packing would show up only here)
+        want = orc.apply_M(dims, U.cpu().numpy(), mass, psi.cpu().numpy())
+        err = np.linalg.norm(o - want) / np.linalg.norm(want)
+        assert err <= 1e-12, f"relative error against the oracle: {err:.3e}"
 
 
 def test_noalloc_rejects_lattices_beyond_the_static_limit(stag):
