@@ -97,6 +97,10 @@ def test_f32_matches_oracle_on_stored_values(stag, dims, recon, parity):
     ref = orc.dslash_half(dims, Us, enc.round_f32(psi), parity)
     got = host(out)
     assert rel(got, ref) <= 1e-5
+    # every element: 48 float products per component, each rounded at 2^-24
+    # of at most max|U| max|psi| (|U| <= 1), plus the float32 output rounding
+    bound = 48 * 2.0 ** -24 * np.abs(psi).max() + 2.0 ** -24 * np.abs(ref).max()
+    assert np.abs(got - ref).max() <= bound
     assert rel(got, orc.dslash_half(dims, U, psi, parity)) <= 1e-5
 
 
@@ -116,6 +120,59 @@ def test_f16_matches_oracle_on_stored_values(stag, dims, recon):
     assert rel(got, ref_out) <= 1e-3
     assert rel(got, ref) <= 1e-3
     assert rel(got, orc.dslash_oe(dims, U, psi)) <= 3e-3
+    # every element, against its own site's scale: the float accumulation
+    # (48 products at 2^-24 of the neighbours' magnitudes) can move a half code
+    # by at most one unit, 2^-10 of the site's norm
+    site = np.abs(ref_out.view(np.float64).reshape(-1, 6)).max(axis=1)
+    nbr = 48 * 2.0 ** -24 * np.abs(psi).max()
+    err = np.abs((got - ref_out).view(np.float64)).reshape(-1, 6).max(axis=1)
+    assert np.all(err <= 2.0 ** -10 * site + 2 * nbr)
+
+
+@pytest.mark.parametrize("prec,recon", [(1, 18), (1, 12), (2, 18), (2, 12)])
+def test_reduced_precision_link_storage_element_by_element(stag, prec, recon):
+    """The stored float / half links, read back one element at a time.
+
+    A unit source e_b at one site makes every output component of the
+    operator a single signed link element (products with 1.0, sums with 0:
+    exact in float), so the kernel's output is the stored link itself: the
+    columns b of the forward links into the site and the conjugated rows b of
+    its own links (Sec. 4.3 12-real storage: rows 0 and 1 stored, row 2
+    rebuilt).  Compared exactly with the oracle's encodings (round_f32,
+    round_f16, and for half the output's own per-site code); only the rebuilt
+    third row, formed in float by the kernel and in double by the oracle,
+    gets a rounding tolerance."""
+    dims = (4, 4, 6, 4)
+    U = li.random_links(dims, "smooth", eps=0.3, seed=361)
+    Vh = li.volume(dims) // 2
+    ctx = make_ctx(stag, dims, U)
+    out = ctx.new_half()
+    rnd = enc.round_f32 if prec == 1 else enc.round_f16
+    Us = rnd(U) if recon == 18 else enc.recon12(U, rnd)
+    for parity in (0, 1):
+        for h, b in ((0, 0), (37, 1), (Vh - 1, 2), (50, 2)):
+            psi = np.zeros((Vh, 3), complex)
+            psi[h, b] = 1.0
+            (ctx.dslash_eo if parity == 0 else ctx.dslash_oe)(out, dev(psi), prec, recon)
+            got = host(out)
+            ref = orc.dslash_half(dims, Us, psi, parity)
+            if prec == 2:
+                ref = enc.half_spinor(ref)
+            nz = np.abs(ref) > 0
+            assert nz.sum() >= 8 * 3 - 3      # eight neighbours, three colours each (row-2 zeros aside)
+            if recon == 18:
+                assert np.array_equal(got, ref)
+            else:
+                # exact where no rebuilt element enters; rebuilt ones within float rounding
+                # (half: a code can move by one unit of 2^-10 of the site's norm)
+                tol = 4 * 2.0 ** -24 if prec == 1 else 2.0 ** -10
+                site = np.abs(ref.view(np.float64)).reshape(-1, 6).max(axis=1)
+                err = np.abs((got - ref).view(np.float64)).reshape(-1, 6).max(axis=1)
+                assert np.all(err <= tol * site)
+                if prec == 1:
+                    # inexact only where the rebuilt row enters: colour 2 of the four
+                    # forward hops, and all of a backward hop's row when b == 2
+                    assert np.count_nonzero(got != ref) <= 4 + (12 if b == 2 else 0)
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 6), (8, 8, 8, 8)])

@@ -437,3 +437,92 @@ def test_half_spinor_code():
     assert np.all(back[7] == 0)
     # the largest component of each site is coded as exactly +-1
     assert np.allclose(np.abs(q.astype(np.float64)).max(axis=1)[n > 0], 1.0)
+
+
+# Round-to-nearest-even onto a binary grid with p significant bits, written
+# from the definition with integer arithmetic on exact power-of-two scalings
+# (independent of numpy's casts): quantum = 2^(e - p) for x = m 2^e with m in
+# [1/2, 1), never below qmin (the subnormal spacing of the target format).
+def _rne(x, p, qmin):
+    import math
+    if x == 0.0:
+        return 0.0
+    _, e = math.frexp(x)
+    quantum = max(math.ldexp(1.0, e - p), qmin)
+    q = x / quantum                      # exact: a power-of-two scaling
+    n = math.floor(q)
+    frac = q - n                         # exact: |q| < 2^(p+1)
+    if frac > 0.5 or (frac == 0.5 and n % 2 == 1):
+        n += 1
+    return n * quantum
+
+
+F32_QMIN = 2.0 ** -149
+F16_QMIN = 2.0 ** -24
+
+
+def _components(a):
+    return np.ascontiguousarray(a, dtype=np.complex128).view(np.float64).ravel()
+
+
+def test_round_f32_is_round_to_nearest_even_per_component():
+    """round_f32 (the stored value of every float link and spinor component)
+    equals round-to-nearest-even onto the 24-bit grid, real and imaginary
+    parts separately; the result is a float32 and within half an ulp."""
+    rng = np.random.default_rng(131)
+    z = li.gaussian(rng, (4000,)) * np.exp2(rng.uniform(-40, 40, 4000))
+    got = _components(enc.round_f32(z))
+    want = np.array([_rne(v, 24, F32_QMIN) for v in _components(z)])
+    assert np.array_equal(got, want)
+    assert np.array_equal(got, got.astype(np.float32).astype(np.float64))
+    import math
+    half_ulp = np.array([math.ldexp(1.0, math.frexp(v)[1] - 25) for v in _components(z)])
+    assert np.all(np.abs(got - _components(z)) <= half_ulp)
+    # the real and imaginary parts are not mixed up
+    w = np.array([1.0 + 2.0 ** -30 + 1j * (3.0 + 2.0 ** -20)])
+    assert np.array_equal(enc.round_f32(w), np.array([1.0 + 1j * (3.0 + 2.0 ** -20)]))
+
+
+def test_round_f32_ties_go_to_even():
+    one = 1.0
+    cases = {
+        one + 2.0 ** -24: one,                              # tie, even neighbour below
+        one + 3 * 2.0 ** -24: one + 2.0 ** -22,              # tie, even neighbour above
+        one + 2.0 ** -24 + 2.0 ** -50: one + 2.0 ** -23,     # just above the tie
+        -(one + 3 * 2.0 ** -24): -(one + 2.0 ** -22),        # sign symmetric
+    }
+    for x, y in cases.items():
+        assert enc.round_f32(np.array([complex(x, -x)]))[0] == complex(y, -y)
+        assert _rne(x, 24, F32_QMIN) == y
+
+
+def test_round_f16_rounds_through_float32_like_the_kernels():
+    """round_f16 is float64 -> float32 -> float16, each round-to-nearest-even
+    (the kernels receive float32 values and round them to half).  A value
+    just above a half-precision tie that float32 rounds onto the tie separates
+    this from a direct float64 -> float16 rounding."""
+    rng = np.random.default_rng(141)
+    z = li.gaussian(rng, (4000,)) * 0.5
+    z[:50] *= 2.0 ** -16                     # subnormal half codes
+    got = _components(enc.round_f16(z))
+    want = np.array([_rne(_rne(v, 24, F32_QMIN), 11, F16_QMIN) for v in _components(z)])
+    assert np.array_equal(got, want)
+    assert np.array_equal(got, got.astype(np.float16).astype(np.float64))
+    # ties in half precision go to even
+    assert _components(enc.round_f16(np.array([complex(1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11)]))).tolist() == \
+        [1.0, 1 + 2.0 ** -9]
+    # double rounding: float32 puts 1 + 2^-11 + 2^-40 on the half tie, which goes to 1
+    x = 1 + 2.0 ** -11 + 2.0 ** -40
+    assert _rne(x, 11, F16_QMIN) == 1 + 2.0 ** -10            # direct rounding would go up
+    assert enc.round_f16(np.array([complex(x, 0)]))[0] == 1.0
+
+
+def test_recon12_keeps_rounded_rows_and_rebuilds_the_third():
+    rng = np.random.default_rng(151)
+    U = li.smooth_su3(rng, 500, 0.3)
+    for rounding in (enc.round_f32, enc.round_f16):
+        R = enc.recon12(U, rounding)
+        assert np.array_equal(R[:, :2, :], rounding(U[:, :2, :]))
+        assert np.array_equal(R[:, 2, :], orc.reconstruct_row2(R))
+        # the rebuilt row is close to the original one (SU(3) links), not equal to a rounded copy
+        assert np.abs(R[:, 2, :] - U[:, 2, :]).max() <= 8 * 2.0 ** -11
