@@ -68,8 +68,10 @@ enum stag_prec {
     STAG_F64X = 3 /* double links and spinors (same bytes as STAG_F64), double-float arithmetic:
                      each double carried as hi + lo floats (48-bit significand) on the FP32 pipe,
                      whose rate on GB300 is 64x the FP64 one; 18-real links only.  Results agree
-                     with STAG_F64 to ~1e-14 relative; values below 2^-74 in magnitude keep only
-                     24 significant bits. */
+                     with STAG_F64 to ~1e-14 relative (2-norm) for fields of any double
+                     magnitude: inputs are normalised by exact powers of two on the device
+                     (largest component in [1, 2)) and results scaled back, and links whose
+                     largest element lies outside 2^-40 .. 2^40 are stored scaled the same way. */
 };
 
 /* Link compression (Sec. 4.3): 18 reals per link, or 12 (rows 0 and 1; row 2
@@ -211,7 +213,10 @@ typedef struct {
     int rhs_block;         /* batched solves: right-hand sides per operator pass; 0: autotune */
     int f64_arith;         /* arithmetic of the double-precision operator passes (stag_cg_solve,
                               the reliable updates of the mixed solver): STAG_F64 (IEEE double)
-                              or STAG_F64X (double-float) */
+                              or STAG_F64X (double-float; taken as STAG_F64 when the links lie
+                              outside the double-float range, see STAG_F64X).  Every solver
+                              solves for 2^-k b (largest component in [1, 2)) and returns
+                              2^k x, exactly, so any double-range b is served alike */
     int temporal_gauge;    /* double-precision CG with f64_arith = STAG_F64X: 1 solves in temporal
                               gauge (Sec. 4.3: the links of the time direction fixed to 1 except
                               on the last slice, 6 link reads per site instead of 8), M' x' = g b

@@ -202,6 +202,9 @@ int stag_destroy(stag_ctx ctx)
     if (ctx->tmp_lo_in) cudaFree(ctx->tmp_lo_in);
     if (ctx->tmp_lo_out) cudaFree(ctx->tmp_lo_out);
     if (ctx->full_tmp) cudaFree(ctx->full_tmp);
+    if (ctx->scale_bits) cudaFree(ctx->scale_bits);
+    if (ctx->scale_k) cudaFree(ctx->scale_k);
+    if (ctx->dfx_tmp) cudaFree(ctx->dfx_tmp);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return STAG_OK;

@@ -61,6 +61,7 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
         set_error("batched solver: unsupported inner precision %d / compression %d", prec, recon);
         return STAG_EUNSUPPORTED;
     }
+    if (prec != STAG_F64) STAG_TRY(check_float_inner_links(ctx));
     BatchSlot* mp = nullptr;
     STAG_TRY(ensure_batch(ctx, prec, recon, nrhs, &mp));
     BatchSlot& m = *mp;
@@ -68,7 +69,10 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
     const double delta = prec == STAG_F64 ? 0.0 : (prm.delta > 0 ? prm.delta : 0.1);
     const size_t vbytes = (size_t)nrhs * m.f64_stride;
-    STAG_CUDA_TRY(cudaMemcpyAsync(m.b, B, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    stag_solver_params prm2 = prm;
+    STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &prm2.f64_arith));
+    // B_k' = 2^-k_k B_k, each with its largest component in [1, 2); X_k = 2^k_k X_k'
+    STAG_TRY(normalise_fields(ctx, B, m.b, nrhs, (size_t)3 * ctx->g.Vh, SLOT_SOLVE, ctx->stream));
     const double* shifts_dev = nullptr;
     if (shifts_host) {
         STAG_CUDA_TRY(cudaMemcpyAsync(m.shifts, shifts_host, nrhs * sizeof(double), cudaMemcpyHostToDevice,
@@ -83,13 +87,13 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
     }
     if (nb == 0) STAG_TRY(multi_dslash(ctx, prec, recon, 1, m.t, m.p, nrhs, 0, &nb));
     int rc;
-    if (prec == STAG_F64) rc = batched_run_f64(ctx, m, recon, lk, X0, mass, shifts_dev, prm, delta, nb);
-    else if (prec == STAG_F32) rc = batched_run_f32(ctx, m, recon, lk, X0, mass, shifts_dev, prm, delta, nb);
-    else rc = batched_run_f16(ctx, m, recon, lk, X0, mass, shifts_dev, prm, delta, nb);
+    if (prec == STAG_F64) rc = batched_run_f64(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, nb);
+    else if (prec == STAG_F32) rc = batched_run_f32(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, nb);
+    else rc = batched_run_f16(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, nb);
     STAG_TRY(rc);
     std::vector<CgScalars> hs(nrhs);
     STAG_CUDA_TRY(cudaMemcpyAsync(hs.data(), m.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    STAG_CUDA_TRY(cudaMemcpyAsync(X, m.x_hi, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    STAG_TRY(scale_fields_out(ctx, m.x_hi, X, nrhs, (size_t)3 * ctx->g.Vh, SLOT_SOLVE, 1, ctx->stream));
     STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     int status = STAG_OK;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

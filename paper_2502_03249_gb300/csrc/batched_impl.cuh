@@ -103,10 +103,12 @@ __device__ __forceinline__ unsigned mask_updating(const BatchScal& b, int k0)
 
 // x_hi = x0 (or 0), xlo = 0, rr0 = |b|^2 per system; every system marked for a
 // residual recomputation.  grid (gx, nrhs).
+// b holds the normalised right-hand sides 2^-k_k B_k; x0 (unnormalised
+// initial guesses) is brought to the same scale.
 template <class SX>
 __global__ void __launch_bounds__(BBS) k_b_init(int Vh, const double2* b, const double2* x0, double2* x_hi, SX xlo,
                                                 size_t sx_stride, BatchScal bs, double tol, int maxiter, double m2,
-                                                const double* shifts, double delta)
+                                                const double* shifts, double delta, const int* kexp)
 {
     __shared__ double red[BBS / 32];
     __shared__ bool last;
@@ -120,7 +122,12 @@ __global__ void __launch_bounds__(BBS) k_b_init(int Vh, const double2* b, const 
             const double2 bv = b[o + c];
             d = fma(bv.x, bv.x, d);
             d = fma(bv.y, bv.y, d);
-            x_hi[o + c] = x0 ? x0[o + c] : make_double2(0.0, 0.0);
+            if (x0) {
+                const double2 v = x0[o + c];
+                x_hi[o + c] = make_double2(scalbn(v.x, -kexp[k]), scalbn(v.y, -kexp[k]));
+            } else {
+                x_hi[o + c] = make_double2(0.0, 0.0);
+            }
             z.c[c].re = z.c[c].im = 0;
         }
         xlo.at(k, sx_stride).store(h, z);
@@ -483,7 +490,7 @@ struct BatchPlan {
         const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
         const dim3 gb(m.gx, m.nrhs), g1(m.gx, 1);
         k_b_init<SX><<<gb, BBS, 0, s>>>(g.Vh, m.b, x0, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs, tol, maxiter,
-                                        mass * mass, shifts_dev, delta);
+                                        mass * mass, shifts_dev, delta, ctx->scale_k + SLOT_SOLVE);
         k_b_hop<LF64, SD64, NB64, 1><<<g1, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
         k_b_resid64<LF64, SD64, NB64><<<g1, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
         k_b_finish<S><<<g1, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 1, 0, 0);

@@ -130,8 +130,8 @@ struct F64Plan {
     {
         Workspace* ws = ctx->ws;
         const int Vh = ctx->g.Vh;
-        STAG_CUDA_TRY(cudaMemcpyAsync(ws->b, b_in, (size_t)3 * Vh * sizeof(double2), cudaMemcpyDeviceToDevice,
-                                      ctx->stream));
+        // b' = 2^-k b with its largest component in [1, 2); x = 2^k x' at the end
+        STAG_TRY(normalise_fields(ctx, b_in, ws->b, 1, (size_t)3 * Vh, SLOT_SOLVE, ctx->stream));
         k_cg_start_f64<BLAS_BS><<<nblk(Vh, BLAS_BS), BLAS_BS, 0, ctx->stream>>>(
             Vh, ws->b, ws->x, ws->r, ws->p, ws->sc, tol, maxiter, mass * mass, sigma, ctx->partials, ctx->counters);
         STAG_CUDA_TRY(cudaGetLastError());
@@ -167,9 +167,7 @@ struct F64Plan {
     }
     static int finish(stag_ctx ctx, double2* x_out)
     {
-        STAG_CUDA_TRY(cudaMemcpyAsync(x_out, ctx->ws->x, (size_t)3 * ctx->g.Vh * sizeof(double2),
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
-        return STAG_OK;
+        return scale_fields_out(ctx, ctx->ws->x, x_out, 1, (size_t)3 * ctx->g.Vh, SLOT_SOLVE, 1, ctx->stream);
     }
 };
 
@@ -204,9 +202,10 @@ struct DFPlanT {
         Workspace* ws = ctx->ws;
         const int Vh = ctx->g.Vh;
         STAG_TRY(decide_df_dir(ctx));
-        // b stays double: the true residual is formed against it
-        STAG_CUDA_TRY(cudaMemcpyAsync(ws->b, b_in, (size_t)3 * Vh * sizeof(double2), cudaMemcpyDeviceToDevice,
-                                      ctx->stream));
+        // b stays double (the true residual is formed against it), normalised to
+        // b' = 2^-k b with its largest component in [1, 2): every vector of the
+        // solve then lies well inside the double-float range
+        STAG_TRY(normalise_fields(ctx, b_in, ws->b, 1, (size_t)3 * Vh, SLOT_SOLVE, ctx->stream));
         k_dfcg_start<BLAS_BS><<<nblk(Vh, BLAS_BS), BLAS_BS, 0, ctx->stream>>>(
             Vh, ws->b, v(ws->x), v(ws->r), v(ws->p), ws->sc, tol, maxiter, mass * mass, sigma, ctx->partials,
             ctx->counters);
@@ -248,7 +247,8 @@ struct DFPlanT {
     }
     static int finish(stag_ctx ctx, double2* x_out)
     {
-        return convert_lo_to_f64(ctx, STAG_F64X, ctx->ws->x, x_out, 1, ctx->stream);
+        return join_fields_scaled(ctx, reinterpret_cast<const float4*>(ctx->ws->x), x_out, 1, (size_t)3 * ctx->g.Vh,
+                                  SLOT_SOLVE, 1, 0, ctx->stream);
     }
 };
 
@@ -377,7 +377,13 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
 {
     const auto t0 = std::chrono::steady_clock::now();
     STAG_TRY(ensure_cg_f64(ctx));
-    if (prm.f64_arith == STAG_F64X && prm.temporal_gauge) {
+    if (prm.temporal_gauge && prm.f64_arith != STAG_F64X) {
+        set_error("temporal_gauge needs f64_arith = STAG_F64X");
+        return STAG_EINVAL;
+    }
+    int arith = STAG_F64;
+    STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &arith));
+    if (arith == STAG_F64X && prm.temporal_gauge) {
         // M x = b as M' x' = g b, x = g^dagger x' (same residual norm: g is unitary)
         const double2* G = nullptr;
         const float4* lk = nullptr;
@@ -391,20 +397,14 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
         STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         return rc;
     }
-    if (prm.temporal_gauge) {
-        set_error("temporal_gauge needs f64_arith = STAG_F64X");
-        return STAG_EINVAL;
-    }
-    if (prm.f64_arith == STAG_F64X) {
+    if (arith == STAG_F64X) {
         const void* lk = nullptr;
         STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lk));
         const LinkFieldDF<18> U{(const float4*)lk, ctx->g.Vh};
         return cg_solve_plan<DFPlan>(ctx, U, x_out, b_in, mass, sigma, prm, st, t0);
     }
-    if (prm.f64_arith != STAG_F64) {
-        set_error("f64_arith must be STAG_F64 or STAG_F64X");
-        return STAG_EINVAL;
-    }
+    // IEEE double: requested, or links outside the double-float range (the
+    // temporal-gauge path needs unitary links, which never are)
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
     const LF64 U{(const double2*)lk, ctx->g.Vh};

@@ -30,6 +30,14 @@ void set_error(const char* fmt, ...);
         if (rc_ < 0) return rc_;    \
     } while (0)
 
+// Exponent slots of the field normalisation (scale.cu): the solve's own
+// right-hand sides, an outer solver's (multi-shift) right-hand side, the
+// operator entry points' inputs, and the gauge field.
+constexpr int SCALE_SLOTS = 200;
+constexpr int SLOT_SOLVE = 0, SLOT_OUTER = 64, SLOT_OPER = 128, SLOT_LINKS = SCALE_SLOTS - 1;
+constexpr int DF_LINK_SAFE_EXP = 40;
+constexpr int FLOAT_INNER_LINK_EXP = 20;
+
 // Index of a (precision, compression) link copy.
 inline int link_slot(int prec, int recon) { return prec * 2 + (recon == 12 ? 1 : 0); }   // 0..7
 
@@ -92,6 +100,18 @@ struct stag_ctx_s {
     int repeat_done;           // tmp_lo_out holds a stag_dslash_repeat result of those fields
     void* tune;                // autotuner cache (tune.cu)
     int last_rhs_block;        // right-hand sides per pass chosen by the last batched solve
+    // power-of-two normalisation of fields (scale.cu): largest-magnitude bits
+    // and exponents per field, SCALE_SLOTS of each
+    unsigned long long* scale_bits;
+    int* scale_k;
+    // double-float links hold 2^-df_link_exp U: 0 for links whose largest
+    // element lies within 2^-40 .. 2^40, else that element's exponent (and the
+    // double-precision solvers then use IEEE double arithmetic)
+    int df_link_exp;
+    int link_exp;              // exponent of the largest link element (valid if link_exp_known)
+    bool link_exp_known;       // cleared by every upload
+    void* dfx_tmp;             // double-float operator on canonical fields: input and output storage
+    size_t dfx_tmp_bytes;
 };
 
 namespace stag {
@@ -115,7 +135,28 @@ int launch_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void*
                            cudaStream_t s);
 int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs,
                           int nb, int* nb_used);
+int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int nb,
+                          int* nb_used, cudaStream_t s);
 int ensure_tg(stag_ctx ctx, const double2** G, const float4** links);
+
+// scale.cu
+int ensure_scale_scratch(stag_ctx ctx);
+int field_exponents(stag_ctx ctx, const double2* v, int nfield, size_t field_elems, int slot, cudaStream_t s);
+int scale_fields_in(stag_ctx ctx, const double2* in, double2* out, int nfield, size_t field_elems, int slot,
+                    int kstride, cudaStream_t s);
+int scale_fields_out(stag_ctx ctx, const double2* in, double2* out, int nfield, size_t field_elems, int slot,
+                     int kstride, cudaStream_t s);
+int normalise_fields(stag_ctx ctx, const double2* in, double2* out, int nfield, size_t field_elems, int slot,
+                     cudaStream_t s);
+int split_fields_scaled(stag_ctx ctx, const double2* in, float4* out, int nfield, size_t field_elems, int slot,
+                        int extra, cudaStream_t s);
+int join_fields_scaled(stag_ctx ctx, const float4* in, double2* out, int nfield, size_t field_elems, int slot,
+                       int kstride, int extra, cudaStream_t s);
+int link_max_exponent(stag_ctx ctx, int* out);
+int check_float_inner_links(stag_ctx ctx);
+// The arithmetic a double-precision pass really uses: STAG_F64X unless the
+// double-float links are scaled (links outside the double-float range).
+int resolve_f64_arith(stag_ctx ctx, int requested, int* out);
 int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int dagger);
 
 }  // namespace stag

@@ -36,10 +36,7 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
         if (recon == 18) return run_dslash(ctx, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, par_out, s);
         return run_dslash(ctx, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, par_out, s);
     }
-    if (prec == STAG_F64X) {
-        SpinorF64asDF si{(double2*)in}, so{(double2*)out};
-        return run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, Vh}, si, so, par_out, s);
-    }
+    if (prec == STAG_F64X) return dslash_f64x_canonical(ctx, par_out, (double2*)out, (const double2*)in, 1, 1, nullptr, s);
     if (prec == STAG_F32) {
         SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
         if (recon == 18) return run_dslash(ctx, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, par_out, s);
@@ -52,6 +49,52 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
     }
     set_error("unsupported precision %d", prec);
     return STAG_EUNSUPPORTED;
+}
+
+// Scratch of the double-float operator on canonical fields: nfield input and
+// nfield output fields of double-float pairs (48 bytes per site each).
+static int ensure_dfx_tmp(stag_ctx ctx, int nfield, float4** in, float4** out)
+{
+    const size_t per = lo_spinor_bytes(ctx->g, STAG_F64X);
+    const size_t bytes = 2 * per * (size_t)nfield;
+    if (ctx->dfx_tmp_bytes < bytes) {
+        if (ctx->dfx_tmp) cudaFree(ctx->dfx_tmp);
+        ctx->dfx_tmp = nullptr;
+        ctx->dfx_tmp_bytes = 0;
+        STAG_CUDA_TRY(cudaMalloc(&ctx->dfx_tmp, bytes));
+        ctx->dfx_tmp_bytes = bytes;
+    }
+    *in = (float4*)ctx->dfx_tmp;
+    *out = (float4*)((char*)ctx->dfx_tmp + per * (size_t)nfield);
+    return STAG_OK;
+}
+
+// out_k = D_{par_out, 1-par_out} in_k (k < nfield) on canonical complex128
+// fields in double-float arithmetic, accurate over the whole double range:
+// each field is scaled by an exact power of two into double-float storage,
+// the operator runs on that storage (the multi-vector kernel with rhs_block nb
+// for nfield > 1), and the result is scaled back by the field's exponent and
+// the links' (scale.cu).  The largest component is put at 2^60, high in the
+// float range (outputs stay below 2^61 * 48 * 2^41 < 2^127), so that
+// components down to 2^-134 of it keep their full 48 bits as well.
+constexpr int DFX_TOP = 60;
+int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int nb,
+                          int* nb_used, cudaStream_t s)
+{
+    const void* lk = nullptr;
+    STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lk));
+    float4 *ti = nullptr, *to = nullptr;
+    STAG_TRY(ensure_dfx_tmp(ctx, nfield, &ti, &to));
+    const size_t elems = (size_t)3 * ctx->g.Vh;
+    STAG_TRY(field_exponents(ctx, in, nfield, elems, SLOT_OPER, s));
+    STAG_TRY(split_fields_scaled(ctx, in, ti, nfield, elems, SLOT_OPER, -DFX_TOP, s));
+    if (nfield == 1) {
+        STAG_TRY(run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh}, SpinorDF{ti}, SpinorDF{to}, par_out, s));
+        if (nb_used) *nb_used = 1;
+    } else {
+        STAG_TRY(multi_dslash_internal(ctx, STAG_F64X, 18, par_out, to, ti, nfield, nb, nb_used));
+    }
+    return join_fields_scaled(ctx, to, out, nfield, elems, SLOT_OPER, 1, ctx->df_link_exp - DFX_TOP, s);
 }
 
 // The operator on a precision's internal storage: as launch_dslash, except

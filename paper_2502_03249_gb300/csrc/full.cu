@@ -85,6 +85,38 @@ static int full_buffers(stag_ctx ctx, double2** bufs)
     return STAG_OK;
 }
 
+// out = a x + c y (double vectors)
+__global__ void k_axpby(long long n, const double2* x, const double2* y, double2* out, double a, double c)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 xv = x[i], yv = y[i];
+    out[i] = make_double2(fma(a, xv.x, c * yv.x), fma(a, xv.y, c * yv.y));
+}
+
+static int axpby(stag_ctx ctx, const double2* x, const double2* y, double2* out, double a, double c)
+{
+    const long long n = 3LL * ctx->g.Vh;
+    k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, x, y, out, a, c);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+// The Schur steps with the double-float operator on canonical fields (which
+// normalises its input, so any scale of b is served): the operator result
+// goes to the output buffer first, then the axpby.
+static int schur_pre_df(stag_ctx ctx, double2* const* B, double mass)
+{
+    STAG_TRY(dslash_f64x_canonical(ctx, 0, B[2], B[1], 1, 1, nullptr, ctx->stream));   // D_eo b_o
+    return axpby(ctx, B[0], B[2], B[2], mass, -1.0);                                   // m b_e - D_eo b_o
+}
+
+static int schur_post_df(stag_ctx ctx, double2* const* B, double2* psi_o, double mass)
+{
+    STAG_TRY(dslash_f64x_canonical(ctx, 1, psi_o, B[3], 1, 1, nullptr, ctx->stream));   // D_oe psi_e
+    return axpby(ctx, B[1], psi_o, psi_o, 1.0 / mass, -1.0 / mass);                      // (b_o - D_oe psi_e)/m
+}
+
 template <class LF, class SD>
 static int schur_pre(stag_ctx ctx, const LF& U, double2* const* B, double mass)
 {
@@ -132,17 +164,19 @@ extern "C" int stag_solve_full(stag_ctx ctx, double* psi, const double* b, doubl
     const unsigned grid = (unsigned)((2LL * g.Vh + 255) / 256);
     k_split_full<<<grid, 256, 0, ctx->stream>>>(g, (const double2*)b, B[0], B[1]);
     STAG_CUDA_TRY(cudaGetLastError());
-    const bool dfx = prm.f64_arith == STAG_F64X;
+    int arith = STAG_F64;
+    STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &arith));
+    const bool dfx = arith == STAG_F64X;
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, dfx ? STAG_F64X : STAG_F64, 18, &lk));
-    if (dfx) STAG_TRY((schur_pre<LinkFieldDF<18>, SpinorF64asDF>(ctx, LinkFieldDF<18>{(const float4*)lk, g.Vh}, B, mass)));
+    STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
+    if (dfx) STAG_TRY(schur_pre_df(ctx, B, mass));
     else STAG_TRY((schur_pre<LinkField<double2, 18>, SpinorF64>(ctx, LinkField<double2, 18>{(const double2*)lk, g.Vh}, B, mass)));
     const int rc = prm.inner_prec == STAG_F64 ? cg_solve_f64(ctx, B[3], B[2], mass, 0.0, prm, stats)
                                               : cg_solve_mixed(ctx, B[3], B[2], mass, prm, stats);
     if (rc < 0) return rc;
     // psi_o goes to the odd-parity scratch slot of B[0] (b_e is no longer needed)
     double2* psi_o = B[0];
-    if (dfx) STAG_TRY((schur_post<LinkFieldDF<18>, SpinorF64asDF>(ctx, LinkFieldDF<18>{(const float4*)lk, g.Vh}, B, psi_o, mass)));
+    if (dfx) STAG_TRY(schur_post_df(ctx, B, psi_o, mass));
     else STAG_TRY((schur_post<LinkField<double2, 18>, SpinorF64>(ctx, LinkField<double2, 18>{(const double2*)lk, g.Vh}, B, psi_o, mass)));
     k_join_full<<<grid, 256, 0, ctx->stream>>>(g, B[3], psi_o, (double2*)psi);
     STAG_CUDA_TRY(cudaGetLastError());

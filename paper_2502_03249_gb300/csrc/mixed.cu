@@ -14,6 +14,7 @@
 // Graph:  while (W) { hop; Mp_dot; update; if (I) { accum_x; hop64; resid64; finish } p }
 #include <chrono>
 #include <new>
+#include <type_traits>
 
 #include "cg_kernels.cuh"
 #include "df64.cuh"
@@ -240,14 +241,15 @@ struct MixedPlan {
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
         const void* lk64 = nullptr;
-        const int p64 = prm.f64_arith == STAG_F64X ? STAG_F64X : STAG_F64;
+        const int p64 = std::is_same<typename LF64T::real, DF>::value ? STAG_F64X : STAG_F64;
         STAG_TRY(ensure_links(ctx, p64, 18, &lk64));
         const LF U{(const typename LF::store*)lk, g.Vh};
         const LF64T U64{(const typename LF64T::store*)lk64, g.Vh};
-        const size_t bytes = (size_t)3 * g.Vh * sizeof(double2);
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
         const double delta = prm.delta > 0 ? prm.delta : 0.1;
-        STAG_CUDA_TRY(cudaMemcpyAsync(ws->b, b_in, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        // b' = 2^-k b (largest component in [1, 2)): the float / half inner
+        // storage and the double-float passes stay in range for any b; x = 2^k x'
+        STAG_TRY(normalise_fields(ctx, b_in, ws->b, 1, (size_t)3 * g.Vh, SLOT_SOLVE, ctx->stream));
         k_mixed_start<S, SX, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, ctx->stream>>>(
             g.Vh, ws->b, ws->x, ws->r, m.template spinor<S>(m.r), m.template spinor<S>(m.p),
             m.template spinor<SX>(m.xlo), m.sc, prm.tol, maxiter, mass * mass, delta, ctx->partials, ctx->counters);
@@ -279,7 +281,7 @@ struct MixedPlan {
         }
         CgScalars* hs = ws->sc_host;
         STAG_CUDA_TRY(cudaMemcpyAsync(hs, m.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
-        STAG_CUDA_TRY(cudaMemcpyAsync(x_out, ws->x, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        STAG_TRY(scale_fields_out(ctx, ws->x, x_out, 1, (size_t)3 * g.Vh, SLOT_SOLVE, 1, ctx->stream));
         STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         int status = STAG_OK;
         if (hs->status == STAG_BREAKDOWN) status = STAG_BREAKDOWN;
@@ -347,15 +349,14 @@ int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mas
         set_error("mixed solver: inner_prec must be STAG_F32 or STAG_F16 and inner_recon 18 or 12");
         return STAG_EUNSUPPORTED;
     }
+    STAG_TRY(check_float_inner_links(ctx));
     MixedSlot* m = nullptr;
     STAG_TRY(ensure_mixed(ctx, prec, recon, &m));
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
-    if (prm.f64_arith == STAG_F64X) return dispatch_inner<LinkFieldDF<18>, SpinorF64asDF>(ctx, *m, lk, x_out, b_in, mass, prm, st);
-    if (prm.f64_arith != STAG_F64) {
-        set_error("f64_arith must be STAG_F64 or STAG_F64X");
-        return STAG_EINVAL;
-    }
+    int arith = STAG_F64;
+    STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &arith));
+    if (arith == STAG_F64X) return dispatch_inner<LinkFieldDF<18>, SpinorF64asDF>(ctx, *m, lk, x_out, b_in, mass, prm, st);
     return dispatch_inner<LinkField<double2, 18>, SpinorF64>(ctx, *m, lk, x_out, b_in, mass, prm, st);
 }
 

@@ -146,7 +146,10 @@ int stag_dslash_multi(stag_ctx ctx, double* out, const double* in, int nrhs, int
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
-    if (prec == STAG_F64 || prec == STAG_F64X) return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr);
+    if (prec == STAG_F64) return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr);
+    if (prec == STAG_F64X)
+        return dslash_f64x_canonical(ctx, out_parity, (double2*)out, (const double2*)in, nrhs,
+                                     rhs_block ? rhs_block : 0, nullptr, ctx->stream);
     const size_t lo = lo_spinor_bytes(ctx->g, prec) * nrhs;
     STAG_TRY(ensure_lo_tmp_public(ctx, lo));
     STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, nrhs, ctx->stream));

@@ -292,6 +292,7 @@ int multishift_solve(stag_ctx ctx, double2* X, const double2* b, const double* s
     const auto t0 = std::chrono::steady_clock::now();
     const int prec = prm.inner_prec == STAG_F64 ? STAG_F64 : STAG_F32;
     const int recon = prm.inner_recon == 18 ? 18 : 12;
+    if (prec != STAG_F64) STAG_TRY(check_float_inner_links(ctx));
     if (!ctx->ws) {
         ctx->ws = new (std::nothrow) Workspace();
         if (!ctx->ws) return STAG_ENOMEM;
@@ -323,26 +324,32 @@ int multishift_solve(stag_ctx ctx, double2* X, const double2* b, const double* s
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
     const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
+    // b' = 2^-k b (largest component in [1, 2)) in the first replica: the Krylov
+    // phase and the refinement solve for b', the solutions are scaled by 2^k
+    // at the end
+    const size_t fbytes = (size_t)g.Vh * 3 * sizeof(double2);
+    STAG_TRY(normalise_fields(ctx, b, m.brep, 1, (size_t)3 * g.Vh, SLOT_OUTER, ctx->stream));
+    const double2* bn = m.brep;
     // the Krylov phase stops at the inner precision's reach; refinement does the rest
     const double tol1 = prec == STAG_F64 ? prm.tol : (prm.tol > 1e-6 ? prm.tol : 1e-6);
     if (prec == STAG_F64) {
-        if (recon == 18) STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 18>>::run(ctx, m, lk, b, mass, m.shifts, tol1, maxiter, prm)));
-        else STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 12>>::run(ctx, m, lk, b, mass, m.shifts, tol1, maxiter, prm)));
+        if (recon == 18) STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 18>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
+        else STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 12>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
     } else {
-        if (recon == 18) STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 18>>::run(ctx, m, lk, b, mass, m.shifts, tol1, maxiter, prm)));
-        else STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 12>>::run(ctx, m, lk, b, mass, m.shifts, tol1, maxiter, prm)));
+        if (recon == 18) STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 18>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
+        else STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 12>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
     }
     CgScalars hs;
     STAG_CUDA_TRY(cudaMemcpyAsync(&hs, m.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
-    // shifted solutions -> double initial guesses; b replicated per system
-    const size_t fbytes = (size_t)g.Vh * 3 * sizeof(double2);
+    // shifted solutions -> double initial guesses; b' replicated per system
     if (prec == STAG_F64) {
         STAG_CUDA_TRY(cudaMemcpyAsync(X, m.X, nshift * fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     } else {
         STAG_TRY(convert_lo_to_f64(ctx, prec, m.X, X, nshift, ctx->stream));
     }
-    for (int i = 0; i < nshift; ++i)
-        STAG_CUDA_TRY(cudaMemcpyAsync((char*)m.brep + i * fbytes, b, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int i = 1; i < nshift; ++i)
+        STAG_CUDA_TRY(cudaMemcpyAsync((char*)m.brep + i * fbytes, m.brep, fbytes, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
     STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     const int ms_iters = hs.iter;
     if (hs.status == STAG_BREAKDOWN) {
@@ -354,6 +361,8 @@ int multishift_solve(stag_ctx ctx, double2* X, const double2* b, const double* s
     p2.maxiter = maxiter > ms_iters ? maxiter - ms_iters : 1;
     const int rc = batched_solve(ctx, X, (const double2*)m.brep, nshift, mass, shifts, X, p2, stats);
     if (rc < 0) return rc;
+    STAG_TRY(scale_fields_out(ctx, X, X, nshift, (size_t)3 * g.Vh, SLOT_OUTER, 0, ctx->stream));
+    STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     if (stats) {
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int i = 0; i < nshift; ++i) {

@@ -65,15 +65,17 @@ __global__ void k_derive_links_vec(int Vh, const double2* __restrict__ in, char*
     C::store(out + (size_t)pm * C::BYTES * Vh, Vh, (int)h, w);
 }
 
-// internal F64/18 -> double-float split (hi = RN(x), lo = RN(x - hi)) per real.
-__global__ void k_split_links(int Vh, const double2* __restrict__ in, float4* __restrict__ out)
+// internal F64/18 -> double-float split (hi = RN(x), lo = RN(x - hi)) per real
+// of x = 2^-e U (e = 0 unless the links lie outside the double-float range).
+__global__ void k_split_links(int Vh, const double2* __restrict__ in, float4* __restrict__ out, int e)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (par, mu, h)
     if (idx >= 8LL * Vh) return;
     const long long pm = idx / Vh, h = idx - pm * Vh;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        const double2 v = in[(pm * 9 + k) * Vh + h];
+        double2 v = in[(pm * 9 + k) * Vh + h];
+        if (e) v = make_double2(scalbn(v.x, -e), scalbn(v.y, -e));
         const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
         out[(pm * 9 + k) * Vh + h] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih,
                                                  __double2float_rn(v.y - (double)ih));
@@ -94,6 +96,7 @@ int upload_gauge(stag_ctx ctx, const double* U, int on_device)
     // their next use: CUDA graphs captured by the solvers hold these pointers.
     for (int s = 1; s < 8; ++s) ctx->link_stale[s] = ctx->links[s] != nullptr;
     ctx->tg_stale = true;
+    ctx->link_exp_known = false;
     if (!ctx->links[0]) {
         STAG_CUDA_TRY(cudaMalloc(&ctx->links[0], n * sizeof(double2)));
         ctx->link_bytes[0] = n * sizeof(double2);
@@ -130,7 +133,18 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
         const unsigned grid = (unsigned)((work + BS - 1) / BS);
         const double2* src = (const double2*)ctx->links[0];
         const int Vh = ctx->g.Vh;
-        if (prec == STAG_F64X) k_split_links<<<grid, BS, 0, ctx->stream>>>(Vh, src, (float4*)p);
+        if (prec == STAG_F64X) {
+            // links whose largest element leaves the double-float range are
+            // stored as 2^-e U (operator results scaled back by 2^e)
+            int e = 0;
+            const int rc = link_max_exponent(ctx, &e);
+            if (rc < 0) {
+                if (!ctx->links[slot]) cudaFree(p);   // allocated just above
+                return rc;
+            }
+            ctx->df_link_exp = (e > DF_LINK_SAFE_EXP || e < -DF_LINK_SAFE_EXP) ? e : 0;
+            k_split_links<<<grid, BS, 0, ctx->stream>>>(Vh, src, (float4*)p, ctx->df_link_exp);
+        }
         else if (prec == STAG_F64) k_derive_links_f64_12<<<grid, BS, 0, ctx->stream>>>(Vh, src, (double2*)p);
         else if (prec == STAG_F32 && NE == 9) k_derive_links_vec<8, 9><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
         else if (prec == STAG_F32) k_derive_links_vec<8, 6><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
@@ -142,6 +156,21 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
         ctx->link_stale[slot] = false;
     }
     *out = ctx->links[slot];
+    return STAG_OK;
+}
+
+int resolve_f64_arith(stag_ctx ctx, int requested, int* out)
+{
+    if (requested != STAG_F64 && requested != STAG_F64X) {
+        set_error("f64_arith must be STAG_F64 or STAG_F64X");
+        return STAG_EINVAL;
+    }
+    if (requested == STAG_F64X) {
+        const void* lk = nullptr;
+        STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lk));
+        if (ctx->df_link_exp != 0) requested = STAG_F64;
+    }
+    *out = requested;
     return STAG_OK;
 }
 
