@@ -1,24 +1,27 @@
 """Benchmark of the staggered Dslash and even-odd CG path on GB300.
 
-Headline step (one GPU): the 32^3 x 8 lattice, smooth links exp(0.3 i H),
-m = 0.01, Gaussian source.  One step is a complete double-precision CG solve
-of M x = b to a true relative residual of 1e-10 -- every half-Dslash
-application, the BLAS and reductions, the device-side iteration loop -- with
-the inputs resident in HBM and L2 flushed before every step.  The operator
-passes use the library's default double-precision arithmetic (double storage,
-double-float arithmetic on the FP32 pipe; IEEE-double passes are timed beside
-it).
+Headline step (one GPU): the 48^3 x 12 lattice, smooth links exp(0.2 i H),
+m = 0.002, Gaussian source.  One step is a complete double-precision CG solve
+of M x = b in IEEE double arithmetic (double links, vectors and FP64
+operations: the paper's "DP" CG, Sec. 4.2 and Table 1) to a true relative
+residual of 1e-10 -- every half-Dslash application, the BLAS and reductions,
+the device-side iteration loop -- with the inputs resident in HBM and L2
+flushed before every step.
 
 Printed value: Dslash GFLOP/s sustained over the solve = 570 flop x V/2 sites
 x (half-Dslash applications in the solve) / solve time (the paper's 570
-flop/site count, Sec. 4.3).  Further keys: CG time-to-solution, the Dslash
-kernel against its roofline, an end-to-end number through the C ABI with host
-buffers, mixed-precision, batched multi-RHS, multi-shift and force results on
-the workloads that name them, and the CPU oracle timed on the host cores.
+flop/site count, Sec. 4.3); ms_per_step is the CG time-to-solution.  Beside it,
+on the same workload and source: the double-float CG (double storage, FP32-pipe
+arithmetic), the same in temporal gauge, and the mixed-precision solves (float
+and half 12-real inner iterations with double reliable updates), each with its
+speed-up over the IEEE solve; the operator kernels against their rooflines (the
+IEEE operator against the FP64 FMA peak and against HBM); an end-to-end number
+through the C ABI with host buffers; batched multi-RHS, multi-shift, force and
+32^3 x 8 sections; the CPU oracle timed on the host cores.
 
-``--impl reference`` times the CPU oracle on the same workload (bounded
-samples: a few CG iterations per step) and prints the same line with
-"impl": "reference".
+``--impl reference`` times the CPU oracle (its OpenMP build, every host core)
+on the same workload (bounded samples: a few CG iterations per step) and prints
+the same line with "impl": "reference".
 
 Multi-GPU (torchrun): every rank solves its own right-hand side (independent
 problems, weak scaling, no collective on the data path); the step time is the
@@ -44,7 +47,7 @@ import lattice_inputs as li  # noqa: E402
 
 METRIC = "Dslash GFLOP/s + HBM roofline frac; CG time-to-solution FP64 vs mixed/multi-RHS"
 FLOP_PER_SITE = 570            # Sec. 4.3: per output site of one half-Dslash
-WORKLOAD_INDEX = 1             # 32^3 x 8 smooth eps=0.3, m=0.01
+WORKLOAD_INDEX = 2             # 48^3 x 12 smooth eps=0.2, m=0.002
 TOL = 1e-10
 L2_FLUSH_BYTES = 512 << 20     # larger than the 129 MB L2
 SHIFTS12 = [10.0 ** (-5 + 5 * i / 11) for i in range(12)]
@@ -194,7 +197,8 @@ def dist_setup():
 # ---------------------------------------------------------------- reference
 
 def run_reference(args, ws, rank):
-    """The CPU oracle as it stands (single thread), bounded CG samples per step."""
+    """The CPU oracle as it stands (its OpenMP build on every host core),
+    bounded CG samples per step on the headline workload."""
     if rank != 0:
         return 0
     import oracle as orc
@@ -205,58 +209,78 @@ def run_reference(args, ws, rank):
     Vh = li.volume(dims) // 2
     iters_per_step = 2
 
-    def step():
-        t0 = time.perf_counter()
-        _, it, _, _ = orc.cg(dims, U, mass, b, tol=TOL, maxiter=iters_per_step)
-        dt = time.perf_counter() - t0
-        return dt, 2 * (it + 1)      # two half-Dslashes per M; one more M for the true residual
+    with orc.threads():
+        cores = orc.num_threads()
 
-    for _ in range(args.warmup):
-        step()
-    tot_t, tot_h = 0.0, 0
-    for _ in range(args.steps):
-        dt, nh = step()
-        tot_t += dt
-        tot_h += nh
+        def step():
+            t0 = time.perf_counter()
+            _, it, _, _ = orc.cg(dims, U, mass, b, tol=TOL, maxiter=iters_per_step)
+            dt = time.perf_counter() - t0
+            return dt, 2 * (it + 1)      # two half-Dslashes per M; one more M for the true residual
+
+        for _ in range(args.warmup):
+            step()
+        tot_t, tot_h = 0.0, 0
+        for _ in range(args.steps):
+            dt, nh = step()
+            tot_t += dt
+            tot_h += nh
     gflops = FLOP_PER_SITE * Vh * tot_h / tot_t * 1e-9
-    sample = f"oracle CG on {dims}, {iters_per_step} iterations + true residual per step"
+    sample = (f"oracle CG on {dims}, {iters_per_step} iterations + true residual per step, OpenMP build on "
+              f"{cores} host threads ({cpu_model()})")
     line = {
         "impl": "reference", "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": headline_config(w),
-        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def headline_config(w):
     """The benchmark step's workload, the same dict in both arms' lines."""
     return {
-        "workload": w["name"] + ", double-precision CG to true residual 1e-10 (one solve per step)",
-        "dims": list(w["dims"]), "mass": w["mass"], "links": "exp(0.3 i H), 18-real double", "tol": TOL,
-        "l2": "GPU arm: flushed (512 MB write, then 512 MB read) before every step; working set 151 MB links "
-              "+ 6 MB per vector",
+        "workload": w["name"] + ", IEEE double CG to true residual 1e-10 (one solve per step)",
+        "dims": list(w["dims"]), "mass": w["mass"], "links": f"exp({w['eps']} i H), 18-real double", "tol": TOL,
+        "arithmetic": "IEEE double (links, vectors, operator, BLAS, reductions)",
+        "l2": "GPU arm: flushed (512 MB write, then 512 MB read) before every step; working set 764 MB links "
+              "+ 32 MB per vector (larger than L2)",
         "value_definition": "570 flop x V/2 x half-Dslash applications per solve / solve time",
     }
 
 
 def cpu_baseline_sample(dims, U, b, mass, Vh, budget_s=12.0):
-    """Oracle timed on the host (single thread) on a bounded sample of the workload."""
+    """Oracle timed on the host cores (its OpenMP build) on a bounded sample of
+    the workload: whole CG runs of 2 iterations plus the true residual."""
     import oracle as orc
-    t0 = time.perf_counter()
-    n_half = 0
-    its = 0
-    while time.perf_counter() - t0 < budget_s:
-        _, it, _, _ = orc.cg(dims, U, mass, b, tol=TOL, maxiter=2)
-        n_half += 2 * (it + 1)
-        its += 1
-    dt = time.perf_counter() - t0
-    return {"value": FLOP_PER_SITE * Vh * n_half / dt * 1e-9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+    with orc.threads():
+        cores = orc.num_threads()
+        t0 = time.perf_counter()
+        n_half = 0
+        its = 0
+        while time.perf_counter() - t0 < budget_s:
+            _, it, _, _ = orc.cg(dims, U, mass, b, tol=TOL, maxiter=2)
+            n_half += 2 * (it + 1)
+            its += 1
+        dt = time.perf_counter() - t0
+    return {"value": FLOP_PER_SITE * Vh * n_half / dt * 1e-9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
             "sample": f"{its} oracle CG runs of 2 iterations + true residual on {dims} ({n_half} half-Dslashes, "
-                      f"{dt:.1f} s)"}
+                      f"{dt:.1f} s), OpenMP build on {cores} threads ({cpu_model()})"}
 
 
 # ---------------------------------------------------------------- helpers
@@ -276,18 +300,18 @@ def cg_df_dir(vh, l2_bytes):
 
 
 def cg_kernel_launches(st, use_graph, arith=0, df_dir=True):
-    """Kernels one double-precision CG solve launches: the start kernel, four
-    per iteration slot (whole graph bodies, or whole host-loop batches; three
-    when the double-float solver applies p = r + beta p inside its operator
-    passes, df_dir), the two true-residual kernels per pass and one restart
-    kernel per restart; the double-float solver converts its solution back to
-    double with one more.  Exact when the solve needed no restart (each pass's
-    iterations are not reported separately)."""
+    """Kernels one double-precision CG solve launches: the normalisation of b
+    (largest-magnitude pass, exponent, scaled copy), the start kernel, four per
+    iteration slot (whole graph bodies, or whole host-loop batches; three when
+    the double-float solver applies p = r + beta p inside its operator passes,
+    df_dir), the two true-residual kernels per pass, one restart kernel per
+    restart and the scaled copy of the solution.  Exact when the solve needed
+    no restart (each pass's iterations are not reported separately)."""
     per = CG_GRAPH_UNROLL if use_graph else CG_CHECK_EVERY
     passes = st["restarts"] + 1
     slots = per * max(passes, math.ceil(max(st["iters"], 1) / per))
     per_iter = 3 if (arith == F64X and df_dir) else 4
-    return 1 + per_iter * slots + 2 * passes + st["restarts"] + (1 if arith == F64X else 0)
+    return 3 + 1 + per_iter * slots + 2 * passes + st["restarts"] + 1
 
 
 class L2Flush:
@@ -417,27 +441,34 @@ def half_dslash(st):
 
 # ---------------------------------------------------------------- sections
 
-def section_48c12(stag, torch, timer, hbm):
-    """48^3 x 12, eps = 0.2, m = 0.002: double CG (both arithmetics) vs mixed F32/F16; Dslash kernels."""
-    w = li.WORKLOADS[2]
+def section_32c8(stag, torch, timer, hbm):
+    """32^3 x 8, eps = 0.3, m = 0.01: the double CG in both arithmetics and in
+    temporal gauge, the mixed solves, and the operator kernels (L2-assisted:
+    the 151 MB of double links barely exceed L2)."""
+    w = li.WORKLOADS[1]
     dims, mass = w["dims"], w["mass"]
     ctx = stag.Context(dims)
-    ctx.upload_gauge(li.random_links_torch(dims, "smooth", w["eps"], seed=li.workload_seed(2, 0)))
-    b = li.gaussian_half_torch(dims, seed=li.workload_seed(2, 1))
+    ctx.upload_gauge(li.random_links_torch(dims, "smooth", w["eps"], seed=li.workload_seed(1, 0)))
+    b = li.gaussian_half_torch(dims, seed=li.workload_seed(1, 1))
     x = ctx.new_half()
     vh = ctx.Vh
     res = {"workload": w["name"] + " (inputs from the torch generator)"}
-    ms, st = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, f64_arith=F64X), reps=2)
-    res["cg_f64x"] = {"time_to_solution_ms": ms, "iters": st["iters"], "true_rel_residual": st["true_rel_residual"]}
-    ms_i, st = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, f64_arith=F64_IEEE), reps=2)
+    ms_i, st = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, f64_arith=F64_IEEE), reps=3)
     res["cg_ieee_f64"] = {"time_to_solution_ms": ms_i, "iters": st["iters"],
-                          "true_rel_residual": st["true_rel_residual"]}
+                          "true_rel_residual": st["true_rel_residual"],
+                          "gflops": FLOP_PER_SITE * vh * half_dslash(st) / (ms_i * 1e-3) * 1e-9}
+    ms, st = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, f64_arith=F64X), reps=3)
+    res["cg_f64x"] = {"time_to_solution_ms": ms, "iters": st["iters"], "true_rel_residual": st["true_rel_residual"],
+                      "speedup_vs_cg_ieee_f64": ms_i / ms}
+    ctx.cg_solve(x, b, mass, tol=TOL, temporal_gauge=1)   # builds the transform once
+    m, s_ = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, temporal_gauge=1), reps=3)
+    res["cg_f64x_temporal_gauge"] = {"time_to_solution_ms": m, "iters": s_["iters"],
+                                     "true_rel_residual": s_["true_rel_residual"], "speedup_vs_cg_ieee_f64": ms_i / m}
     for name, prec in (("mixed_f32_12", stag.F32), ("mixed_f16_12", stag.F16)):
-        m, s = timer(lambda: ctx.cg_solve_mixed(x, b, mass, tol=TOL, inner_prec=prec, inner_recon=12), reps=2)
-        res[name] = {"time_to_solution_ms": m, "iters": s["iters"], "reliable_updates": s["reliable_updates"],
-                     "true_rel_residual": s["true_rel_residual"], "speedup_vs_cg_f64x": ms / m,
-                     "speedup_vs_cg_ieee_f64": ms_i / m}
-    psi = li.gaussian_half_torch(dims, seed=5)
+        m, s_ = timer(lambda: ctx.cg_solve_mixed(x, b, mass, tol=TOL, inner_prec=prec, inner_recon=12), reps=3)
+        res[name] = {"time_to_solution_ms": m, "iters": s_["iters"], "reliable_updates": s_["reliable_updates"],
+                     "true_rel_residual": s_["true_rel_residual"], "speedup_vs_cg_ieee_f64": ms_i / m}
+    psi = li.gaussian_half_torch(dims, seed=99)
     out = ctx.new_half()
     res["dslash"] = {name: dslash_kernel_entry(timer, ctx, psi, out, p, r, vh, hbm)
                      for name, p, r in (("f64x_18", F64X, 18), ("f64_18", F64_IEEE, 18), ("f32_12", stag.F32, 12),
@@ -572,20 +603,20 @@ def section_force(stag, torch, timer, hbm):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline step only (no workload sections)")
     ap.add_argument("--use-graph", type=int, default=1,
                     help="1: device-side loop in one CUDA graph; 0: host-driven loop (per-kernel profiling)")
-    ap.add_argument("--f64-arith", type=int, default=F64X, choices=[F64_IEEE, F64X],
-                    help="arithmetic of the headline solve's operator passes (0 IEEE double, 3 double-float)")
+    ap.add_argument("--f64-arith", type=int, default=F64_IEEE, choices=[F64_IEEE, F64X],
+                    help="arithmetic of the headline solve (0 IEEE double, the default; 3 double-float)")
     ap.add_argument("--profile-kernel", default=None,
                     help="only run a few launches of one operator on the workload (for ncu): "
                          "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., or whole host-driven "
-                         "solves cg_f64 / cg_f64x, multi_f32_12 / multishift_f32_12 (32^3 x 16), mixed_f16_12 / mixed_f32_12 "
-                         "(48^3 x 12); optional @LXxLYxLZxLT")
+                         "solves cg_f64 / cg_f64x, multi_f32_12 / multishift_f32_12 (32^3 x 16), mixed_f16_12 / "
+                         "mixed_f32_12 (48^3 x 12); optional @LXxLYxLZxLT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -651,37 +682,64 @@ def main():
     df_dir = cg_df_dir(Vh, getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 126 << 20))
     launches = sum(cg_kernel_launches(s, ug, arith, df_dir) for s in stats)
     clocks = clk.summary()
+    x_ieee = x.clone()
 
-    # ---- the same solve with IEEE-double operator passes
-    ms_ieee, st_ieee = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, f64_arith=F64_IEEE), reps=3)
-    # ---- and in temporal gauge (6 link reads per site, the paper's storage; same system and residual)
-    ms_tg, st_tg = (None, None)
-    if arith == F64X:
-        ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, temporal_gauge=1)   # builds the transform once
-        ms_tg, st_tg = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, temporal_gauge=1), reps=3)
+    # ---- the other arithmetics on the same system: double-float, temporal
+    # gauge (6 link reads per site, the paper's storage), mixed precision
+    arms = {}
+    ms_df, st_df = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, f64_arith=F64X), reps=3)
+    arms["cg_f64x"] = {"arithmetic": "double storage, double-float (f32x2) operator and BLAS, double reductions",
+                       "time_to_solution_ms": ms_df, "iters": st_df["iters"],
+                       "true_rel_residual": st_df["true_rel_residual"], "speedup_vs_ieee_f64": ms_per_step / ms_df,
+                       "rel_diff_to_ieee_solution": float(torch.linalg.norm(x - x_ieee) / torch.linalg.norm(x_ieee))}
+    ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, temporal_gauge=1)   # builds the transform once
+    ms_tg, st_tg = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, temporal_gauge=1), reps=3)
+    arms["cg_f64x_temporal_gauge"] = {
+        "arithmetic": "as cg_f64x, links gauge-transformed so that the time links are 1 off the last slice",
+        "time_to_solution_ms": ms_tg, "iters": st_tg["iters"], "true_rel_residual": st_tg["true_rel_residual"],
+        "speedup_vs_ieee_f64": ms_per_step / ms_tg}
+    for name, prec in (("mixed_f32_12", stag.F32), ("mixed_f16_12", stag.F16)):
+        m, sm = timer(lambda: ctx.cg_solve_mixed(x, b, mass, tol=TOL, inner_prec=prec, inner_recon=12,
+                                                 use_graph=ug), reps=3)
+        arms[name] = {"arithmetic": f"{'float' if prec == stag.F32 else 'half + per-site norm'} 12-real inner "
+                                    "iteration, double-float reliable updates, double solution",
+                      "time_to_solution_ms": m, "iters": sm["iters"], "reliable_updates": sm["reliable_updates"],
+                      "true_rel_residual": sm["true_rel_residual"], "speedup_vs_ieee_f64": ms_per_step / m}
 
     # ---- the dominant kernel, standalone: per-launch CUDA events, L2 flushed before each
     psi = torch.from_numpy(li.gaussian_half(dims, seed=99)).to(dev)
     out = ctx.new_half()
-    kern = {"f64x_18": dslash_kernel_entry(timer, ctx, psi, out, F64X, 18, Vh, hbm),
-            "f64_18": dslash_kernel_entry(timer, ctx, psi, out, F64_IEEE, 18, Vh, hbm)}
-    main_k = kern["f64x_18" if arith == F64X else "f64_18"]
-    traffic = load_traffic().get("dslash_f64x_df_18_32c8" if arith == F64X else "dslash_f64_18_32c8")
-    fp64_peak = fp64_peak_gflops()
-    if arith == F64X:
-        roofline = {"kernel": "k_dslash<LinkFieldDF<18>, SpinorDF, SpinorDF> (the solver's double-float operator "
-                              "on its double-float vectors; stag_dslash_repeat, STAG_F64X)",
-                    "bound": "hbm", "achieved": main_k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                    "frac": main_k["achieved_gbs"] / hbm, "traffic": traffic,
-                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind} copy bandwidth)",
-                    "algorithmic_bytes_per_launch": main_k["algorithmic_bytes_per_site"] * Vh,
-                    "kernel_ms": main_k["ms"]}
+    kern = {"f64_18": dslash_kernel_entry(timer, ctx, psi, out, F64_IEEE, 18, Vh, hbm),
+            "f64x_18": dslash_kernel_entry(timer, ctx, psi, out, F64X, 18, Vh, hbm),
+            "f32_12": dslash_kernel_entry(timer, ctx, psi, out, stag.F32, 12, Vh, hbm),
+            "f16_12": dslash_kernel_entry(timer, ctx, psi, out, stag.F16, 12, Vh, hbm)}
+    traffic = load_traffic()
+    fp64_probe = stag.fma_probe(stag.F64) * 1e3
+    fp32_probe = stag.fma_probe(stag.F32) * 1e3
+    if arith == F64_IEEE:
+        mk = kern["f64_18"]
+        peak = fp64_peak_gflops()
+        roofline = {"kernel": "k_dslash<LinkField<double2,18>, SpinorF64, SpinorF64> (the IEEE-double operator of "
+                              "the CG; stag_dslash_repeat, STAG_F64)",
+                    "bound": "alu", "achieved": mk["gflops"], "peak": peak, "unit": "GFLOP/s",
+                    "frac": mk["gflops"] / peak, "traffic": traffic.get("dslash_f64_18_48c12"),
+                    "peak_source": "FP64 FMA rate from unit counts and max clock: 152 SM x 2 DFMA/clk x 2 flop x "
+                                   "2.07 GHz",
+                    "peak_probe_gflops": fp64_probe,
+                    "frac_of_probe": mk["gflops"] / fp64_probe,
+                    "hbm": {"achieved_gbs": mk["achieved_gbs"], "peak_gbs": hbm, "frac": mk["achieved_gbs"] / hbm,
+                            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind} copy bandwidth)"},
+                    "algorithmic_flop_per_launch": FLOP_PER_SITE * Vh,
+                    "algorithmic_bytes_per_launch": mk["algorithmic_bytes_per_site"] * Vh,
+                    "kernel_ms": mk["ms"]}
     else:
-        roofline = {"kernel": "k_dslash<LinkField<double2,18>, SpinorF64> (stag_dslash_eo, STAG_F64)",
-                    "bound": "alu", "achieved": main_k["gflops"], "peak": fp64_peak, "unit": "GFLOP/s",
-                    "frac": main_k["gflops"] / fp64_peak, "traffic": traffic,
-                    "peak_source": "FP64 FMA rate from unit counts and max clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
-                    "kernel_ms": main_k["ms"]}
+        mk = kern["f64x_18"]
+        roofline = {"kernel": "k_dslash<LinkFieldDF<18>, SpinorDF, SpinorDF> (the double-float operator on its "
+                              "double-float vectors; stag_dslash_repeat, STAG_F64X)",
+                    "bound": "hbm", "achieved": mk["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": mk["achieved_gbs"] / hbm, "traffic": traffic.get("dslash_f64x_df_18_48c12"),
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind} copy bandwidth)",
+                    "algorithmic_bytes_per_launch": mk["algorithmic_bytes_per_site"] * Vh, "kernel_ms": mk["ms"]}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     b_host = torch.from_numpy(b_np).pin_memory()
@@ -701,19 +759,10 @@ def main():
         e2e_half.append(half_dslash(st))
     e2e_val = FLOP_PER_SITE * Vh * statistics.mean(e2e_half) / statistics.mean(e2e_t) * 1e-9
 
-    # ---- mixed precision on the same workload
-    mixed = {}
-    for name, prec in (("f32_12", stag.F32), ("f16_12", stag.F16)):
-        xm = ctx.new_half()
-        m, sm = timer(lambda: ctx.cg_solve_mixed(xm, b, mass, tol=TOL, inner_prec=prec, inner_recon=12,
-                                                 use_graph=ug), reps=3)
-        mixed[name] = {"time_to_solution_ms": m, "iters": sm["iters"], "reliable_updates": sm["reliable_updates"],
-                       "true_rel_residual": sm["true_rel_residual"], "speedup_vs_f64": ms_per_step / m}
-
     sections = {}
     if rank == 0 and ws == 1 and not args.quick:
         ctx.close()
-        for name, fn in (("w48c12", lambda: section_48c12(stag, torch, timer, hbm)),
+        for name, fn in (("w32c8", lambda: section_32c8(stag, torch, timer, hbm)),
                          ("w32c16", lambda: section_32c16(stag, torch, timer)),
                          ("force_64c16", lambda: section_force(stag, torch, timer, hbm)),
                          ("paper_tables", lambda: section_paper_tables(stag, torch, timer, hbm))):
@@ -743,24 +792,19 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 storage; operator in double-float (f32x2)" if arith == F64X else "f64",
+        "dtype": "f64" if arith == F64_IEEE else "f64 storage; operator in double-float (f32x2)",
         "data": "synthetic",
         "config": headline_config(w),
         "cg": {"time_to_solution_ms": ms_per_step, "iters": last["iters"], "restarts": last["restarts"],
                "true_rel_residual": last["true_rel_residual"], "half_dslash_per_solve": half_per_step,
-               "f64_arith": "double-float (STAG_F64X)" if arith == F64X else "IEEE double (STAG_F64)"},
-        "cg_ieee_f64": {"time_to_solution_ms": ms_ieee, "iters": st_ieee["iters"],
-                        "true_rel_residual": st_ieee["true_rel_residual"]},
-        "cg_temporal_gauge": None if st_tg is None else {
-            "time_to_solution_ms": ms_tg, "iters": st_tg["iters"], "true_rel_residual": st_tg["true_rel_residual"],
-            "speedup_vs_cg": ms_per_step / ms_tg,
-            "note": "same system: links gauge-transformed so that the time links are 1 off the last slice "
-                    "(6 link reads per site), solution transformed back"},
+               "f64_arith": "IEEE double (STAG_F64)" if arith == F64_IEEE else "double-float (STAG_F64X)"},
+        "arms_48c12": arms,
         "roofline": roofline,
-        "dslash_kernels_32c8": kern,
+        "dslash_kernels_48c12": kern,
+        "alu_probes": {"fp64_fma_gflops": fp64_probe, "fp32_fma_gflops": fp32_probe,
+                       "note": "stag_fma_probe: independent FMA chains on every SM, CUDA events"},
         "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": int(b_host.numel() * 16),
                 "d2h_bytes_per_step": int(x_host.numel() * 16), "seconds_per_step": statistics.mean(e2e_t)},
-        "mixed": mixed,
         "sections": sections,
         "gpu_launches": launches,
         "clocks": clocks,

@@ -156,6 +156,15 @@ int stag_dslash_repeat_multi(stag_ctx ctx, int prec, int recon, int rhs_block, i
  * STAG_ENOMEM, STAG_ECUDA. */
 int stag_cg_update_time(stag_ctx ctx, int f64_arith, int nrep, double *ms_per_launch);
 
+/* Measurement support for the ALU rooflines (Sec. 4.3 compares the operator
+ * with the peak of the arithmetic that binds it): the sustained FMA rate of
+ * the FP64 (prec STAG_F64) or FP32 (STAG_F32) pipe of the current device, in
+ * TFLOP/s (2 flop per FMA), from one launch of independent FMA chains on every
+ * SM (iters FMA steps per chain; ~2048 for FP64 and ~32768 for FP32 run a few
+ * milliseconds), timed with CUDA events on the legacy default stream.  Blocks;
+ * writes *tflops (host).  Errors: STAG_EINVAL, STAG_ECUDA. */
+int stag_fma_probe(int prec, int iters, double *tflops);
+
 /* Multi-vector operator (Sec. 4.3, NMULTI): out_k = D_{p,1-p} in_k for
  * k = 0..nrhs-1, with each link loaded once per site for a block of
  * rhs_block vectors (1, 2, 4, 8 or 16; 0 = autotuned, cached per context).

@@ -27,29 +27,64 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "stag_oracle.c")
 _LIB = os.path.join(_HERE, "libstag_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libstag_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_threaded = False
 
 STATUS = {0: "converged", 1: "not converged", 2: "breakdown"}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library with gcc (portable flags, no -march)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+def _compile(out, extra):
+    if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", *extra,
                "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+        os.replace(tmp, out)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared libraries with gcc (portable flags, no -march):
+    the single-threaded parity build and an OpenMP build used only to time the
+    oracle on every host core (identical results: see stag_oracle.c)."""
+    if force:
+        for p in (_LIB, _LIB_OMP):
+            if os.path.exists(p):
+                os.remove(p)
+    _compile(_LIB, [])
+    _compile(_LIB_OMP, ["-fopenmp"])
     return _LIB
 
 
+class threads:
+    """Context manager: oracle calls inside it use the OpenMP build (timing only).
+
+        with oracle.threads():
+            oracle.cg(...)
+    """
+
+    def __enter__(self):
+        global _threaded
+        self._prev, _threaded = _threaded, True
+        return self
+
+    def __exit__(self, *exc):
+        global _threaded
+        _threaded = self._prev
+
+
+def num_threads() -> int:
+    """Threads the OpenMP build's site loops use (1 for the parity build)."""
+    return int(_load().orc_num_threads())
+
+
 def _load():
-    global _lib
+    key = "omp" if _threaded else "serial"
     with _lock:
-        if _lib is None:
+        if key not in _libs:
             build()
-            lib = ctypes.CDLL(_LIB)
+            lib = ctypes.CDLL(_LIB_OMP if key == "omp" else _LIB)
             P = ctypes.c_void_p
             I4 = ctypes.POINTER(ctypes.c_int)
             lib.orc_check_dims.argtypes = [I4]
@@ -68,8 +103,9 @@ def _load():
             lib.orc_action.restype = ctypes.c_double
             lib.orc_force.argtypes = [I4, P, P, P, P]
             lib.orc_reconstruct_row2.argtypes = [ctypes.c_long, P, P]
-            _lib = lib
-    return _lib
+            lib.orc_num_threads.restype = ctypes.c_int
+            _libs[key] = lib
+    return _libs[key]
 
 
 def _dims(dims):

@@ -23,7 +23,7 @@ import threading
 __all__ = [
     "F64", "F32", "F16", "F64X", "RECON_18", "RECON_12", "StagError", "NotConverged",
     "load", "build", "Context", "SolverParams", "SolverStats", "StaggeredAction", "fermion_force",
-    "apply_M_noalloc", "NOALLOC_MAX_VH",
+    "apply_M_noalloc", "NOALLOC_MAX_VH", "fma_probe",
 ]
 
 F64, F32, F16, F64X = 0, 1, 2, 3
@@ -111,6 +111,7 @@ def _declare(lib):
         "stag_last_error": ([], ctypes.c_char_p),
         "stag_abi_version": ([], I),
         "stag_apply_M_noalloc": ([ctypes.POINTER(I), P, P, P, D, P], I),
+        "stag_fma_probe": ([I, I, ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -479,6 +480,16 @@ def fermion_force(U, phi, lattice, mass, **params):
     P = torch.empty_like(U)
     lattice.fermion_force(X, P=P)
     return P
+
+
+def fma_probe(prec=F64, iters=None):
+    """stag_fma_probe: sustained FMA throughput (TFLOP/s) of the FP64 or FP32 pipe."""
+    _torch()
+    if iters is None:
+        iters = 2048 if prec == F64 else 32768
+    v = ctypes.c_double()
+    _check(load().stag_fma_probe(int(prec), int(iters), ctypes.byref(v)))
+    return v.value
 
 
 def apply_M_noalloc(dims, U, out, inp, mass, stream=None):

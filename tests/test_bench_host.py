@@ -78,20 +78,22 @@ def test_max_over_ranks_gloo_two_ranks():
 
 def test_cg_kernel_launch_count():
     import bench
+    # normalisation of b (3) + start (1) + iterations + residual pair per pass
+    # + restart kernels + scaled copy of the solution (1)
     # graph: iterations run in whole bodies of CG_GRAPH_UNROLL
     st = {"iters": 80, "restarts": 0}
-    assert bench.cg_kernel_launches(st, 1) == 1 + 4 * 80 + 2
+    assert bench.cg_kernel_launches(st, 1) == 4 + 4 * 80 + 2 + 1
     st = {"iters": 81, "restarts": 0}
-    assert bench.cg_kernel_launches(st, 1) == 1 + 4 * 84 + 2
+    assert bench.cg_kernel_launches(st, 1) == 4 + 4 * 84 + 2 + 1
     # host loop: whole batches of CG_CHECK_EVERY
-    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 0) == 1 + 4 * 100 + 2
+    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 0) == 4 + 4 * 100 + 2 + 1
     # a restart adds a pass: its residual kernels and the restart kernel
-    assert bench.cg_kernel_launches({"iters": 2, "restarts": 1}, 1) == 1 + 4 * 8 + 4 + 1
+    assert bench.cg_kernel_launches({"iters": 2, "restarts": 1}, 1) == 4 + 4 * 8 + 4 + 1 + 1
 
     # the double-float solver: three kernels per iteration (four with the
-    # direction update as a pass of its own) and its final conversion kernel
-    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3) == 1 + 3 * 80 + 2 + 1
-    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3, False) == 1 + 4 * 80 + 2 + 1
+    # direction update as a pass of its own)
+    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3) == 4 + 3 * 80 + 2 + 1
+    assert bench.cg_kernel_launches({"iters": 80, "restarts": 0}, 1, 3, False) == 4 + 4 * 80 + 2 + 1
 
 
 def test_cg_direction_update_rule(monkeypatch):
@@ -149,6 +151,10 @@ def test_reference_arm_line(tmp_path):
     assert line["higher_is_better"] is True and line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3
     assert line["config"] == bench.headline_config(li.WORKLOADS[bench.WORKLOAD_INDEX])
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    import oracle
+    with oracle.threads():
+        cores = oracle.num_threads()
+    assert cb["kind"] == "oracle" and cb["cores"] == cores and cb["value"] == line["value"] and cb["sample"]
+    assert line["dtype"] == "f64" and line["config"]["dims"] == [48, 48, 48, 12]
     assert line["e2e"] == {"value": line["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}

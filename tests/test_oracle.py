@@ -526,3 +526,22 @@ def test_recon12_keeps_rounded_rows_and_rebuilds_the_third():
         assert np.array_equal(R[:, 2, :], orc.reconstruct_row2(R))
         # the rebuilt row is close to the original one (SU(3) links), not equal to a rounded copy
         assert np.abs(R[:, 2, :] - U[:, 2, :]).max() <= 8 * 2.0 ** -11
+
+
+def test_threaded_timing_build_gives_identical_bits():
+    """The OpenMP build (used only to time the oracle on every host core)
+    spreads independent sites over threads and keeps every sum sequential, so
+    its operator, M and CG results equal the parity build's bit for bit."""
+    dims, mass = (6, 4, 4, 6), 0.1
+    U = li.random_links(dims, "haar", seed=161)
+    psi = li.gaussian_half(dims, seed=162)
+    full = li.gaussian_full(dims, seed=163)
+    ref = (orc.dslash_half(dims, U, psi, 0), orc.dslash_half(dims, U, psi, 1), orc.apply_M(dims, U, mass, psi),
+           orc.dslash_full(dims, U, full), orc.cg(dims, U, mass, psi, tol=1e-10)[0])
+    with orc.threads():
+        assert orc.num_threads() >= 1
+        got = (orc.dslash_half(dims, U, psi, 0), orc.dslash_half(dims, U, psi, 1), orc.apply_M(dims, U, mass, psi),
+               orc.dslash_full(dims, U, full), orc.cg(dims, U, mass, psi, tol=1e-10)[0])
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+    assert orc.num_threads() == 1
