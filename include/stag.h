@@ -139,7 +139,11 @@ int stag_dslash_result(stag_ctx ctx, double *out);
  * nrhs in [1, STAG_MAX_RHS]): stag_dslash_repeat_multi applies the
  * multi-vector operator of stag_dslash_multi (Sec. 4.3, NMULTI: each link
  * loaded once per site for rhs_block vectors; 0 = autotuned) nrep times;
- * stag_dslash_result then writes nrhs fields.  Any other operator call of the
+ * stag_dslash_result then writes nrhs fields.  For measurement, rhs_block
+ * may also name one configuration of the multi-vector kernels,
+ * (G << 8) | NBT: G warp groups of a block sharing one shared-memory tile of
+ * links, NBT right-hand sides per thread (G = 1: no tile; the codes offered
+ * for the storage, else STAG_EINVAL).  Any other operator call of the
  * context that converts fields (F32 / F16 dslash, dslash_multi) discards the
  * prepared fields (STAG_EINVAL on the next repeat or result).  Errors as above. */
 int stag_dslash_prepare_multi(stag_ctx ctx, const double *in, int nrhs, int prec);

@@ -290,8 +290,9 @@ int stag_dslash_repeat_multi(stag_ctx ctx, int prec, int recon, int rhs_block, i
         set_error("nrep must be >= 1 and recon 18 or 12");
         return STAG_EINVAL;
     }
-    if (rhs_block != 0 && rhs_block != 1 && rhs_block != 2 && rhs_block != 4 && rhs_block != 8 && rhs_block != 16) {
-        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
+    if (rhs_block != 0 && rhs_block != 1 && rhs_block != 2 && rhs_block != 4 && rhs_block != 8 && rhs_block != 16 &&
+        rhs_block < 256) {
+        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8, 16 or a configuration code (G << 8) | NBT");
         return STAG_EINVAL;
     }
     if (!ctx->have_gauge) {

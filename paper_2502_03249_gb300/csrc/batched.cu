@@ -37,8 +37,10 @@ static int ensure_batch(stag_ctx ctx, int prec, int recon, int nrhs, BatchSlot**
         STAG_CUDA_TRY(cudaMalloc(&m.r_hi, n * m.f64_stride));
         STAG_CUDA_TRY(cudaMalloc(&m.b, n * m.f64_stride));
         STAG_CUDA_TRY(cudaMalloc(&m.t64, n * m.f64_stride));
+        STAG_CUDA_TRY(cudaMalloc(&m.x_df, n * m.f64_stride));
         STAG_CUDA_TRY(cudaMalloc(&m.sc, n * sizeof(CgScalars)));
-        STAG_CUDA_TRY(cudaMalloc(&m.part, n * m.gx * sizeof(double)));
+        // partials: one per block of BBS sites, or per tile of 32 (tile kernels)
+        STAG_CUDA_TRY(cudaMalloc(&m.part, n * (size_t)((g.Vh + 31) / 32) * sizeof(double)));
         STAG_CUDA_TRY(cudaMalloc(&m.shifts, n * sizeof(double)));
         STAG_CUDA_TRY(cudaMalloc(&m.cnt_sys, n * sizeof(unsigned)));
         STAG_CUDA_TRY(cudaMemset(m.cnt_sys, 0, n * sizeof(unsigned)));
@@ -81,15 +83,18 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
     }
     // right-hand sides per operator pass: given, or tuned on the inner operator
     int nb = prm.rhs_block;
-    if (nb != 0 && nb != 1 && nb != 2 && nb != 4 && nb != 8 && nb != 16) {
-        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
+    if (nb != 0 && nb != 1 && nb != 2 && nb != 4 && nb != 8 && nb != 16 && nb < 256) {
+        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8, 16 or a configuration code (G << 8) | NBT");
         return STAG_EINVAL;
     }
-    if (nb == 0) STAG_TRY(multi_dslash(ctx, prec, recon, 1, m.t, m.p, nrhs, 0, &nb));
+    // the configuration (multi_tile.cuh) of a given block, or the autotuner's
+    // choice for the inner operator on these buffers
+    int cfg = multi_cfg_for(prec, nb);
+    if (nb == 0) STAG_TRY(multi_dslash(ctx, prec, recon, 1, m.t, m.p, nrhs, 0, &nb, &cfg));
     int rc;
-    if (prec == STAG_F64) rc = batched_run_f64(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, nb);
-    else if (prec == STAG_F32) rc = batched_run_f32(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, nb);
-    else rc = batched_run_f16(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, nb);
+    if (prec == STAG_F64) rc = batched_run_f64(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, cfg);
+    else if (prec == STAG_F32) rc = batched_run_f32(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, cfg);
+    else rc = batched_run_f16(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, cfg);
     STAG_TRY(rc);
     std::vector<CgScalars> hs(nrhs);
     STAG_CUDA_TRY(cudaMemcpyAsync(hs.data(), m.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
@@ -119,14 +124,15 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
         }
     }
     STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    ctx->last_rhs_block = nb;
+    ctx->last_rhs_block = mcfg_block(cfg);
+    ctx->last_multi_cfg = cfg;
     return status;
 }
 
 void BatchSlot::release()
 {
     lg.destroy();
-    void* bufs[] = {r, p, Ap, t, xlo, x_hi, r_hi, b, t64, sc, part, shifts, cnt_sys};
+    void* bufs[] = {r, p, Ap, t, xlo, x_hi, r_hi, b, t64, x_df, sc, part, shifts, cnt_sys};
     for (void* q : bufs)
         if (q) cudaFree(q);
     *this = BatchSlot();

@@ -17,10 +17,12 @@
 
 #include <chrono>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "batched.cuh"
 #include "df64.cuh"
+#include "multi_tile.cuh"
 #include "cg_kernels.cuh"
 #include "graph.h"
 #include "tune.h"
@@ -29,14 +31,6 @@
 namespace stag {
 
 constexpr int BBS = 128;      // threads (sites) per block of every batched kernel
-
-// Right-hand sides per thread of the double-precision passes (reliable
-// updates): the systems reach their updates at different iterations, so a
-// pass usually works on one or two of them.  IEEE double (FP64-ALU bound)
-// shares each link load among 4; double-float uses 1 per thread, which keeps
-// its operator at 96 registers and full occupancy (4 per thread needs 128-152).
-template <class LF64> struct Nb64 { static constexpr int value = 4; };
-template <> struct Nb64<LinkFieldDF<18>> { static constexpr int value = 1; };
 
 struct BatchScal {
     CgScalars* sc;      // [nrhs]
@@ -105,10 +99,12 @@ __device__ __forceinline__ unsigned mask_updating(const BatchScal& b, int k0)
 // residual recomputation.  grid (gx, nrhs).
 // b holds the normalised right-hand sides 2^-k_k B_k; x0 (unnormalised
 // initial guesses) is brought to the same scale.
+// x_df (double-float arithmetic only, else NULL) keeps x_hi split into
+// double-float pairs, the storage the reliable updates' operator reads.
 template <class SX>
 __global__ void __launch_bounds__(BBS) k_b_init(int Vh, const double2* b, const double2* x0, double2* x_hi, SX xlo,
                                                 size_t sx_stride, BatchScal bs, double tol, int maxiter, double m2,
-                                                const double* shifts, double delta, const int* kexp)
+                                                const double* shifts, double delta, const int* kexp, float4* x_df)
 {
     __shared__ double red[BBS / 32];
     __shared__ bool last;
@@ -122,11 +118,15 @@ __global__ void __launch_bounds__(BBS) k_b_init(int Vh, const double2* b, const 
             const double2 bv = b[o + c];
             d = fma(bv.x, bv.x, d);
             d = fma(bv.y, bv.y, d);
+            double2 xv = make_double2(0.0, 0.0);
             if (x0) {
                 const double2 v = x0[o + c];
-                x_hi[o + c] = make_double2(scalbn(v.x, -kexp[k]), scalbn(v.y, -kexp[k]));
-            } else {
-                x_hi[o + c] = make_double2(0.0, 0.0);
+                xv = make_double2(scalbn(v.x, -kexp[k]), scalbn(v.y, -kexp[k]));
+            }
+            x_hi[o + c] = xv;
+            if (x_df) {
+                const DF re = split_double(xv.x), im = split_double(xv.y);
+                x_df[o + c] = make_float4(re.hi, re.lo, im.hi, im.lo);
             }
             z.c[c].re = z.c[c].im = 0;
         }
@@ -236,6 +236,191 @@ __global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_Mp_d
     }
 }
 
+// ----------------------------------------- tile kernels (multi_tile.cuh)
+
+// t_k = D_oe p_k for the active systems, links staged per tile and shared by
+// the block's G NBT systems.  grid (tiles, ceil(nrhs / (G NBT))).
+template <class LF, class S, int G, int NBT>
+__global__ void __launch_bounds__(32 * TileSW<G>::value * G, TileMinBlocks<32 * TileSW<G>::value * G, NBT>::value)
+    k_tile_b_hop(Geom g, LF U, S in, S out, size_t stride, BatchScal bs)
+{
+    __shared__ uint4 sm[TileSmem<LF, G>::value / 16];
+    constexpr int SW = TileSW<G>::value, TS = 32 * SW;
+    const int kb = blockIdx.y * G * NBT;
+    if (!mask_active<G * NBT>(bs, kb)) return;   // uniform over the block
+    const int h = blockIdx.x * TS + threadIdx.x % TS;
+    const int k0 = kb + (threadIdx.x / TS) * NBT;
+    const unsigned mask = mask_active<NBT>(bs, k0);
+    SiteNbrs s;
+    site_nbrs(g, 1, h < g.Vh ? h : g.Vh - 1, s);
+    Vec3<typename LF::real> acc[NBT];
+    tile_site_multi<LF, S, G, NBT>(g, 1, h, s, U, in, stride, k0, mask, sm, acc);
+    if (h >= g.Vh) return;
+#pragma unroll
+    for (int k = 0; k < NBT; ++k)
+        if (mask & (1u << k)) out.at(k0 + k, stride).store(h, acc[k]);
+}
+
+// Ap_k = (m^2 + sigma_k) p_k - D_eo t_k and the partial sums of <p_k, Ap_k>,
+// as k_b_Mp_dot with the tile operator.  The block's partial of system k is
+// the sum over its SW site warps of the warp sums (fixed order), stored at
+// part[k * tiles + tile]; k_b_alpha forms the totals (no arrival counting
+// here: with 16 systems per block and thousands of tiles, the per-block
+// atomics and the serial final sums of the last arrivers cost more than the
+// operator).  grid (tiles, ceil(nrhs / (G NBT))).
+template <class LF, class S, int G, int NBT>
+__global__ void __launch_bounds__(32 * TileSW<G>::value * G, TileMinBlocks<32 * TileSW<G>::value * G, NBT>::value)
+    k_tile_b_Mp_dot(Geom g, LF U, S t, S p, S Ap, size_t stride, BatchScal bs)
+{
+    constexpr int SW = TileSW<G>::value, TS = 32 * SW, NT = TS * G, NW = NT / 32;
+    __shared__ uint4 sm[TileSmem<LF, G>::value / 16];
+    __shared__ double wsum[NW * NBT];
+    typedef typename S::real real;
+    const int kb = blockIdx.y * G * NBT;
+    const unsigned bmask = mask_active<G * NBT>(bs, kb);
+    if (!bmask) return;   // uniform over the block
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = blockIdx.x * TS + threadIdx.x % TS;
+    const int k0 = kb + (threadIdx.x / TS) * NBT;
+    const unsigned mask = (bmask >> ((threadIdx.x / TS) * NBT)) & ((1u << NBT) - 1u);
+    SiteNbrs s;
+    site_nbrs(g, 0, h < g.Vh ? h : g.Vh - 1, s);
+    Vec3<real> acc[NBT];
+    tile_site_multi<LF, S, G, NBT>(g, 0, h, s, U, t, stride, k0, mask, sm, acc);
+    double d[NBT];
+#pragma unroll
+    for (int k = 0; k < NBT; ++k) d[k] = 0.0;
+    if (h < g.Vh) {
+#pragma unroll
+        for (int k = 0; k < NBT; ++k) {
+            if (!(mask & (1u << k))) continue;
+            const real m2s = (real)(bs.sc[k0 + k].m2 + bs.sc[k0 + k].sigma);
+            const Vec3<real> pv = p.at(k0 + k, stride).load(h);
+            Vec3<real> a;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a.c[c].re = fma(m2s, pv.c[c].re, -acc[k].c[c].re);
+                a.c[c].im = fma(m2s, pv.c[c].im, -acc[k].c[c].im);
+            }
+            Ap.at(k0 + k, stride).store(h, a);
+            d[k] = site_dot(pv, a);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NBT; ++k) {
+        double x = d[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) wsum[w * NBT + k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < G * NBT && (bmask & (1u << threadIdx.x))) {
+        const int gi = threadIdx.x / NBT, k = threadIdx.x % NBT;
+        double x = 0.0;
+#pragma unroll
+        for (int sw = 0; sw < SW; ++sw) x += wsum[(gi * SW + sw) * NBT + k];
+        bs.part[(size_t)(kb + threadIdx.x) * bs.gx + blockIdx.x] = x;
+    }
+}
+
+// pAp_k = the sum of system k's bs.gx partials (fixed order), alpha_k =
+// rr_k / pAp_k, or a breakdown.  One block per system (grid nrhs).
+template <int BS>
+__global__ void __launch_bounds__(BS) k_b_alpha(BatchScal bs)
+{
+    __shared__ double red[BS / 32];
+    const int k = blockIdx.x;
+    if (!active(bs.sc[k])) return;
+    const double pAp = sum_partials<BS>(bs.part + (size_t)k * bs.gx, bs.gx, red);
+    if (threadIdx.x == 0) {
+        CgScalars& c = bs.sc[k];
+        c.pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            c.status = STAG_BREAKDOWN;
+            c.done = 1;
+            c.reliable = 0;
+        } else {
+            c.alpha = c.rr / pAp;
+        }
+    }
+}
+
+// ------------------------------------- reliable updates with link tiles
+//
+// The double-precision passes of a reliable update, for every system due,
+// with the links of a tile of 32 sites staged once for up to 16 systems
+// (multi_tile.cuh, G = 16 groups of one system): the systems' updates are
+// gathered into the same iterations (k_b_update), so that one pass over the
+// links serves all of them.  grid (tiles, ceil(nrhs / 16)).
+constexpr int RG = 16;
+
+// t64_k = D_oe x_hi_k for the systems due.
+template <class LF, class SD>
+__global__ void __launch_bounds__(32 * RG, 2) k_tile_b_hop64(Geom g, LF U, SD in, SD out, size_t stride,
+                                                             BatchScal bs)
+{
+    __shared__ uint4 sm[TileSmem<LF, RG>::value / 16];
+    const int kb = blockIdx.y * RG;
+    if (!mask_updating<RG>(bs, kb)) return;   // uniform over the block
+    const int h = blockIdx.x * 32 + threadIdx.x % 32;
+    const int k0 = kb + threadIdx.x / 32;
+    const unsigned mask = mask_updating<1>(bs, k0);
+    SiteNbrs s;
+    site_nbrs(g, 1, h < g.Vh ? h : g.Vh - 1, s);
+    Vec3<typename LF::real> acc[1];
+    tile_site_multi<LF, SD, RG, 1>(g, 1, h, s, U, in, stride, k0, mask, sm, acc);
+    if (h < g.Vh && mask) out.at(k0, stride).store(h, acc[0]);
+}
+
+// r_hi_k = b_k - ((m^2 + sigma_k) x_hi_k - D_eo t64_k) in double and the
+// tile's partial of |r_hi_k|^2 at part[k * tiles + tile]; k_b_rrtrue sums them.
+template <class LF, class SD>
+__global__ void __launch_bounds__(32 * RG, 2) k_tile_b_resid64(Geom g, LF U, SD t, const double2* x_hi,
+                                                               const double2* b, double2* r_hi, BatchScal bs)
+{
+    __shared__ uint4 sm[TileSmem<LF, RG>::value / 16];
+    const int kb = blockIdx.y * RG;
+    if (!mask_updating<RG>(bs, kb)) return;   // uniform over the block
+    const int lane = threadIdx.x % 32;
+    const int h = blockIdx.x * 32 + lane;
+    const int k0 = kb + threadIdx.x / 32;
+    const unsigned mask = mask_updating<1>(bs, k0);
+    const size_t stride = (size_t)g.Vh * 3 * sizeof(double2);
+    SiteNbrs s;
+    site_nbrs(g, 0, h < g.Vh ? h : g.Vh - 1, s);
+    Vec3<typename LF::real> acc[1];
+    tile_site_multi<LF, SD, RG, 1>(g, 0, h, s, U, t, stride, k0, mask, sm, acc);
+    double d = 0.0;
+    if (h < g.Vh && mask) {
+        const double m2s = bs.sc[k0].m2 + bs.sc[k0].sigma;
+        const size_t o = ((size_t)k0 * g.Vh + h) * 3;
+        const Vec3<double> Dt = vconv<double>(acc[0]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 xv = x_hi[o + c], bv = b[o + c];
+            const double re = bv.x - fma(m2s, xv.x, -Dt.c[c].re);
+            const double im = bv.y - fma(m2s, xv.y, -Dt.c[c].im);
+            r_hi[o + c] = make_double2(re, im);
+            d = fma(re, re, d);
+            d = fma(im, im, d);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0 && mask) bs.part[(size_t)k0 * bs.gx + blockIdx.x] = d;
+}
+
+// rr_true_k = the sum of system k's bs.gx partials (fixed order), systems due.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_b_rrtrue(BatchScal bs)
+{
+    __shared__ double red[BS / 32];
+    const int k = blockIdx.x;
+    if (!updating(bs.sc[k])) return;
+    const double rr = sum_partials<BS>(bs.part + (size_t)k * bs.gx, bs.gx, red);
+    if (threadIdx.x == 0) bs.sc[k].rr_true = rr;
+}
+
 // x_k += alpha_k p_k, r_k -= alpha_k Ap_k, rr_k; flag reliable updates.  grid (gx, nrhs).
 template <class S, class SX>
 __global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride, S r, S p, S Ap, size_t stride,
@@ -299,9 +484,19 @@ __global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride
     *bs.cnt = 0;
     __threadfence();
     // other systems' flags were written by other blocks in this kernel: read past L1
-    const volatile CgScalars* vs = bs.sc;
+    volatile CgScalars* vs = bs.sc;
     int any_rel = 0;
     for (int kk = 0; kk < bs.nrhs; ++kk) any_rel |= !vs[kk].done && vs[kk].reliable;
+    // When one system is due, every active system takes its reliable update
+    // in the same pass: the double-precision passes share each link load
+    // among all systems due (k_tile_b_hop64 / k_tile_b_resid64), so that a few
+    // gathered passes replace one pass every iteration or two for whichever
+    // system happens to be due.  (An update replaces the iterated residual by
+    // the true one and keeps the direction; doing it earlier than needed
+    // costs no accuracy.)
+    if (any_rel)
+        for (int kk = 0; kk < bs.nrhs; ++kk)
+            if (!vs[kk].done) vs[kk].reliable = 1;
     if (use_cond) {
         cudaGraphSetConditional(ih, any_rel ? 1 : 0);
         cudaGraphSetConditional(wh, 1);
@@ -311,7 +506,8 @@ __global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride
 // x_hi_k += xlo_k, xlo_k = 0 for systems due a reliable update.  grid (gx, 1):
 // each block loops over the systems and skips those not due.
 template <class SX>
-__global__ void __launch_bounds__(BBS) k_b_accum_x(int Vh, double2* x_hi, SX xlo, size_t sx_stride, BatchScal bs)
+__global__ void __launch_bounds__(BBS) k_b_accum_x(int Vh, double2* x_hi, SX xlo, size_t sx_stride, BatchScal bs,
+                                                   float4* x_df)
 {
     const int h = blockIdx.x * BBS + threadIdx.x;
     if (h >= Vh) return;
@@ -327,76 +523,14 @@ __global__ void __launch_bounds__(BBS) k_b_accum_x(int Vh, double2* x_hi, SX xlo
             xv.x += (double)v.c[c].re;
             xv.y += (double)v.c[c].im;
             x_hi[o + c] = xv;
+            if (x_df) {
+                const DF re = split_double(xv.x), im = split_double(xv.y);
+                x_df[o + c] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            }
             z.c[c].re = z.c[c].im = 0;
         }
         xk.store(h, z);
     }
-}
-
-// One group of NB systems of k_b_resid64 (below).
-template <class LF, class SD, int NB>
-__device__ __forceinline__ void resid64_group(const Geom& g, const LF& U, const double2* t, const double2* x_hi,
-                                              const double2* b, double2* r_hi, const BatchScal& bs, int k0,
-                                              double* red, unsigned* lastm_p)
-{
-    unsigned& lastm = *lastm_p;
-    const unsigned mask = mask_updating<NB>(bs, k0);
-    if (!mask) return;   // uniform over the block
-    const int h = blockIdx.x * BBS + threadIdx.x;
-    const size_t stride = (size_t)g.Vh * 3 * sizeof(double2);
-    double d[NB];
-#pragma unroll
-    for (int k = 0; k < NB; ++k) d[k] = 0.0;
-    if (mask && h < g.Vh) {
-        Vec3<typename LF::real> acc[NB];
-        dslash_site_multi<LF, SD, NB>(g, 0, h, U, SD{(double2*)t}, stride, k0, mask, acc);
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            if (!(mask & (1u << k))) continue;
-            const double m2s = bs.sc[k0 + k].m2 + bs.sc[k0 + k].sigma;
-            const size_t o = ((size_t)(k0 + k) * g.Vh + h) * 3;
-            const Vec3<double> Dt = vconv<double>(acc[k]);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double2 xv = x_hi[o + c], bv = b[o + c];
-                const double re = bv.x - fma(m2s, xv.x, -Dt.c[c].re);
-                const double im = bv.y - fma(m2s, xv.y, -Dt.c[c].im);
-                r_hi[o + c] = make_double2(re, im);
-                d[k] = fma(re, re, d[k]);
-                d[k] = fma(im, im, d[k]);
-            }
-        }
-    }
-    {
-        const double s = block_sum_n<BBS, NB>(d, mask, red);
-        if (threadIdx.x < NB && (mask & (1u << threadIdx.x)))
-            bs.part[(size_t)(k0 + threadIdx.x) * bs.gx + blockIdx.x] = s;
-    }
-    const unsigned fin = arrive_last_sys<NB>(bs, k0, mask, &lastm);
-#pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        if (!(fin & (1u << k))) continue;
-        const double rr = sum_partials<BBS>(bs.part + (size_t)(k0 + k) * bs.gx, bs.gx, red);
-        if (threadIdx.x == 0) bs.sc[k0 + k].rr_true = rr;
-    }
-}
-
-// r_hi_k = b_k - (m^2 + sigma_k) x_hi_k + D_eo t_k, rr_true_k (double) for updating systems.
-// The operator pass runs in LF's arithmetic (IEEE double, or double-float on
-// the same double vectors through SD), the epilogue in double.  grid (gx, 1):
-// each block loops over the groups of NB systems and skips those with none
-// due; every system due gets one partial from every block and is finished by
-// its own last block, as in the iteration's reductions.
-template <class LF, class SD, int NB>
-__global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_resid64(Geom g, LF U, const double2* t,
-                                                                                        const double2* x_hi,
-                                                                                        const double2* b, double2* r_hi,
-                                                                                        BatchScal bs)
-{
-    __shared__ double red[(BBS / 32) * (NB > 1 ? NB : 1)];
-    __shared__ unsigned lastm;
-    for (int k0 = 0; k0 < bs.nrhs; k0 += NB)
-        resid64_group<LF, SD, NB>(g, U, t, x_hi, b, r_hi, bs, k0, red, &lastm);
 }
 
 // r_k = lo(r_hi_k) (and p_k = r_k at the start); then, in the last block,
@@ -476,13 +610,37 @@ typedef LinkField<double2, 18> LF64B;
 
 // LF64 / SD64: link field and spinor view of the double-precision passes
 // (reliable updates): IEEE double (LinkField<double2,18>, SpinorF64) or
-// double-float on the same double vectors (LinkFieldDF<18>, SpinorF64asDF).
-template <class S, class SX, class LF, int NB, class LF64, class SD64>
+// double-float (LinkFieldDF<18>, SpinorDF on double-float copies of the vectors).
+// CFG: the multi-vector configuration of the iteration's operator passes
+// (multi_tile.cuh): G = 1 register-blocked with NBT right-hand sides per
+// thread, G > 1 link tiles shared by G NBT right-hand sides.
+template <class S, class SX, class LF, int CFG, class LF64, class SD64>
 struct BatchPlan {
-    static constexpr int NB64 = Nb64<LF64>::value;
+    static constexpr int G = mcfg_G(CFG), NBT = mcfg_NBT(CFG);
     static S spin(const BatchSlot& m, void* buf) { return m.template spinor<S>(buf); }
     static SX spinx(const BatchSlot& m, void* buf) { return m.template spinor<SX>(buf); }
 
+    // the reliable update's double-precision operator passes (link tiles
+    // shared by up to 16 systems due) and the true residual norms
+    // SD64: the operator's vector storage, double (IEEE) or double-float pairs
+    // (x_df, a split copy of x_hi kept by k_b_init / k_b_accum_x, so that no
+    // neighbour load splits doubles)
+    static constexpr bool DFX = std::is_same<SD64, SpinorDF>::value;
+    static SD64 view64(void* p) { return SD64{(typename std::conditional<DFX, float4, double2>::type*)p}; }
+    static float4* xdf(const BatchSlot& m) { return DFX ? (float4*)m.x_df : nullptr; }
+    static int enqueue_hop_resid64(stag_ctx ctx, BatchSlot& m, const LF64& U64, cudaStream_t s)
+    {
+        const Geom g = ctx->g;
+        const int tiles = (g.Vh + 31) / 32;
+        const BatchScal bst{m.sc, m.nrhs, m.part, ctx->counters + 1, tiles, m.cnt_sys};
+        const dim3 gt(tiles, (m.nrhs + RG - 1) / RG);
+        k_tile_b_hop64<LF64, SD64><<<gt, 32 * RG, 0, s>>>(g, U64, view64(DFX ? m.x_df : m.x_hi), view64(m.t64),
+                                                          m.f64_stride, bst);
+        k_tile_b_resid64<LF64, SD64><<<gt, 32 * RG, 0, s>>>(g, U64, view64(m.t64), m.x_hi, m.b, m.r_hi, bst);
+        k_b_rrtrue<256><<<m.nrhs, 256, 0, s>>>(bst);
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
     static int enqueue_start(stag_ctx ctx, BatchSlot& m, const LF64& U64, cudaStream_t s, const double2* x0,
                              double tol, int maxiter, double mass, const double* shifts_dev, double delta)
     {
@@ -490,9 +648,8 @@ struct BatchPlan {
         const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
         const dim3 gb(m.gx, m.nrhs), g1(m.gx, 1);
         k_b_init<SX><<<gb, BBS, 0, s>>>(g.Vh, m.b, x0, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs, tol, maxiter,
-                                        mass * mass, shifts_dev, delta, ctx->scale_k + SLOT_SOLVE);
-        k_b_hop<LF64, SD64, NB64, 1><<<g1, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
-        k_b_resid64<LF64, SD64, NB64><<<g1, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+                                        mass * mass, shifts_dev, delta, ctx->scale_k + SLOT_SOLVE, xdf(m));
+        STAG_TRY(enqueue_hop_resid64(ctx, m, U64, s));
         k_b_finish<S><<<g1, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 1, 0, 0);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
@@ -501,9 +658,22 @@ struct BatchPlan {
     {
         const Geom g = ctx->g;
         const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
-        const dim3 gb(m.gx, m.nrhs), gn(m.gx, (m.nrhs + NB - 1) / NB);
-        k_b_hop<LF, S, NB, 0><<<gn, BBS, 0, s>>>(g, U, spin(m, m.p), spin(m, m.t), m.s_stride, bs);
-        k_b_Mp_dot<LF, S, NB><<<gn, BBS, 0, s>>>(g, U, spin(m, m.t), spin(m, m.p), spin(m, m.Ap), m.s_stride, bs);
+        const dim3 gb(m.gx, m.nrhs);
+        if constexpr (G == 1) {
+            const dim3 gn(m.gx, (m.nrhs + NBT - 1) / NBT);
+            k_b_hop<LF, S, NBT, 0><<<gn, BBS, 0, s>>>(g, U, spin(m, m.p), spin(m, m.t), m.s_stride, bs);
+            k_b_Mp_dot<LF, S, NBT><<<gn, BBS, 0, s>>>(g, U, spin(m, m.t), spin(m, m.p), spin(m, m.Ap), m.s_stride,
+                                                      bs);
+        } else {
+            constexpr int TS = 32 * TileSW<G>::value;
+            const int tiles = (g.Vh + TS - 1) / TS;
+            const BatchScal bst{m.sc, m.nrhs, m.part, ctx->counters + 1, tiles, m.cnt_sys};
+            const dim3 gt(tiles, (m.nrhs + G * NBT - 1) / (G * NBT));
+            k_tile_b_hop<LF, S, G, NBT><<<gt, TS * G, 0, s>>>(g, U, spin(m, m.p), spin(m, m.t), m.s_stride, bst);
+            k_tile_b_Mp_dot<LF, S, G, NBT><<<gt, TS * G, 0, s>>>(g, U, spin(m, m.t), spin(m, m.p), spin(m, m.Ap),
+                                                                 m.s_stride, bst);
+            k_b_alpha<256><<<m.nrhs, 256, 0, s>>>(bst);
+        }
         k_b_update<S, SX><<<gb, BBS, 0, s>>>(g.Vh, spinx(m, m.xlo), m.sx_stride, spin(m, m.r), spin(m, m.p),
                                              spin(m, m.Ap), m.s_stride, bs, lg ? lg->w : 0, lg ? lg->i : 0, use_cond);
         STAG_CUDA_TRY(cudaGetLastError());
@@ -516,9 +686,8 @@ struct BatchPlan {
         const BatchScal bs{m.sc, m.nrhs, m.part, ctx->counters + 1, m.gx, m.cnt_sys};
         // one grid row: the blocks loop over the (usually one or two) systems due
         const dim3 g1(m.gx, 1);
-        k_b_accum_x<SX><<<g1, BBS, 0, s>>>(g.Vh, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs);
-        k_b_hop<LF64, SD64, NB64, 1><<<g1, BBS, 0, s>>>(g, U64, SD64{m.x_hi}, SD64{m.t64}, m.f64_stride, bs);
-        k_b_resid64<LF64, SD64, NB64><<<g1, BBS, 0, s>>>(g, U64, m.t64, m.x_hi, m.b, m.r_hi, bs);
+        k_b_accum_x<SX><<<g1, BBS, 0, s>>>(g.Vh, m.x_hi, spinx(m, m.xlo), m.sx_stride, bs, xdf(m));
+        STAG_TRY(enqueue_hop_resid64(ctx, m, U64, s));
         k_b_finish<S><<<g1, BBS, 0, s>>>(g.Vh, m.r_hi, spin(m, m.r), spin(m, m.p), m.s_stride, bs, 0,
                                          lg ? lg->w : 0, use_cond);
         STAG_CUDA_TRY(cudaGetLastError());
@@ -542,13 +711,13 @@ struct BatchPlan {
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
         STAG_TRY(enqueue_start(ctx, m, U64, ctx->stream, x0, prm.tol, maxiter, mass, shifts_dev, delta));
         if (prm.use_graph) {
-            if (!m.lg.exec || m.graph_nb != NB || m.graph_arith != arith) {
+            if (!m.lg.exec || m.graph_nb != CFG || m.graph_arith != arith) {
                 LoopGraph& lg = m.lg;
                 STAG_TRY(build_loop_graph(
                     ctx->cap_stream, lg, true, [&](cudaStream_t s) { return enqueue_main(ctx, m, U, s, &lg, 1); },
                     [&](cudaStream_t s) { return enqueue_reliable(ctx, m, U64, s, &lg, 1); },
                     [&](cudaStream_t s) { return enqueue_p(ctx, m, s); }));
-                m.graph_nb = NB;
+                m.graph_nb = CFG;
                 m.graph_arith = arith;
             }
             STAG_CUDA_TRY(cudaGraphLaunch(m.lg.exec, ctx->stream));
@@ -575,16 +744,38 @@ struct BatchPlan {
 
 template <class S, class SX, class LF, class LF64, class SD64>
 static int run_with_nb_arith(stag_ctx ctx, BatchSlot& m, const void* lk, const double2* x0, double mass,
-                             const double* shifts_dev, const stag_solver_params& prm, double delta, int nb, int arith)
+                             const double* shifts_dev, const stag_solver_params& prm, double delta, int cfg, int arith)
 {
-    switch (nb) {
-    case 1: return BatchPlan<S, SX, LF, 1, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
-    case 2: return BatchPlan<S, SX, LF, 2, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
-    case 4: return BatchPlan<S, SX, LF, 4, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
-    case 8: return BatchPlan<S, SX, LF, 8, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
-    case 16: return BatchPlan<S, SX, LF, 16, LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, arith);
-    default: set_error("unsupported rhs block %d", nb); return STAG_EINVAL;
+#define STAG_BATCH_CFG(Gv, Nv)                                                                              \
+    case mcfg(Gv, Nv):                                                                                      \
+        return BatchPlan<S, SX, LF, mcfg(Gv, Nv), LF64, SD64>::run(ctx, m, lk, x0, mass, shifts_dev, prm, delta, \
+                                                                   arith)
+    switch (cfg) {
+        STAG_BATCH_CFG(1, 1);
+        STAG_BATCH_CFG(1, 2);
+        STAG_BATCH_CFG(1, 4);
+        STAG_BATCH_CFG(1, 8);
+        STAG_BATCH_CFG(1, 16);
+    default: break;
     }
+    if constexpr (TileOK<LF>::value) {
+        switch (cfg) {
+            STAG_BATCH_CFG(2, 1);
+            STAG_BATCH_CFG(2, 2);
+            STAG_BATCH_CFG(4, 1);
+            STAG_BATCH_CFG(2, 4);
+            STAG_BATCH_CFG(4, 2);
+            STAG_BATCH_CFG(8, 1);
+            STAG_BATCH_CFG(2, 8);
+            STAG_BATCH_CFG(4, 4);
+            STAG_BATCH_CFG(8, 2);
+            STAG_BATCH_CFG(16, 1);
+        default: break;
+        }
+    }
+#undef STAG_BATCH_CFG
+    set_error("unsupported multi-vector configuration (%d groups x %d)", mcfg_G(cfg), mcfg_NBT(cfg));
+    return STAG_EINVAL;
 }
 
 // The double-precision passes follow prm.f64_arith (IEEE double or double-float).
@@ -593,7 +784,7 @@ static int run_with_nb(stag_ctx ctx, BatchSlot& m, const void* lk, const double2
                        const double* shifts_dev, const stag_solver_params& prm, double delta, int nb)
 {
     if (prm.f64_arith == STAG_F64X)
-        return run_with_nb_arith<S, SX, LF, LinkFieldDF<18>, SpinorF64asDF>(ctx, m, lk, x0, mass, shifts_dev, prm,
+        return run_with_nb_arith<S, SX, LF, LinkFieldDF<18>, SpinorDF>(ctx, m, lk, x0, mass, shifts_dev, prm,
                                                                            delta, nb, STAG_F64X);
     if (prm.f64_arith != STAG_F64) {
         set_error("f64_arith must be STAG_F64 or STAG_F64X");

@@ -100,6 +100,7 @@ struct stag_ctx_s {
     int repeat_done;           // tmp_lo_out holds a stag_dslash_repeat result of those fields
     void* tune;                // autotuner cache (tune.cu)
     int last_rhs_block;        // right-hand sides per pass chosen by the last batched solve
+    int last_multi_cfg;        // and its configuration (G << 8 | NBT, multi_tile.cuh)
     // power-of-two normalisation of fields (scale.cu): largest-magnitude bits
     // and exponents per field, SCALE_SLOTS of each
     unsigned long long* scale_bits;
@@ -125,7 +126,9 @@ size_t lo_spinor_bytes(const Geom& g, int prec);
 
 int ensure_lo_tmp_public(stag_ctx ctx, size_t bytes);
 int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs, int nb,
-                 int* nb_used);
+                 int* nb_used, int* cfg_used = nullptr);
+// multi-vector configuration (multi_tile.cuh) used for an explicit rhs block
+int multi_cfg_for(int prec, int block);
 
 // dslash.cu: out = D_{par_out, 1-par_out} in, storage chosen by prec/recon.
 // in/out are in the internal storage of prec (F64: canonical AoS).

@@ -43,25 +43,94 @@ int launch_multi_dslash_nb(stag_ctx ctx, int nb, const LF& U, const S& in, const
     return STAG_OK;
 }
 
+template <class LF, class S, int G, int NBT>
+static int launch_tile(stag_ctx ctx, const LF& U, const S& in, const S& out, size_t stride, int nrhs, int p,
+                       cudaStream_t s)
+{
+    constexpr int TS = 32 * TileSW<G>::value;
+    const dim3 grid((ctx->g.Vh + TS - 1) / TS, (nrhs + G * NBT - 1) / (G * NBT));
+    k_tile_dslash<LF, S, G, NBT><<<grid, TS * G, 0, s>>>(ctx->g, p, U, in, out, stride, nrhs);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
+// One multi-vector operator pass in configuration cfg (multi_tile.cuh):
+// G = 1 the register-blocked kernel with NBT right-hand sides per thread,
+// G > 1 the tile kernel (float arithmetic only).
+template <class LF, class S>
+int launch_multi_cfg(stag_ctx ctx, int cfg, const LF& U, const S& in, const S& out, size_t stride, int nrhs, int p,
+                     cudaStream_t s)
+{
+    if (mcfg_G(cfg) == 1) return launch_multi_dslash_nb(ctx, mcfg_NBT(cfg), U, in, out, stride, nrhs, p, s);
+    if constexpr (TileOK<LF>::value) {
+        switch (cfg) {
+        case mcfg(2, 1): return launch_tile<LF, S, 2, 1>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(2, 2): return launch_tile<LF, S, 2, 2>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(4, 1): return launch_tile<LF, S, 4, 1>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(2, 4): return launch_tile<LF, S, 2, 4>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(4, 2): return launch_tile<LF, S, 4, 2>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(8, 1): return launch_tile<LF, S, 8, 1>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(2, 8): return launch_tile<LF, S, 2, 8>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(4, 4): return launch_tile<LF, S, 4, 4>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(8, 2): return launch_tile<LF, S, 8, 2>(ctx, U, in, out, stride, nrhs, p, s);
+        case mcfg(16, 1): return launch_tile<LF, S, 16, 1>(ctx, U, in, out, stride, nrhs, p, s);
+        default: break;
+        }
+    }
+    set_error("unsupported multi-vector configuration (%d groups x %d)", mcfg_G(cfg), mcfg_NBT(cfg));
+    return STAG_EINVAL;
+}
+
+// The configuration of an explicitly requested rhs block (0: autotuned).
+template <class LF>
+int multi_cfg_of_block(int block)
+{
+    if (!TileOK<LF>::value || block <= 1) return mcfg(1, block < 1 ? 1 : block);
+    return block == 2 ? mcfg(2, 1) : block == 4 ? mcfg(4, 1) : block == 8 ? mcfg(4, 2) : mcfg(4, 4);
+}
+
 // Apply the multi Dslash on internal-storage multi fields; nb = 0 asks the
-// autotuner (timed on these buffers, cached per context and shape).
+// autotuner (timed on these buffers, cached per context and shape) for the
+// configuration; *nb_used receives the right-hand sides sharing a link load.
 template <class LF, class S>
 static int multi_dslash_tuned(stag_ctx ctx, const char* tag, const LF& U, const S& in, const S& out, size_t stride,
-                              int nrhs, int p, int nb, int* nb_used)
+                              int nrhs, int p, int nb, int* nb_used, int* cfg_used = nullptr)
 {
+    int cfg = nb >= 256 ? nb : multi_cfg_of_block<LF>(nb);   // >= 256: an explicit configuration code
+    if (nb >= 256) {
+        bool ok = false;
+        for (int c : multi_cfg_candidates<LF>(16)) ok |= c == cfg;
+        if (!ok) {
+            set_error("multi-vector configuration %d x %d is not offered for this storage", mcfg_G(cfg), mcfg_NBT(cfg));
+            return STAG_EINVAL;
+        }
+    }
     if (nb == 0) {
+        // the default when timing is off: the whole batch per link load (at
+        // most 16; 4 for the register-blocked double kernels)
+        int cap = 1;
+        while (cap < nrhs && cap < 16) cap *= 2;
+        cfg = multi_cfg_of_block<LF>(TileOK<LF>::value ? cap : (cap < 4 ? cap : 4));
         char key[128];
         snprintf(key, sizeof(key), "multi_dslash/%s/nrhs%d", tag, nrhs);
-        STAG_TRY(tune_choice(ctx, key, {1, 2, 4, 8, 16}, nrhs, &nb, [&](int c) {
-            return launch_multi_dslash_nb(ctx, c, U, in, out, stride, nrhs, p, ctx->stream);
+        STAG_TRY(tune_choice(ctx, key, multi_cfg_candidates<LF>(nrhs), &cfg, [&](int c) {
+            return launch_multi_cfg(ctx, c, U, in, out, stride, nrhs, p, ctx->stream);
         }));
     }
-    if (nb_used) *nb_used = nb;
-    return launch_multi_dslash_nb(ctx, nb, U, in, out, stride, nrhs, p, ctx->stream);
+    if (nb_used) *nb_used = mcfg_block(cfg);
+    if (cfg_used) *cfg_used = cfg;
+    return launch_multi_cfg(ctx, cfg, U, in, out, stride, nrhs, p, ctx->stream);
+}
+
+int multi_cfg_for(int prec, int block)
+{
+    if (block >= 256) return block;   // an explicit configuration code
+    return (prec == STAG_F32 || prec == STAG_F16) ? multi_cfg_of_block<LinkField<float2, 12>>(block)
+                                                  : multi_cfg_of_block<LinkField<double2, 18>>(block);
 }
 
 int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs, int nb,
-                 int* nb_used)
+                 int* nb_used, int* cfg_used)
 {
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
@@ -73,29 +142,31 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
         SpinorF64 si{(double2*)in}, so{(double2*)out};
         if (recon == 18)
             return multi_dslash_tuned(ctx, tag, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, stride, nrhs,
-                                      par_out, nb, nb_used);
+                                      par_out, nb, nb_used, cfg_used);
         return multi_dslash_tuned(ctx, tag, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, stride, nrhs,
-                                  par_out, nb, nb_used);
+                                  par_out, nb, nb_used, cfg_used);
     }
     if (prec == STAG_F64X) {
-        SpinorF64asDF si{(double2*)in}, so{(double2*)out};
-        return multi_dslash_tuned(ctx, tag, LinkFieldDF<18>{(const float4*)lk, Vh}, si, so, stride, nrhs, par_out, nb,
-                                  nb_used);
+        // canonical fields in double-float arithmetic go through the
+        // normalising dslash_f64x_canonical, internal ones through
+        // multi_dslash_internal
+        set_error("multi_dslash: double-float fields are not canonical storage here");
+        return STAG_EINVAL;
     }
     if (prec == STAG_F32) {
         SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
         if (recon == 18)
             return multi_dslash_tuned(ctx, tag, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, stride, nrhs,
-                                      par_out, nb, nb_used);
+                                      par_out, nb, nb_used, cfg_used);
         return multi_dslash_tuned(ctx, tag, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, stride, nrhs,
-                                  par_out, nb, nb_used);
+                                  par_out, nb, nb_used, cfg_used);
     }
     SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
     if (recon == 18)
         return multi_dslash_tuned(ctx, tag, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, stride, nrhs,
-                                  par_out, nb, nb_used);
+                                  par_out, nb, nb_used, cfg_used);
     return multi_dslash_tuned(ctx, tag, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, stride, nrhs, par_out,
-                              nb, nb_used);
+                              nb, nb_used, cfg_used);
 }
 
 // The multi operator on a precision's internal storage (as multi_dslash,
@@ -134,8 +205,9 @@ int stag_dslash_multi(stag_ctx ctx, double* out, const double* in, int nrhs, int
         set_error("nrhs must be in [1, %d] and out_parity 0 or 1", STAG_MAX_RHS);
         return STAG_EINVAL;
     }
-    if (rhs_block != 0 && rhs_block != 1 && rhs_block != 2 && rhs_block != 4 && rhs_block != 8 && rhs_block != 16) {
-        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8 or 16");
+    if (rhs_block != 0 && rhs_block != 1 && rhs_block != 2 && rhs_block != 4 && rhs_block != 8 && rhs_block != 16 &&
+        rhs_block < 256) {
+        set_error("rhs_block must be 0 (autotune), 1, 2, 4, 8, 16 or a configuration code (G << 8) | NBT");
         return STAG_EINVAL;
     }
     if (prec < STAG_F64 || prec > STAG_F64X || (recon != 18 && recon != 12) || (prec == STAG_F64X && recon != 18)) {

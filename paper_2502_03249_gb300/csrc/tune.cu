@@ -22,7 +22,7 @@ static TuneCache* cache_of(stag_ctx ctx)
     return (TuneCache*)ctx->tune;
 }
 
-int tune_choice(stag_ctx ctx, const char* key, std::initializer_list<int> candidates, int limit, int* choice,
+int tune_choice(stag_ctx ctx, const char* key, const std::vector<int>& cands, int* choice,
                 const std::function<int(int)>& launch)
 {
     TuneCache* tc = cache_of(ctx);
@@ -31,20 +31,9 @@ int tune_choice(stag_ctx ctx, const char* key, std::initializer_list<int> candid
         *choice = it->second;
         return STAG_OK;
     }
-    int cap = 1;
-    while (cap < limit) cap *= 2;
-    std::vector<int> cands;
-    for (int c : candidates)
-        if (c <= cap) cands.push_back(c);
-    if (cands.empty()) cands.push_back(*candidates.begin());
     const char* env = getenv("STAG_TUNE");
     if (env && strcmp(env, "0") == 0) {
-        // default: the largest candidate not above min(limit, 8)
-        int pick = cands.front();
-        for (int c : cands)
-            if (c <= std::min(limit, 8)) pick = c;
-        tc->best[key] = pick;
-        *choice = pick;
+        tc->best[key] = *choice;   // the caller's default
         return STAG_OK;
     }
     cudaEvent_t e0, e1;

@@ -6,6 +6,7 @@
 
 #include <functional>
 #include <initializer_list>
+#include <vector>
 
 #include "ctx.h"
 
@@ -13,7 +14,7 @@ namespace stag {
 
 // Candidates above the smallest power of two >= limit are skipped.  Must not
 // be called while the context's stream is being captured.
-int tune_choice(stag_ctx ctx, const char* key, std::initializer_list<int> candidates, int limit, int* choice,
+int tune_choice(stag_ctx ctx, const char* key, const std::vector<int>& candidates, int* choice,
                 const std::function<int(int)>& launch);
 
 void free_tune_cache(stag_ctx ctx);

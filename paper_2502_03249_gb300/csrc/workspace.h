@@ -30,6 +30,7 @@ template <> inline SpinorF16 MixedSlot::spinor<SpinorF16>(void* buf) const
 struct BatchSlot {
     void *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr, *xlo = nullptr;
     double2 *x_hi = nullptr, *r_hi = nullptr, *b = nullptr, *t64 = nullptr;
+    double2* x_df = nullptr;       // x_hi split into double-float pairs (double-float reliable updates)
     CgScalars* sc = nullptr;
     double* part = nullptr;
     double* shifts = nullptr;

@@ -152,3 +152,66 @@ def test_batched_graph_and_host_loop_identical(stag, prec, f64_arith):
     assert np.array_equal(out[0][1], out[1][1])
     for k in range(nrhs):
         assert orc.true_residual(dims, U, mass, out[1][1][k], B[k]) <= 1e-10
+
+
+TILE_CODES = [(2, 1), (2, 2), (4, 1), (2, 4), (4, 2), (8, 1), (4, 4), (8, 2), (16, 1)]
+
+
+def code(G, N):
+    return (G << 8) | N
+
+
+@pytest.mark.parametrize("prec,recon", [(1, 12), (1, 18), (2, 12), (2, 18)])
+@pytest.mark.parametrize("dims,nrhs", [((10, 6, 4, 6), 5), ((6, 4, 2, 10), 16)])
+def test_tile_configurations_equal_the_single_vector_operator(stag, prec, recon, dims, nrhs):
+    """Every link-tile configuration (G warp groups sharing one shared-memory
+    tile of hop matrices, NBT right-hand sides per thread; Sec. 4.3 NMULTI)
+    gives the single-vector operator bit for bit, for both output parities,
+    with ragged site tiles (V/2 = 720, 240) and masked right-hand sides."""
+    import torch
+    U = li.random_links(dims, "smooth", eps=0.3, seed=551)
+    psi = li.gaussian_half(dims, seed=552, nvec=nrhs)
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(dev(U))
+    ind = dev(psi)
+    for parity in (0, 1):
+        fn = ctx.dslash_eo if parity == 0 else ctx.dslash_oe
+        single = torch.stack([fn(ctx.new_half(), ind[k], prec, recon) for k in range(nrhs)])
+        for G, N in TILE_CODES:
+            out = ctx.new_half(nrhs)
+            out.fill_(float("nan"))
+            ctx.dslash_multi(out, ind, parity, prec, recon, code(G, N))
+            assert bool((out == single).all()), (G, N, parity)
+
+
+@pytest.mark.parametrize("G,N", [(1, 4), (2, 2), (4, 1), (4, 4), (8, 2), (16, 1)])
+def test_batched_cg_tile_configurations(stag, G, N):
+    """The batched solver with tile configurations: every system at the
+    oracle's true residual; the iterations and reliable updates equal those of
+    the register-blocked configuration (the operator is bit-identical; only
+    the grouping of the <p, Ap> partial sums differs)."""
+    dims, mass, nrhs = (10, 6, 4, 6), 0.05, 7
+    U = li.random_links(dims, "smooth", eps=0.3, seed=561)
+    B = li.gaussian_half(dims, seed=562, nvec=nrhs)
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(dev(U))
+    X = ctx.new_half(nrhs)
+    st = ctx.cg_solve_multi(X, dev(B), mass, tol=1e-10, inner_prec=1, inner_recon=12, rhs_block=code(G, N))
+    assert ctx.last_rhs_block() == G * N
+    xs = host(X)
+    for k in range(nrhs):
+        assert st[k]["status"] == 0
+        assert orc.true_residual(dims, U, mass, xs[k], B[k]) <= 1e-10
+    X1 = ctx.new_half(nrhs)
+    st1 = ctx.cg_solve_multi(X1, dev(B), mass, tol=1e-10, inner_prec=1, inner_recon=12, rhs_block=1)
+    assert max(abs(a["iters"] - b["iters"]) for a, b in zip(st, st1)) <= 2
+
+
+def test_tile_configuration_codes_rejected_for_double_links(stag):
+    dims = (4, 4, 4, 4)
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(dev(li.random_links(dims, "haar", seed=571)))
+    psi = dev(li.gaussian_half(dims, seed=572, nvec=4))
+    with pytest.raises(stag.StagError) as e:
+        ctx.dslash_multi(ctx.new_half(4), psi, 0, 0, 18, code(4, 1))
+    assert e.value.code == -1
