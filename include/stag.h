@@ -364,6 +364,39 @@ int stag_fermion_force_multi(stag_ctx ctx, double *P, double *G, const double *X
  * rhs_block was 0). */
 int stag_last_rhs_block(stag_ctx ctx);
 
+/* ------------------------------------------------------------- autotuner
+ *
+ * Launch shapes the library chooses by timing (the multi-vector operator's
+ * right-hand-side block and tile split of Sec. 4.3's NMULTI, the block sizes
+ * and sites per thread of the solvers' operator and vector kernels).  Each
+ * decision is keyed by "kernel|LxxLyxLzxLt|p<prec>|r<recon>|n<nrhs>|<gpu>"
+ * and timed once: candidates run with CUDA events on the context's stream, L2
+ * flushed before every timed launch, the median of three.  Decisions are kept
+ * in a process-wide cache backed by a JSON file: environment STAG_TUNE_CACHE
+ * (path; empty = no file; default $XDG_CACHE_HOME/stag/tune.json or
+ * $HOME/.cache/stag/tune.json) and STAG_TUNE (0 = never time, use defaults;
+ * 1 or unset = time what the cache lacks; force = time again what came from
+ * the file).  Every candidate of a decision gives the same results bit for
+ * bit; only the time differs.  These functions touch no GPU. */
+
+/* Compose a key into out (len bytes); returns its length or STAG_EINVAL. */
+int stag_tune_make_key(const char *kernel, const int dims[4], int prec, int recon, int nrhs, const char *gpu,
+                       char *out, int len);
+/* Replace the in-memory cache by the entries of a cache file (path NULL: the
+ * default file); returns the number of entries or STAG_EINVAL. */
+int stag_tune_cache_load(const char *path);
+/* Write the in-memory cache to a file (path NULL: the default file). */
+int stag_tune_cache_save(const char *path);
+/* 1 and *choice set if key is cached, else 0. */
+int stag_tune_cache_lookup(const char *key, int *choice);
+/* Put a decision into the in-memory cache. */
+int stag_tune_cache_insert(const char *key, int choice);
+/* Empty the in-memory cache (the default file is not read again) and zero
+ * the counters. */
+void stag_tune_cache_clear(void);
+/* Decisions made by timing, and decisions served from the cache, so far. */
+int stag_tune_stats(long long *timed, long long *from_cache);
+
 /* ------------------------------------------------------------- utilities */
 
 const char *stag_strerror(int code);

@@ -23,7 +23,7 @@ import threading
 __all__ = [
     "F64", "F32", "F16", "F64X", "RECON_18", "RECON_12", "StagError", "NotConverged",
     "load", "build", "Context", "SolverParams", "SolverStats", "StaggeredAction", "fermion_force",
-    "apply_M_noalloc", "NOALLOC_MAX_VH", "fma_probe",
+    "apply_M_noalloc", "NOALLOC_MAX_VH", "fma_probe", "tuner",
 ]
 
 F64, F32, F16, F64X = 0, 1, 2, 3
@@ -112,6 +112,13 @@ def _declare(lib):
         "stag_abi_version": ([], I),
         "stag_apply_M_noalloc": ([ctypes.POINTER(I), P, P, P, D, P], I),
         "stag_fma_probe": ([I, I, ctypes.POINTER(D)], I),
+        "stag_tune_make_key": ([ctypes.c_char_p, ctypes.POINTER(I), I, I, I, ctypes.c_char_p, ctypes.c_char_p, I], I),
+        "stag_tune_cache_load": ([ctypes.c_char_p], I),
+        "stag_tune_cache_save": ([ctypes.c_char_p], I),
+        "stag_tune_cache_lookup": ([ctypes.c_char_p, ctypes.POINTER(I)], I),
+        "stag_tune_cache_insert": ([ctypes.c_char_p, I], I),
+        "stag_tune_cache_clear": ([], None),
+        "stag_tune_stats": ([ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -480,6 +487,45 @@ def fermion_force(U, phi, lattice, mass, **params):
     P = torch.empty_like(U)
     lattice.fermion_force(X, P=P)
     return P
+
+
+class tuner:
+    """The library's autotuner cache (stag_tune_*): keys, file load / save,
+    lookups and counters.  Needs no GPU."""
+
+    @staticmethod
+    def make_key(kernel, dims, prec, recon, nrhs, gpu):
+        buf = ctypes.create_string_buffer(512)
+        d = (ctypes.c_int * 4)(*(int(v) for v in dims))
+        _check(load().stag_tune_make_key(kernel.encode(), d, int(prec), int(recon), int(nrhs), gpu.encode(), buf, 512))
+        return buf.value.decode()
+
+    @staticmethod
+    def load(path=None):
+        return _check(load().stag_tune_cache_load(None if path is None else str(path).encode()))
+
+    @staticmethod
+    def save(path=None):
+        _check(load().stag_tune_cache_save(None if path is None else str(path).encode()))
+
+    @staticmethod
+    def lookup(key):
+        c = ctypes.c_int()
+        return c.value if _check(load().stag_tune_cache_lookup(key.encode(), ctypes.byref(c))) else None
+
+    @staticmethod
+    def insert(key, choice):
+        _check(load().stag_tune_cache_insert(key.encode(), int(choice)))
+
+    @staticmethod
+    def clear():
+        load().stag_tune_cache_clear()
+
+    @staticmethod
+    def stats():
+        t, h = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().stag_tune_stats(ctypes.byref(t), ctypes.byref(h)))
+        return {"timed": t.value, "from_cache": h.value}
 
 
 def fma_probe(prec=F64, iters=None):

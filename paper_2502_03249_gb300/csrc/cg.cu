@@ -8,6 +8,7 @@
 
 #include "cg_df.cuh"
 #include "tgauge.cuh"
+#include "tune.h"
 #include "workspace.h"
 
 namespace stag {
@@ -24,6 +25,32 @@ constexpr int GRAPH_UNROLL = 4;
 typedef LinkField<double2, 18> LF64;
 
 static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
+
+// ------------------------------------------------- tuned launch shapes
+//
+// The autotuner picks, per plan and lattice, the block size of the hop kernel
+// (64, 128 or 256 threads, registers per thread unchanged) and the launch
+// shape of the vector kernels (vcfg: 128 or 256 threads, one or two sites per
+// thread).  Every shape computes the same bits (the reductions use fixed
+// 128-site chunks, common.cuh).
+#define STAG_VEC_SWITCH(cfg, CALL)                                   \
+    switch (cfg) {                                                   \
+    case vcfg(256, 1): { constexpr int BS = 256, SPT = 1; CALL; } break; \
+    case vcfg(128, 1): { constexpr int BS = 128, SPT = 1; CALL; } break; \
+    case vcfg(256, 2): { constexpr int BS = 256, SPT = 2; CALL; } break; \
+    case vcfg(128, 2): { constexpr int BS = 128, SPT = 2; CALL; } break; \
+    default: set_error("bad vector kernel shape %d", cfg); return STAG_EINVAL; \
+    }
+#define STAG_HOP_SWITCH(bs, CALL)                                    \
+    switch (bs) {                                                    \
+    case 128: { constexpr int BS = 128; CALL; } break;               \
+    case 64: { constexpr int BS = 64; CALL; } break;                 \
+    case 256: { constexpr int BS = 256; CALL; } break;               \
+    default: set_error("bad hop block size %d", bs); return STAG_EINVAL; \
+    }
+static inline int vgrid(int Vh, int cfg) { return nblk(Vh, vcfg_BS(cfg) * vcfg_SPT(cfg)); }
+static const std::vector<int> HOP_CANDS = {128, 64, 256};
+static const std::vector<int> VEC_CANDS = {vcfg(256, 1), vcfg(128, 1), vcfg(256, 2), vcfg(128, 2)};
 
 // -------------------------------------------------------------- M apply
 
@@ -126,6 +153,7 @@ int ensure_cg_f64(stag_ctx ctx)
 struct F64Plan {
     typedef LF64 LF;
     static constexpr int slot = 0;
+    static int prepare(stag_ctx) { return STAG_OK; }
     static int start(stag_ctx ctx, const double2* b_in, double mass, double sigma, double tol, int maxiter)
     {
         Workspace* ws = ctx->ws;
@@ -137,19 +165,43 @@ struct F64Plan {
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
-    // one CG iteration (four kernels) on stream s
+    static constexpr const char* name = "cg_f64";
+    static int launch_hop(stag_ctx ctx, const LF& U, int bs, cudaStream_t s, const CgScalars* sc)
+    {
+        Workspace* ws = ctx->ws;
+        STAG_HOP_SWITCH(bs, (k_hop_guarded<LF, SpinorF64, BS><<<nblk(ctx->g.Vh, BS), BS, 0, s>>>(
+                                ctx->g, 1, U, SpinorF64{ws->p}, SpinorF64{ws->t}, sc)));
+        return STAG_OK;
+    }
+    static int launch_update(stag_ctx ctx, int cfg, cudaStream_t s, CgScalars* sc, cudaGraphConditionalHandle cond,
+                             int use_cond)
+    {
+        Workspace* ws = ctx->ws;
+        STAG_VEC_SWITCH(cfg, (k_cg_update<SpinorF64, BS, SPT><<<vgrid(ctx->g.Vh, cfg), BS, 0, s>>>(
+                                 ctx->g.Vh, SpinorF64{ws->x}, SpinorF64{ws->r}, SpinorF64{ws->p}, SpinorF64{ws->Ap},
+                                 sc, ctx->partials, ctx->counters, cond, use_cond)));
+        return STAG_OK;
+    }
+    static int launch_p(stag_ctx ctx, int cfg, cudaStream_t s, const CgScalars* sc)
+    {
+        Workspace* ws = ctx->ws;
+        STAG_VEC_SWITCH(cfg, (k_cg_p<SpinorF64, BS, SPT><<<vgrid(ctx->g.Vh, cfg), BS, 0, s>>>(
+                                 ctx->g.Vh, SpinorF64{ws->r}, SpinorF64{ws->p}, sc)));
+        return STAG_OK;
+    }
+    static bool has_p(stag_ctx) { return true; }
+    // one CG iteration (four kernels) on stream s, in the tuned shapes
     static int enqueue_iter(stag_ctx ctx, const LF& U, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
     {
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
-        const int gh = nblk(g.Vh, HOP_BS), gb = nblk(g.Vh, BLAS_BS);
-        SpinorF64 p{ws->p}, Ap{ws->Ap}, x{ws->x}, r{ws->r}, t{ws->t};
-        k_hop_guarded<LF, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, p, t, ws->sc);
-        k_Mp_dot<LF, SpinorF64, SpinorF64, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, t, p, Ap, ws->sc, ctx->partials,
-                                                                         ctx->counters);
-        k_cg_update<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, x, r, p, Ap, ws->sc, ctx->partials,
-                                                              ctx->counters, cond, use_cond);
-        k_cg_p<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, r, p, ws->sc);
+        const CgShape& sh = ws->cg_shape[slot];
+        SpinorF64 p{ws->p}, Ap{ws->Ap}, t{ws->t};
+        STAG_TRY(launch_hop(ctx, U, sh.hop, s, ws->sc));
+        k_Mp_dot<LF, SpinorF64, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, s>>>(g, U, t, p, Ap, ws->sc,
+                                                                                       ctx->partials, ctx->counters);
+        STAG_TRY(launch_update(ctx, sh.upd, s, ws->sc, cond, use_cond));
+        STAG_TRY(launch_p(ctx, sh.pk, s, ws->sc));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
@@ -197,6 +249,7 @@ struct DFPlanT {
     typedef LFT LF;
     static constexpr int slot = SLOT;
     static SpinorDF v(double2* p) { return SpinorDF{reinterpret_cast<float4*>(p)}; }
+    static int prepare(stag_ctx ctx) { return decide_df_dir(ctx); }
     static int start(stag_ctx ctx, const double2* b_in, double mass, double sigma, double tol, int maxiter)
     {
         Workspace* ws = ctx->ws;
@@ -212,25 +265,52 @@ struct DFPlanT {
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
+    static constexpr const char* name = SLOT == 1 ? "cg_f64x" : "cg_f64x_tg";
+    static int launch_hop(stag_ctx ctx, const LF& U, int bs, cudaStream_t s, const CgScalars* sc)
+    {
+        Workspace* ws = ctx->ws;
+        const Geom g = ctx->g;
+        if (ws->df_dir == 1)
+            STAG_HOP_SWITCH(bs, (k_dfcg_hop<LF, BS><<<nblk(g.Vh, BS), BS, 0, s>>>(g, U, v(ws->r), v(ws->p),
+                                                                                  v(ws->t), sc)))
+        else
+            STAG_HOP_SWITCH(bs, (k_hop_guarded<LF, SpinorDF, BS><<<nblk(g.Vh, BS), BS, 0, s>>>(
+                                    g, 1, U, v(ws->p), v(ws->t), sc)))
+        return STAG_OK;
+    }
+    static int launch_update(stag_ctx ctx, int cfg, cudaStream_t s, CgScalars* sc, cudaGraphConditionalHandle cond,
+                             int use_cond)
+    {
+        Workspace* ws = ctx->ws;
+        STAG_VEC_SWITCH(cfg, (k_dfcg_update<BS, SPT><<<vgrid(ctx->g.Vh, cfg), BS, 0, s>>>(
+                                 ctx->g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), sc, ctx->partials,
+                                 ctx->counters, cond, use_cond)));
+        return STAG_OK;
+    }
+    static int launch_p(stag_ctx ctx, int cfg, cudaStream_t s, const CgScalars* sc)
+    {
+        Workspace* ws = ctx->ws;
+        STAG_VEC_SWITCH(cfg, (k_dfcg_p<BS, SPT><<<vgrid(ctx->g.Vh, cfg), BS, 0, s>>>(ctx->g.Vh, v(ws->r),
+                                                                                      v(ws->p), sc)));
+        return STAG_OK;
+    }
+    // the direction update runs as a pass of its own only without df_dir
+    static bool has_p(stag_ctx ctx) { return ctx->ws->df_dir != 1; }
     static int enqueue_iter(stag_ctx ctx, const LF& U, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
     {
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
-        const int gh = nblk(g.Vh, HOP_BS), gb = nblk(g.Vh, BLAS_BS);
-        if (ws->df_dir == 1) {
-            k_dfcg_hop<LF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->r), v(ws->p), v(ws->t), ws->sc);
+        const CgShape& sh = ws->cg_shape[slot];
+        const int gh = nblk(g.Vh, HOP_BS);
+        STAG_TRY(launch_hop(ctx, U, sh.hop, s, ws->sc));
+        if (ws->df_dir == 1)
             k_dfcg_Mp_dot<LF, HOP_BS, true><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->r), v(ws->p), v(ws->Ap),
                                                                   ws->sc, ctx->partials, ctx->counters);
-            k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), ws->sc,
-                                                          ctx->partials, ctx->counters, cond, use_cond);
-        } else {
-            k_hop_guarded<LF, SpinorDF, HOP_BS><<<gh, HOP_BS, 0, s>>>(g, 1, U, v(ws->p), v(ws->t), ws->sc);
+        else
             k_dfcg_Mp_dot<LF, HOP_BS, false><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->r), v(ws->p), v(ws->Ap),
                                                                    ws->sc, ctx->partials, ctx->counters);
-            k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), ws->sc,
-                                                          ctx->partials, ctx->counters, cond, use_cond);
-            k_dfcg_p<BLAS_BS><<<gb, BLAS_BS, 0, s>>>(g.Vh, v(ws->r), v(ws->p), ws->sc);
-        }
+        STAG_TRY(launch_update(ctx, sh.upd, s, ws->sc, cond, use_cond));
+        if (ws->df_dir != 1) STAG_TRY(launch_p(ctx, sh.pk, s, ws->sc));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
@@ -327,6 +407,49 @@ int free_graph_pair(cudaGraph_t& g, cudaGraphExec_t& e)
     return STAG_OK;
 }
 
+// Scalar record for timing the update kernel alone: never done (tol2 < 0,
+// maxiter at its largest), a fixed alpha.
+__global__ void k_update_time_init(CgScalars* sc)
+{
+    CgScalars s = {};
+    s.rr = 1.0;
+    s.alpha = 1e-3;
+    s.tol2 = -1.0;
+    s.maxiter = 0x7fffffff;
+    *sc = s;
+}
+
+// Choose the plan's launch shapes (once per context and plan, before its
+// graph is built): each candidate runs on the workspace vectors with a scalar
+// record that never reports convergence; the solve then starts from scratch.
+template <class Plan>
+static int tune_cg_plan(stag_ctx ctx, const typename Plan::LF& U)
+{
+    Workspace* ws = ctx->ws;
+    if (ws->cg_tuned[Plan::slot]) return STAG_OK;
+    STAG_TRY(Plan::prepare(ctx));
+    CgScalars* tsc = ws->sc + 63;
+    k_update_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
+    STAG_CUDA_TRY(cudaGetLastError());
+    CgShape sh;
+    const int prec = Plan::slot == 0 ? STAG_F64 : STAG_F64X;
+    char kname[64];
+    snprintf(kname, sizeof(kname), "%s_hop%s", Plan::name, ws->df_dir == 1 && Plan::slot ? "_dir" : "");
+    STAG_TRY(tune_choice(ctx, tune_key(ctx, kname, prec, 18, 1), HOP_CANDS, &sh.hop,
+                         [&](int c) { return Plan::launch_hop(ctx, U, c, ctx->stream, tsc); }));
+    snprintf(kname, sizeof(kname), "%s_update", Plan::name);
+    STAG_TRY(tune_choice(ctx, tune_key(ctx, kname, prec, 18, 1), VEC_CANDS, &sh.upd,
+                         [&](int c) { return Plan::launch_update(ctx, c, ctx->stream, tsc, 0, 0); }));
+    if (Plan::has_p(ctx)) {
+        snprintf(kname, sizeof(kname), "%s_p", Plan::name);
+        STAG_TRY(tune_choice(ctx, tune_key(ctx, kname, prec, 18, 1), VEC_CANDS, &sh.pk,
+                             [&](int c) { return Plan::launch_p(ctx, c, ctx->stream, tsc); }));
+    }
+    ws->cg_shape[Plan::slot] = sh;
+    ws->cg_tuned[Plan::slot] = true;
+    return STAG_OK;
+}
+
 template <class Plan>
 static int cg_solve_plan(stag_ctx ctx, const typename Plan::LF& U, double2* x_out, const double2* b_in, double mass,
                          double sigma, const stag_solver_params& prm, stag_solver_stats* st,
@@ -335,6 +458,7 @@ static int cg_solve_plan(stag_ctx ctx, const typename Plan::LF& U, double2* x_ou
     Workspace* ws = ctx->ws;
     const Geom g = ctx->g;
     const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
+    STAG_TRY(tune_cg_plan<Plan>(ctx, U));
     STAG_TRY(Plan::start(ctx, b_in, mass, sigma, prm.tol, maxiter));
     int restarts = 0;
     CgScalars* hs = ws->sc_host;
@@ -411,18 +535,6 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
     return cg_solve_plan<F64Plan>(ctx, U, x_out, b_in, mass, sigma, prm, st, t0);
 }
 
-// Scalar record for timing the update kernel alone: never done (tol2 < 0,
-// maxiter at its largest), a fixed alpha.
-__global__ void k_update_time_init(CgScalars* sc)
-{
-    CgScalars s = {};
-    s.rr = 1.0;
-    s.alpha = 1e-3;
-    s.tol2 = -1.0;
-    s.maxiter = 0x7fffffff;
-    *sc = s;
-}
-
 void free_workspace(stag_ctx ctx)
 {
     Workspace* ws = ctx->ws;
@@ -464,11 +576,11 @@ int stag_cg_update_time(stag_ctx ctx, int f64_arith, int nrep, double* ms_per_la
     k_update_time_init<<<1, 1, 0, ctx->stream>>>(ws->sc);
     auto launch = [&]() {
         if (f64_arith == STAG_F64X)
-            k_dfcg_update<BLAS_BS><<<gb, BLAS_BS, 0, ctx->stream>>>(Vh, DFPlan::v(ws->x), DFPlan::v(ws->r),
+            k_dfcg_update<BLAS_BS, 1><<<gb, BLAS_BS, 0, ctx->stream>>>(Vh, DFPlan::v(ws->x), DFPlan::v(ws->r),
                                                                    DFPlan::v(ws->p), DFPlan::v(ws->Ap), ws->sc,
                                                                    ctx->partials, ctx->counters, 0, 0);
         else
-            k_cg_update<SpinorF64, BLAS_BS><<<gb, BLAS_BS, 0, ctx->stream>>>(
+            k_cg_update<SpinorF64, BLAS_BS, 1><<<gb, BLAS_BS, 0, ctx->stream>>>(
                 Vh, SpinorF64{ws->x}, SpinorF64{ws->r}, SpinorF64{ws->p}, SpinorF64{ws->Ap}, ws->sc, ctx->partials,
                 ctx->counters, 0, 0);
     };

@@ -90,7 +90,7 @@ struct SpinorDFDir {
 
 // t = D_oe (r + beta p) on odd sites (p itself is updated by Mp_dot).
 template <class LF, int BS>
-__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfcg_hop(Geom g, LF U, SpinorDF r,
+__global__ void __launch_bounds__(BS, (OpMinBlocksBS<LF, SpinorDF, BS>::value)) k_dfcg_hop(Geom g, LF U, SpinorDF r,
                                                                                        SpinorDF p, SpinorDF t,
                                                                                        const CgScalars* sc)
 {
@@ -148,40 +148,72 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfc
     }
 }
 
-// x += alpha p, r -= alpha Ap, rr' = |r|^2; the last block sets beta, the
-// convergence flag and the graph loop's condition.
-template <int BS>
+// chunk_partials (common.cuh) for double-float site values: each warp sums its
+// 32 sites in double-float by a butterfly, converts to double, and the chunk
+// adds its four warp sums in ascending order.
+template <int BS, int SPT>
+__device__ __forceinline__ void chunk_partials_df(const DF* v, double* part, int nchunks, double* smem)
+{
+    constexpr int NW = BS / 32, NCH = BS * SPT / RCHUNK;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        DF x = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const DF y(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
+            x = df_add(x, y);
+        }
+        if (lane == 0) smem[j * NW + w] = df_to_double(x);
+    }
+    __syncthreads();
+    if (threadIdx.x < NCH) {
+        const int c = threadIdx.x, ch = blockIdx.x * NCH + c;
+        const double x = ((smem[4 * c] + smem[4 * c + 1]) + smem[4 * c + 2]) + smem[4 * c + 3];
+        if (ch < nchunks) part[ch] = x;
+    }
+    __syncthreads();
+}
+
+// x += alpha p, r -= alpha Ap, rr' = |r|^2 over SPT sites per thread (partials
+// in 128-site chunks: every launch shape gives the same bits); the last block
+// sets beta, the convergence flag and the graph loop's condition.
+template <int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_dfcg_update(int Vh, SpinorDF x, SpinorDF r, SpinorDF p, SpinorDF Ap,
                                                     CgScalars* sc, double* part, unsigned* cnt,
                                                     cudaGraphConditionalHandle cond, int use_cond)
 {
-    __shared__ double red[BS / 32];
+    __shared__ double red[BS / 32 * SPT];
     __shared__ bool last;
     if (sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
         return;
     }
     const DF alpha = split_double(sc->alpha), nalpha = df_neg(alpha);
-    const int h = blockIdx.x * BS + threadIdx.x;
-    DF d(0);
-    if (h < Vh) {
-        Vec3<DF> xv = x.load_rw(h), rv = r.load_rw(h);
-        const Vec3<DF> pv = p.load(h), av = Ap.load(h);
+    DF d[SPT];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xv.c[c].re = df_fma(alpha, pv.c[c].re, xv.c[c].re);
-            xv.c[c].im = df_fma(alpha, pv.c[c].im, xv.c[c].im);
-            rv.c[c].re = df_fma(nalpha, av.c[c].re, rv.c[c].re);
-            rv.c[c].im = df_fma(nalpha, av.c[c].im, rv.c[c].im);
+    for (int j = 0; j < SPT; ++j) {
+        const int h = (blockIdx.x * SPT + j) * BS + threadIdx.x;
+        d[j] = DF(0);
+        if (h < Vh) {
+            Vec3<DF> xv = x.load_rw(h), rv = r.load_rw(h);
+            const Vec3<DF> pv = p.load(h), av = Ap.load(h);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xv.c[c].re = df_fma(alpha, pv.c[c].re, xv.c[c].re);
+                xv.c[c].im = df_fma(alpha, pv.c[c].im, xv.c[c].im);
+                rv.c[c].re = df_fma(nalpha, av.c[c].re, rv.c[c].re);
+                rv.c[c].im = df_fma(nalpha, av.c[c].im, rv.c[c].im);
+            }
+            x.store(h, xv);
+            r.store(h, rv);
+            df_site_dot(d[j], rv, rv);
         }
-        x.store(h, xv);
-        r.store(h, rv);
-        df_site_dot(d, rv, rv);
     }
-    const double bs = block_sum_df<BS>(d, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    const int nch = (Vh + RCHUNK - 1) / RCHUNK;
+    chunk_partials_df<BS, SPT>(d, part, nch, red);
     if (!arrive_last(cnt, &last)) return;
-    const double rr_new = sum_partials<BS>(part, gridDim.x, red);
+    const double rr_new = sum_chunks<BS>(part, nch, red);
     if (threadIdx.x == 0) {
         *cnt = 0;
         sc->beta = rr_new / sc->rr;
@@ -197,22 +229,25 @@ __global__ void __launch_bounds__(BS) k_dfcg_update(int Vh, SpinorDF x, SpinorDF
     }
 }
 
-// p = r + beta p as a pass of its own (the four-launch iteration)
-template <int BS>
+// p = r + beta p as a pass of its own (the four-launch iteration), SPT sites per thread
+template <int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_dfcg_p(int Vh, SpinorDF r, SpinorDF p, const CgScalars* sc)
 {
     if (sc->done) return;
     const DF beta = split_double(sc->beta);
-    const int h = blockIdx.x * BS + threadIdx.x;
-    if (h >= Vh) return;
-    const Vec3<DF> rv = r.load(h);
-    Vec3<DF> pv = p.load_rw(h);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        pv.c[c].re = df_fma(beta, pv.c[c].re, rv.c[c].re);
-        pv.c[c].im = df_fma(beta, pv.c[c].im, rv.c[c].im);
+    for (int j = 0; j < SPT; ++j) {
+        const int h = (blockIdx.x * SPT + j) * BS + threadIdx.x;
+        if (h >= Vh) return;
+        const Vec3<DF> rv = r.load(h);
+        Vec3<DF> pv = p.load_rw(h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pv.c[c].re = df_fma(beta, pv.c[c].re, rv.c[c].re);
+            pv.c[c].im = df_fma(beta, pv.c[c].im, rv.c[c].im);
+        }
+        p.store(h, pv);
     }
-    p.store(h, pv);
 }
 
 // r = b - ((m^2 + sigma) x - D_eo t)  (t = D_oe x), rr_true = |r|^2.  The

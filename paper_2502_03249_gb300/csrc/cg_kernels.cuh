@@ -32,8 +32,15 @@ __device__ __forceinline__ double site_dot(const Vec3<T>& a, const Vec3<T>& b)
     return (double)s;
 }
 
+// Minimum resident blocks of an operator kernel of BS threads: the 128-thread
+// bound of the link field (OpMinBlocksS) kept at the same registers per thread.
+template <class LF, class S, int BS> struct OpMinBlocksBS {
+    static constexpr int v = OpMinBlocksS<LF, S>::value * 128 / BS;
+    static constexpr int value = v > 0 ? v : 1;
+};
+
 template <class LF, class S, int BS>
-__global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, S>::value)) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
+__global__ void __launch_bounds__(BS, (OpMinBlocksBS<LF, S, BS>::value)) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
 {
     if (sc->done) return;
     const int h = blockIdx.x * BS + threadIdx.x;
@@ -82,11 +89,15 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SD>::value)) k_Mp_dot(Ge
     }
 }
 
-template <class S, int BS>
+// x += alpha p, r -= alpha Ap, rr' = |r|^2 over SPT sites per thread (the
+// partials in 128-site chunks, common.cuh: every launch shape gives the same
+// bits); the last block sets beta, the convergence flag and the graph loop's
+// condition.
+template <class S, int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_cg_update(int Vh, S x, S r, S p, S Ap, CgScalars* sc, double* part,
                                                   unsigned* cnt, cudaGraphConditionalHandle cond, int use_cond)
 {
-    __shared__ double red[BS / 32];
+    __shared__ double red[BS / 32 * SPT];
     __shared__ bool last;
     if (sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
@@ -94,26 +105,30 @@ __global__ void __launch_bounds__(BS) k_cg_update(int Vh, S x, S r, S p, S Ap, C
     }
     typedef typename S::real real;
     const real alpha = (real)sc->alpha;
-    const int h = blockIdx.x * BS + threadIdx.x;
-    double d = 0.0;
-    if (h < Vh) {
-        Vec3<real> xv = x.load_rw(h), rv = r.load_rw(h);
-        const Vec3<real> pv = p.load(h), av = Ap.load(h);
+    double d[SPT];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xv.c[c].re = fma(alpha, pv.c[c].re, xv.c[c].re);
-            xv.c[c].im = fma(alpha, pv.c[c].im, xv.c[c].im);
-            rv.c[c].re = fma(-alpha, av.c[c].re, rv.c[c].re);
-            rv.c[c].im = fma(-alpha, av.c[c].im, rv.c[c].im);
+    for (int j = 0; j < SPT; ++j) {
+        const int h = (blockIdx.x * SPT + j) * BS + threadIdx.x;
+        d[j] = 0.0;
+        if (h < Vh) {
+            Vec3<real> xv = x.load_rw(h), rv = r.load_rw(h);
+            const Vec3<real> pv = p.load(h), av = Ap.load(h);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xv.c[c].re = fma(alpha, pv.c[c].re, xv.c[c].re);
+                xv.c[c].im = fma(alpha, pv.c[c].im, xv.c[c].im);
+                rv.c[c].re = fma(-alpha, av.c[c].re, rv.c[c].re);
+                rv.c[c].im = fma(-alpha, av.c[c].im, rv.c[c].im);
+            }
+            x.store(h, xv);
+            r.store(h, rv);
+            d[j] = site_dot(rv, rv);
         }
-        x.store(h, xv);
-        r.store(h, rv);
-        d = site_dot(rv, rv);
     }
-    const double bs = block_sum<BS>(d, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    const int nch = (Vh + RCHUNK - 1) / RCHUNK;
+    chunk_partials<BS, SPT>(d, part, nch, red);
     if (!arrive_last(cnt, &last)) return;
-    const double rr_new = sum_partials<BS>(part, gridDim.x, red);
+    const double rr_new = sum_chunks<BS>(part, nch, red);
     if (threadIdx.x == 0) {
         *cnt = 0;
         sc->beta = rr_new / sc->rr;
@@ -129,22 +144,34 @@ __global__ void __launch_bounds__(BS) k_cg_update(int Vh, S x, S r, S p, S Ap, C
     }
 }
 
-template <class S, int BS>
+// p = r + beta p over SPT sites per thread
+template <class S, int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_cg_p(int Vh, S r, S p, const CgScalars* sc)
 {
     if (sc->done) return;
     typedef typename S::real real;
     const real beta = (real)sc->beta;
-    const int h = blockIdx.x * BS + threadIdx.x;
-    if (h >= Vh) return;
-    const Vec3<real> rv = r.load(h);
-    Vec3<real> pv = p.load_rw(h);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        pv.c[c].re = fma(beta, pv.c[c].re, rv.c[c].re);
-        pv.c[c].im = fma(beta, pv.c[c].im, rv.c[c].im);
+    for (int j = 0; j < SPT; ++j) {
+        const int h = (blockIdx.x * SPT + j) * BS + threadIdx.x;
+        if (h >= Vh) return;
+        const Vec3<real> rv = r.load(h);
+        Vec3<real> pv = p.load_rw(h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pv.c[c].re = fma(beta, pv.c[c].re, rv.c[c].re);
+            pv.c[c].im = fma(beta, pv.c[c].im, rv.c[c].im);
+        }
+        p.store(h, pv);
     }
-    p.store(h, pv);
+}
+
+// Candidate launch shapes of the vector kernels (vcfg codes), the first the default.
+inline const int* vec_cfgs(int* n)
+{
+    static const int c[] = {vcfg(256, 1), vcfg(128, 1), vcfg(256, 2), vcfg(128, 2)};
+    *n = 4;
+    return c;
 }
 
 template <class LF, class SD, class S, int BS>

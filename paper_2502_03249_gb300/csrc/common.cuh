@@ -582,4 +582,78 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
     return block_sum<BS>(s, smem);
 }
 
+// ------------------------------------- reductions in fixed 128-site chunks
+//
+// The vector kernels the autotuner may launch with different block sizes and
+// sites per thread reduce in a shape that does not depend on either: every
+// partial covers one chunk of 128 consecutive sites (four warps of 32); a warp
+// reduces its 32 sites by a butterfly, the chunk adds its four warp sums in
+// ascending order, and the final sum runs over the chunk partials with 128
+// lanes in a fixed pattern.  All launch shapes therefore give the same bits.
+constexpr int RCHUNK = 128;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// A block of BS threads with SPT sites per thread (thread t of the block holds
+// sites base + j BS + t, base = blockIdx.x BS SPT): v[j] are the threads'
+// per-site values.  Writes the block's BS SPT / 128 chunk partials to
+// part[blockIdx.x * BS * SPT / 128 + c] (chunks past nchunks are skipped).
+// smem: BS / 32 * SPT doubles.  All threads must call it.
+template <int BS, int SPT>
+__device__ __forceinline__ void chunk_partials(const double* v, double* part, int nchunks, double* smem)
+{
+    static_assert((BS * SPT) % RCHUNK == 0 && BS % 32 == 0, "chunks of 128 sites");
+    constexpr int NW = BS / 32, NCH = BS * SPT / RCHUNK;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        const double s = warp_sum(v[j]);
+        if (lane == 0) smem[j * NW + w] = s;   // index = (site offset in the block) / 32
+    }
+    __syncthreads();
+    if (threadIdx.x < NCH) {
+        const int c = threadIdx.x, ch = blockIdx.x * NCH + c;
+        const double x = ((smem[4 * c] + smem[4 * c + 1]) + smem[4 * c + 2]) + smem[4 * c + 3];
+        if (ch < nchunks) part[ch] = x;
+    }
+    __syncthreads();
+}
+
+// Sum of n chunk partials in a fixed order by the first 128 threads of the
+// block (BS >= 128; every thread must call it): lane l adds part[l],
+// part[l + 128], ... in order, then the four warps' butterfly sums are added
+// in ascending order.  Valid in thread 0.  smem: 4 doubles.
+template <int BS>
+__device__ __forceinline__ double sum_chunks(const double* part, int n, double* smem)
+{
+    static_assert(BS >= 128, "128 lanes");
+    double s = 0.0;
+    if (threadIdx.x < 128) {
+        for (int k0 = threadIdx.x; k0 < n; k0 += 8 * 128) {
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (k0 + j * 128 < n) ? __ldcg(part + k0 + j * 128) : 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s += v[j];
+        }
+        s = warp_sum(s);
+        if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    const double r = ((smem[0] + smem[1]) + smem[2]) + smem[3];
+    __syncthreads();
+    return r;
+}
+
+// Launch shape of a vector kernel: block size and sites per thread, coded
+// (BS << 4) | SPT for the autotuner.
+constexpr int vcfg(int BS, int SPT) { return (BS << 4) | SPT; }
+constexpr int vcfg_BS(int c) { return c >> 4; }
+constexpr int vcfg_SPT(int c) { return c & 15; }
+
 }  // namespace stag

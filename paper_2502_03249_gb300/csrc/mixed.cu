@@ -19,6 +19,7 @@
 #include "cg_kernels.cuh"
 #include "df64.cuh"
 #include "graph.h"
+#include "tune.h"
 #include "workspace.h"
 
 namespace stag {
@@ -74,13 +75,15 @@ __global__ void __launch_bounds__(BS) k_mixed_start(int Vh, const double2* b, do
     }
 }
 
-// xlo += alpha p, r -= alpha Ap, rr' = |r|^2; decide whether a reliable update is due.
-template <class S, class SX, int BS>
+// xlo += alpha p, r -= alpha Ap, rr' = |r|^2 over SPT sites per thread
+// (partials in 128-site chunks: every launch shape gives the same bits);
+// decide whether a reliable update is due.
+template <class S, class SX, int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_mixed_update(int Vh, SX x, S r, S p, S Ap, CgScalars* sc, double* part,
                                                      unsigned* cnt, cudaGraphConditionalHandle wh,
                                                      cudaGraphConditionalHandle ih, int use_cond)
 {
-    __shared__ double red[BS / 32];
+    __shared__ double red[BS / 32 * SPT];
     __shared__ bool last;
     if (sc->done) {
         // iterations launched after convergence (host-driven loop) must not
@@ -96,27 +99,31 @@ __global__ void __launch_bounds__(BS) k_mixed_update(int Vh, SX x, S r, S p, S A
     }
     typedef typename S::real real;
     const real alpha = (real)sc->alpha;
-    const int h = blockIdx.x * BS + threadIdx.x;
-    double d = 0.0;
-    if (h < Vh) {
-        Vec3<typename SX::real> xv = x.load_rw(h);
-        Vec3<real> rv = r.load_rw(h);
-        const Vec3<real> pv = p.load(h), av = Ap.load(h);
+    double d[SPT];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xv.c[c].re = fma(alpha, pv.c[c].re, xv.c[c].re);
-            xv.c[c].im = fma(alpha, pv.c[c].im, xv.c[c].im);
-            rv.c[c].re = fma(-alpha, av.c[c].re, rv.c[c].re);
-            rv.c[c].im = fma(-alpha, av.c[c].im, rv.c[c].im);
+    for (int j = 0; j < SPT; ++j) {
+        const int h = (blockIdx.x * SPT + j) * BS + threadIdx.x;
+        d[j] = 0.0;
+        if (h < Vh) {
+            Vec3<typename SX::real> xv = x.load_rw(h);
+            Vec3<real> rv = r.load_rw(h);
+            const Vec3<real> pv = p.load(h), av = Ap.load(h);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xv.c[c].re = fma(alpha, pv.c[c].re, xv.c[c].re);
+                xv.c[c].im = fma(alpha, pv.c[c].im, xv.c[c].im);
+                rv.c[c].re = fma(-alpha, av.c[c].re, rv.c[c].re);
+                rv.c[c].im = fma(-alpha, av.c[c].im, rv.c[c].im);
+            }
+            x.store(h, xv);
+            r.store(h, rv);
+            d[j] = site_dot(rv, rv);
         }
-        x.store(h, xv);
-        r.store(h, rv);
-        d = site_dot(rv, rv);
     }
-    const double bs = block_sum<BS>(d, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    const int nch = (Vh + RCHUNK - 1) / RCHUNK;
+    chunk_partials<BS, SPT>(d, part, nch, red);
     if (!arrive_last(cnt, &last)) return;
-    const double rr_new = sum_partials<BS>(part, gridDim.x, red);
+    const double rr_new = sum_chunks<BS>(part, nch, red);
     if (threadIdx.x == 0) {
         *cnt = 0;
         sc->rr_prev = sc->rr;
@@ -191,21 +198,93 @@ __global__ void __launch_bounds__(BS) k_reliable_finish(int Vh, const double2* r
     }
 }
 
+// Scalar record for timing the inner kernels: never done, never due a
+// reliable update, a fixed alpha and beta.
+__global__ void k_mixed_time_init(CgScalars* sc)
+{
+    CgScalars s = {};
+    s.rr = s.rmax2 = 1.0;
+    s.alpha = 1e-3;
+    s.beta = 0.5;
+    s.tol2 = -1.0;
+    s.delta2 = 0.0;
+    s.maxiter = 0x7fffffff;
+    *sc = s;
+}
+
 // ------------------------------------------------------------- driver
+
+#define STAG_VEC_SWITCH(cfg, CALL)                                             \
+    switch (cfg) {                                                             \
+    case vcfg(256, 1): { constexpr int BS = 256, SPT = 1; CALL; } break;       \
+    case vcfg(128, 1): { constexpr int BS = 128, SPT = 1; CALL; } break;       \
+    case vcfg(256, 2): { constexpr int BS = 256, SPT = 2; CALL; } break;       \
+    case vcfg(128, 2): { constexpr int BS = 128, SPT = 2; CALL; } break;       \
+    default: set_error("bad vector kernel shape %d", cfg); return STAG_EINVAL; \
+    }
+#define STAG_HOP_SWITCH(bs, CALL)                                            \
+    switch (bs) {                                                            \
+    case 128: { constexpr int BS = 128; CALL; } break;                       \
+    case 64: { constexpr int BS = 64; CALL; } break;                         \
+    case 256: { constexpr int BS = 256; CALL; } break;                       \
+    default: set_error("bad hop block size %d", bs); return STAG_EINVAL;     \
+    }
 
 template <class S, class SX, class LF, class LF64T, class SD64>
 struct MixedPlan {
+    // the inner iteration's kernels in the tuned launch shapes (m.shape)
+    static int launch_hop(stag_ctx ctx, MixedSlot& m, const LF& U, int bs, cudaStream_t s, const CgScalars* sc)
+    {
+        const Geom g = ctx->g;
+        S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p);
+        STAG_HOP_SWITCH(bs, (k_hop_guarded<LF, S, BS><<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
+        return STAG_OK;
+    }
+    static int launch_update(stag_ctx ctx, MixedSlot& m, int cfg, cudaStream_t s, CgScalars* sc, LoopGraph* lg,
+                             int use_cond)
+    {
+        const Geom g = ctx->g;
+        S p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap), r = m.template spinor<S>(m.r);
+        SX x = m.template spinor<SX>(m.xlo);
+        STAG_VEC_SWITCH(cfg, (k_mixed_update<S, SX, BS, SPT><<<nblk_m(g.Vh, BS * SPT), BS, 0, s>>>(
+                                 g.Vh, x, r, p, Ap, sc, ctx->partials, ctx->counters, lg ? lg->w : 0,
+                                 lg ? lg->i : 0, use_cond)));
+        return STAG_OK;
+    }
+    static int launch_p(stag_ctx ctx, MixedSlot& m, int cfg, cudaStream_t s, const CgScalars* sc)
+    {
+        S r = m.template spinor<S>(m.r), p = m.template spinor<S>(m.p);
+        STAG_VEC_SWITCH(cfg, (k_cg_p<S, BS, SPT><<<nblk_m(ctx->g.Vh, BS * SPT), BS, 0, s>>>(ctx->g.Vh, r, p, sc)));
+        return STAG_OK;
+    }
+    // launch shapes of the inner kernels, chosen once per slot (timed on the
+    // slot's vectors with a scalar record that never converges)
+    static int tune(stag_ctx ctx, MixedSlot& m, const LF& U, int prec, int recon)
+    {
+        if (m.tuned) return STAG_OK;
+        CgScalars* tsc = ctx->ws->sc + 62;
+        k_mixed_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
+        STAG_CUDA_TRY(cudaGetLastError());
+        CgShape sh;
+        STAG_TRY(tune_choice(ctx, tune_key(ctx, "mixed_hop", prec, recon, 1), {128, 64, 256}, &sh.hop,
+                             [&](int c) { return launch_hop(ctx, m, U, c, ctx->stream, tsc); }));
+        const std::vector<int> vc = {vcfg(256, 1), vcfg(128, 1), vcfg(256, 2), vcfg(128, 2)};
+        STAG_TRY(tune_choice(ctx, tune_key(ctx, "mixed_update", prec, recon, 1), vc, &sh.upd,
+                             [&](int c) { return launch_update(ctx, m, c, ctx->stream, tsc, nullptr, 0); }));
+        STAG_TRY(tune_choice(ctx, tune_key(ctx, "mixed_p", prec, recon, 1), vc, &sh.pk,
+                             [&](int c) { return launch_p(ctx, m, c, ctx->stream, tsc); }));
+        m.shape = sh;
+        m.tuned = true;
+        return STAG_OK;
+    }
     static int enqueue_main(stag_ctx ctx, MixedSlot& m, const LF& U, cudaStream_t s, LoopGraph* lg, int use_cond)
     {
         const Geom g = ctx->g;
-        S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap),
-          r = m.template spinor<S>(m.r);
-        SX x = m.template spinor<SX>(m.xlo);
-        k_hop_guarded<LF, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, 1, U, p, t, m.sc);
+        S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap);
+        STAG_TRY(launch_hop(ctx, m, U, m.shape.hop, s, m.sc));
         k_Mp_dot<LF, S, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, m.sc, ctx->partials,
                                                                            ctx->counters);
-        k_mixed_update<S, SX, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(
-            g.Vh, x, r, p, Ap, m.sc, ctx->partials, ctx->counters, lg ? lg->w : 0, lg ? lg->i : 0, use_cond);
+        STAG_TRY(launch_update(ctx, m, m.shape.upd, s, m.sc, lg, use_cond));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
@@ -228,8 +307,7 @@ struct MixedPlan {
     }
     static int enqueue_p(stag_ctx ctx, MixedSlot& m, cudaStream_t s)
     {
-        S r = m.template spinor<S>(m.r), p = m.template spinor<S>(m.p);
-        k_cg_p<S, MBLAS_BS><<<nblk_m(ctx->g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(ctx->g.Vh, r, p, m.sc);
+        STAG_TRY(launch_p(ctx, m, m.shape.pk, s, m.sc));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
@@ -247,6 +325,7 @@ struct MixedPlan {
         const LF64T U64{(const typename LF64T::store*)lk64, g.Vh};
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
         const double delta = prm.delta > 0 ? prm.delta : 0.1;
+        STAG_TRY(tune(ctx, m, U, prm.inner_prec, prm.inner_recon));
         // b' = 2^-k b (largest component in [1, 2)): the float / half inner
         // storage and the double-float passes stay in range for any b; x = 2^k x'
         STAG_TRY(normalise_fields(ctx, b_in, ws->b, 1, (size_t)3 * g.Vh, SLOT_SOLVE, ctx->stream));

@@ -93,8 +93,9 @@ int multi_cfg_of_block(int block)
 // autotuner (timed on these buffers, cached per context and shape) for the
 // configuration; *nb_used receives the right-hand sides sharing a link load.
 template <class LF, class S>
-static int multi_dslash_tuned(stag_ctx ctx, const char* tag, const LF& U, const S& in, const S& out, size_t stride,
-                              int nrhs, int p, int nb, int* nb_used, int* cfg_used = nullptr)
+static int multi_dslash_tuned(stag_ctx ctx, const char* tag, int tag_prec, int tag_recon, const LF& U, const S& in,
+                              const S& out, size_t stride, int nrhs, int p, int nb, int* nb_used,
+                              int* cfg_used = nullptr)
 {
     int cfg = nb >= 256 ? nb : multi_cfg_of_block<LF>(nb);   // >= 256: an explicit configuration code
     if (nb >= 256) {
@@ -111,8 +112,7 @@ static int multi_dslash_tuned(stag_ctx ctx, const char* tag, const LF& U, const 
         int cap = 1;
         while (cap < nrhs && cap < 16) cap *= 2;
         cfg = multi_cfg_of_block<LF>(TileOK<LF>::value ? cap : (cap < 4 ? cap : 4));
-        char key[128];
-        snprintf(key, sizeof(key), "multi_dslash/%s/nrhs%d", tag, nrhs);
+        const std::string key = tune_key(ctx, tag, tag_prec, tag_recon, nrhs);
         STAG_TRY(tune_choice(ctx, key, multi_cfg_candidates<LF>(nrhs), &cfg, [&](int c) {
             return launch_multi_cfg(ctx, c, U, in, out, stride, nrhs, p, ctx->stream);
         }));
@@ -136,14 +136,12 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
     const int Vh = ctx->g.Vh;
     const size_t stride = lo_spinor_bytes(ctx->g, prec);
-    char tag[32];
-    snprintf(tag, sizeof(tag), "p%d_r%d", prec, recon);
     if (prec == STAG_F64) {
         SpinorF64 si{(double2*)in}, so{(double2*)out};
         if (recon == 18)
-            return multi_dslash_tuned(ctx, tag, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+            return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, stride, nrhs,
                                       par_out, nb, nb_used, cfg_used);
-        return multi_dslash_tuned(ctx, tag, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+        return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, stride, nrhs,
                                   par_out, nb, nb_used, cfg_used);
     }
     if (prec == STAG_F64X) {
@@ -156,16 +154,16 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
     if (prec == STAG_F32) {
         SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
         if (recon == 18)
-            return multi_dslash_tuned(ctx, tag, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+            return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, stride, nrhs,
                                       par_out, nb, nb_used, cfg_used);
-        return multi_dslash_tuned(ctx, tag, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+        return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, stride, nrhs,
                                   par_out, nb, nb_used, cfg_used);
     }
     SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
     if (recon == 18)
-        return multi_dslash_tuned(ctx, tag, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, stride, nrhs,
+        return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, stride, nrhs,
                                   par_out, nb, nb_used, cfg_used);
-    return multi_dslash_tuned(ctx, tag, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, stride, nrhs, par_out,
+    return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, stride, nrhs, par_out,
                               nb, nb_used, cfg_used);
 }
 
@@ -177,7 +175,7 @@ int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* 
     if (prec != STAG_F64X) return multi_dslash(ctx, prec, recon, par_out, out, in, nrhs, nb, nb_used);
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
-    return multi_dslash_tuned(ctx, "p3_r18_df", LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh},
+    return multi_dslash_tuned(ctx, "multi_dslash_df", prec, recon, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh},
                               SpinorDF{(float4*)in}, SpinorDF{(float4*)out}, lo_spinor_bytes(ctx->g, prec), nrhs,
                               par_out, nb, nb_used);
 }

@@ -7,6 +7,13 @@
 
 namespace stag {
 
+// Launch shapes of a CG plan's kernels, chosen by the autotuner (cg.cu).
+struct CgShape {
+    int hop = 128;                 // hop kernel block size
+    int upd = vcfg(256, 1);        // update kernel (vcfg: block size, sites per thread)
+    int pk = vcfg(256, 1);         // direction update kernel
+};
+
 // Buffers of one mixed-precision configuration (inner precision x compression).
 struct MixedSlot {
     void *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr;   // inner precision
@@ -16,6 +23,8 @@ struct MixedSlot {
     int Vh = 0;
     int graph_arith = -1;   // double arithmetic the graph's reliable update was built with
     bool ready = false;
+    CgShape shape;          // launch shapes of the inner kernels (autotuned once)
+    bool tuned = false;
     template <class S> S spinor(void* buf) const;
 };
 template <> inline SpinorF32 MixedSlot::spinor<SpinorF32>(void* buf) const { return SpinorF32{(float2*)buf, Vh}; }
@@ -80,6 +89,8 @@ struct Workspace {
     // double-float CG: 1 applies p = r + beta p inside the operator passes
     // (three launches per iteration), 0 as a pass of its own; -1 undecided
     int df_dir = -1;
+    CgShape cg_shape[3];            // per plan [IEEE double, double-float, temporal gauge]
+    bool cg_tuned[3] = {false, false, false};
     MixedSlot mixed[2][2];          // [F32, F16][18, 12]
     BatchSlot batch[3][2];          // [F64, F32, F16][18, 12]
     MsSlot ms[2];                   // multi-shift [F64, F32]

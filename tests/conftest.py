@@ -9,6 +9,11 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # the library's autotuner keeps its decisions in a file: a private one per
+    # test session, so that runs neither read nor leave a cache elsewhere
+    import tempfile
+    if "STAG_TUNE_CACHE" not in os.environ:
+        os.environ["STAG_TUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="stag_tune_"), "tune.json")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: larger CPU oracle runs")
 
