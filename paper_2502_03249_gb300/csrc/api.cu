@@ -155,9 +155,7 @@ int stag_create(stag_ctx* out, const int dims[4], void* stream)
     stag_ctx ctx = new (std::nothrow) stag_ctx_s();
     if (!ctx) return STAG_ENOMEM;
     memset((void*)ctx, 0, sizeof(*ctx));
-    for (int mu = 0; mu < 4; ++mu) ctx->g.L[mu] = dims[mu];
-    ctx->g.Lxh = dims[0] / 2;
-    ctx->g.Vh = (int)(V / 2);
+    ctx->g = make_geom(dims);
     ctx->V = V;
     ctx->stream = (cudaStream_t)stream;
     ctx->prepared_prec = -1;

@@ -40,11 +40,11 @@ __device__ __forceinline__ void dslash_site_multi(const Geom& g, int p, int h, c
         const Mat3<real> Uf = U.load(p, mu, h);
 #pragma unroll
         for (int k = 0; k < NB; ++k)
-            if (mask & (1u << k)) mv_acc(acc[k], Uf, vflip(in.at(k0 + k, stride).load(s.fwd[mu]), s.sf[mu]));
+            if (mask & (1u << k)) mv_acc(acc[k], Uf, load_flipped(in.at(k0 + k, stride), s.fwd[mu], s.sf[mu]));
         const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
 #pragma unroll
         for (int k = 0; k < NB; ++k)
-            if (mask & (1u << k)) mdv_acc(acc[k], Ub, vflip(in.at(k0 + k, stride).load(s.bwd[mu]), s.sb[mu]));
+            if (mask & (1u << k)) mdv_acc(acc[k], Ub, load_flipped(in.at(k0 + k, stride), s.bwd[mu], s.sb[mu]));
     }
 }
 

@@ -14,11 +14,54 @@ namespace stag {
 // A half field of parity p holds the V/2 sites with (x+y+z+t) mod 2 == p,
 // indexed h = i/2 with i = x + Lx*(y + Ly*(z + Lz*t)).  Writing h = xh + Lxh*r
 // (Lxh = Lx/2, r the row index of (y,z,t)), the site's x is 2*xh + ((p+y+z+t)&1).
+// Division of a non-negative int by an invariant positive divisor with one
+// multiply-high, two adds and two shifts instead of the integer division
+// routine: Granlund and Montgomery's unsigned method ("Division by invariant
+// integers using multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n) gives
+// floor(n / d) = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) for every
+// 0 <= n < 2^32.
+struct FastDiv {
+    uint32_t m;
+    uint32_t s1, s2;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(int d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < (unsigned long long)d) ++l;
+    FastDiv f;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1ull);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ int fast_div(int n, const FastDiv& f)
+{
+    const uint32_t un = (uint32_t)n, t = __umulhi(f.m, un);
+    return (int)((t + ((un - t) >> f.s1)) >> f.s2);
+}
+
 struct Geom {
     int L[4];     // Lx, Ly, Lz, Lt
     int Lxh;      // Lx / 2
     int Vh;       // V / 2
+    FastDiv dxh, dy, dz;   // division by Lxh, Ly, Lz
 };
+
+// Geometry of an Lx x Ly x Lz x Lt lattice (extents even and >= 2).
+__host__ inline Geom make_geom(const int dims[4])
+{
+    Geom g;
+    for (int mu = 0; mu < 4; ++mu) g.L[mu] = dims[mu];
+    g.Lxh = dims[0] / 2;
+    g.Vh = (int)((long long)dims[0] * dims[1] * dims[2] * dims[3] / 2);
+    g.dxh = make_fastdiv(g.Lxh);
+    g.dy = make_fastdiv(dims[1]);
+    g.dz = make_fastdiv(dims[2]);
+    return g;
+}
 
 struct SiteNbrs {
     int h;             // own half index
@@ -35,12 +78,12 @@ struct SiteNbrs {
 __device__ __forceinline__ void site_nbrs(const Geom& g, int p, int h, SiteNbrs& s)
 {
     const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
-    const int r = h / g.Lxh;
+    const int r = fast_div(h, g.dxh);
     const int xh = h - r * g.Lxh;
-    const int y = r % Ly;
-    const int zt = r / Ly;
-    const int z = zt % Lz;
-    const int t = zt / Lz;
+    const int zt = fast_div(r, g.dy);
+    const int y = r - zt * Ly;
+    const int t = fast_div(zt, g.dz);
+    const int z = zt - t * Lz;
     const int x = 2 * xh + ((p + y + z + t) & 1);
     s.h = h;
     const int rowh = g.Lxh * r;
@@ -75,12 +118,12 @@ __device__ __forceinline__ void site_nbrs(const Geom& g, int p, int h, SiteNbrs&
 __device__ __forceinline__ void fwd_nbr(const Geom& g, int p, int h, int mu, int& fw, uint32_t& sf)
 {
     const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
-    const int r = h / g.Lxh;
+    const int r = fast_div(h, g.dxh);
     const int xh = h - r * g.Lxh;
-    const int y = r % Ly;
-    const int zt = r / Ly;
-    const int z = zt % Lz;
-    const int t = zt / Lz;
+    const int zt = fast_div(r, g.dy);
+    const int y = r - zt * Ly;
+    const int t = fast_div(zt, g.dz);
+    const int z = zt - t * Lz;
     const int x = 2 * xh + ((p + y + z + t) & 1);
     const uint32_t SB = 0x80000000u;
     if (mu == 0) {
@@ -479,6 +522,14 @@ struct SpinorF16 {
     }
     __device__ __forceinline__ Vec3<float> load(int h) const { return unpack(__ldg(p + h)); }
     __device__ __forceinline__ Vec3<float> load_rw(int h) const { return unpack(p[h]); }
+    // The site's value times the sign of sign bit sbit: the sign goes onto the
+    // norm (one operation instead of six; code * (-n) = -(code * n) exactly).
+    __device__ __forceinline__ Vec3<float> load_signed(int h, uint32_t sbit) const
+    {
+        uint4 q = __ldg(p + h);
+        q.w ^= sbit;
+        return unpack(q);
+    }
     // Encode: norm = max |component| (float), code = RN_half(component / norm)
     // with an IEEE float division; a zero site stores zeros.
     __device__ __forceinline__ void store(int h, const Vec3<float>& v) const
@@ -500,6 +551,19 @@ struct SpinorF16 {
         p[h] = make_uint4(w[0], w[1], w[2], __float_as_uint(n));
     }
 };
+
+// A neighbour's spinor times the hop's sign (sign bit sbit): the value with
+// its components' signs flipped, or, for storage that can do it with fewer
+// operations (a per-site norm), the same value formed at load.
+template <class S>
+__device__ __forceinline__ Vec3<typename S::real> load_flipped(const S& in, int h, uint32_t sbit)
+{
+    return vflip(in.load(h), sbit);
+}
+__device__ __forceinline__ Vec3<float> load_flipped(const SpinorF16& in, int h, uint32_t sbit)
+{
+    return in.load_signed(h, sbit);
+}
 
 // ------------------------------------------------------------ reductions
 

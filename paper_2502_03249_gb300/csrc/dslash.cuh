@@ -23,10 +23,10 @@ __device__ __forceinline__ Vec3<typename LF::real> dslash_site(const Geom& g, in
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
         const Mat3<real> Uf = U.load(p, mu, h);
-        const Vec3<real> vf = vflip(in.load(s.fwd[mu]), s.sf[mu]);
+        const Vec3<real> vf = load_flipped(in, s.fwd[mu], s.sf[mu]);
         mv_acc(acc, Uf, vf);
         const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
-        const Vec3<real> vb = vflip(in.load(s.bwd[mu]), s.sb[mu]);
+        const Vec3<real> vb = load_flipped(in, s.bwd[mu], s.sb[mu]);
         mdv_acc(acc, Ub, vb);
     }
     return acc;

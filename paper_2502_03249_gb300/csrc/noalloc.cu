@@ -143,10 +143,7 @@ extern "C" int stag_apply_M_noalloc(const int dims[4], const double* U, double* 
     }
     double2* t = nullptr;
     STAG_TRY(noalloc_scratch(&t));
-    Geom g;
-    for (int mu = 0; mu < 4; ++mu) g.L[mu] = dims[mu];
-    g.Lxh = dims[0] / 2;
-    g.Vh = (int)(V / 2);
+    const Geom g = make_geom(dims);
     const LinkCanonicalF64 L{(const double2*)U, g};
     constexpr int BS = 128;
     const int grid = (g.Vh + BS - 1) / BS;
