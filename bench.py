@@ -580,12 +580,14 @@ def section_force(stag, torch, timer, hbm):
     bpl = 144 + 144 + 24
     gbs = bpl * nlinks / (ms_f * 1e-3) * 1e-9
     res = {"workload": w["name"] + " (inputs from the torch generator)",
-           "force_kernel_ms": ms_f, "links": nlinks, "algorithmic_bytes_per_link": bpl, "achieved_gbs": gbs,
-           "frac_of_hbm": gbs / hbm, "action_solve_iters": st["iters"]}
+           "force_call_ms": ms_f, "links": nlinks, "algorithmic_bytes_per_link": bpl, "achieved_gbs": gbs,
+           "frac_of_hbm": gbs / hbm, "action_solve_iters": st["iters"],
+           "force_note": "stag_fermion_force with P only: Y = D_oe X (double-float operator, normalised), the "
+                         "exponents of X and Y, and the force kernel (P in double-float arithmetic)"}
     Ug = U.clone().requires_grad_(True)
 
     def fwd_bwd():
-        S = stag.StaggeredAction(Ug, phi, ctx, mass, tol=TOL)
+        S = stag.StaggeredAction(Ug, phi, ctx, mass, tol=TOL)   # default solver: mixed, float 18-real inner
         S.backward()
         return S
 

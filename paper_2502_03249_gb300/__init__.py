@@ -465,25 +465,32 @@ def StaggeredAction(U, phi, lattice, mass, **params):
 
     U: complex128 (V,4,3,3) CUDA tensor; phi: complex128 (V/2,3) CUDA tensor on
     even sites.  Solver keyword arguments (tol, inner_prec, ...) are passed to
-    stag_fermion_action.  The gradient with respect to U is the Euclidean one
-    (dS/dRe U + i dS/dIm U)."""
+    stag_fermion_action (defaults: _action_params).  The gradient with respect
+    to U is the Euclidean one (dS/dRe U + i dS/dIm U)."""
     global _SA
     if _SA is None:
         _SA = _autograd_function()
+    return _SA.apply(U, phi, lattice, float(mass), _action_params(params))
+
+
+def _action_params(params):
+    """Solver defaults of the action and its force: true residual 1e-10 by the
+    mixed-precision solver (float inner iteration on 18-real links, valid for
+    any complex links, double-precision reliable updates); tolerances below
+    1e-11, near the double-float residual floor, use the double-precision CG."""
     params = dict(params)
-    params.setdefault("tol", 1e-12)
-    params.setdefault("inner_prec", F64)   # exact for any complex links; F32/F16 inner solves assume SU(3)
-    return _SA.apply(U, phi, lattice, float(mass), params)
+    params.setdefault("tol", 1e-10)
+    if "inner_prec" not in params:
+        params["inner_prec"] = F32 if params["tol"] >= 1e-11 else F64
+        params.setdefault("inner_recon", RECON_18)
+    return params
 
 
 def fermion_force(U, phi, lattice, mass, **params):
     """The projected HMC force P = TA(U G^dagger) per link, (V,4,3,3), for S = phi^dagger M^{-1} phi."""
     import torch
     lattice.upload_gauge(U)
-    params = dict(params)
-    params.setdefault("tol", 1e-12)
-    params.setdefault("inner_prec", F64)
-    _, X, _ = lattice.fermion_action(phi, mass, **params)
+    _, X, _ = lattice.fermion_action(phi, mass, **_action_params(params))
     P = torch.empty_like(U)
     lattice.fermion_force(X, P=P)
     return P

@@ -428,7 +428,7 @@ static int tune_cg_plan(stag_ctx ctx, const typename Plan::LF& U)
     Workspace* ws = ctx->ws;
     if (ws->cg_tuned[Plan::slot]) return STAG_OK;
     STAG_TRY(Plan::prepare(ctx));
-    CgScalars* tsc = ws->sc + 63;
+    CgScalars* tsc = ws->sc + 61;   // spare records: 61 CG tuning, 62 mixed tuning, 63 the action
     k_update_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
     STAG_CUDA_TRY(cudaGetLastError());
     CgShape sh;

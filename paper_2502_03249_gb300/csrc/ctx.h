@@ -34,7 +34,7 @@ void set_error(const char* fmt, ...);
 // right-hand sides, an outer solver's (multi-shift) right-hand side, the
 // operator entry points' inputs, and the gauge field.
 constexpr int SCALE_SLOTS = 200;
-constexpr int SLOT_SOLVE = 0, SLOT_OUTER = 64, SLOT_OPER = 128, SLOT_LINKS = SCALE_SLOTS - 1;
+constexpr int SLOT_SOLVE = 0, SLOT_OUTER = 64, SLOT_OPER = 128, SLOT_FORCE = 192, SLOT_LINKS = SCALE_SLOTS - 1;
 constexpr int DF_LINK_SAFE_EXP = 40;
 constexpr int FLOAT_INNER_LINK_EXP = 20;
 

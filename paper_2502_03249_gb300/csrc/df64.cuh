@@ -113,6 +113,40 @@ __device__ __forceinline__ DF split_double(double x)
 
 __device__ __forceinline__ double df_to_double(const DF& v) { return (double)v.hi + (double)v.lo; }
 
+// split_double(2^-k x) with the scaling done on the exponent field (integer
+// operations only): exact, like the split itself, for 2^-k |x| in
+// [2^-74, 2^128).
+__device__ __forceinline__ DF split_double_scaled(double x, int k)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    if (e == 0) return DF(0.f, 0.f);   // zero or subnormal: far below any normalised field's scale
+    const int es = e - k;
+    if (es < 1 || es > 2046) return split_double(scalbn(x, -k));   // outside the double range: the slow path
+    return split_double(__longlong_as_double((long long)((b & ~(0x7FFull << 52)) | ((unsigned long long)es << 52))));
+}
+
+// 2^k f as a double from the float's fields (integer operations only), for a
+// normal float f and a result inside the normal double range (0 for a zero
+// or subnormal f, whose contribution is below the rounding of the sum it
+// enters).
+__device__ __forceinline__ double f2d_scaled(float f, int k)
+{
+    const uint32_t u = __float_as_uint(f);
+    const int e = (int)((u >> 23) & 0xFFu);
+    if (e == 0) return 0.0;
+    const int ed = e + 896 + k;   // 1023 - 127 = 896
+    if (ed < 1 || ed > 2046) return scalbn((double)f, k);
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                            ((unsigned long long)ed << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+// 2^k (hi + lo) in double: one FP64 addition
+__device__ __forceinline__ double df_to_double_scaled(const DF& v, int k)
+{
+    return f2d_scaled(v.hi, k) + f2d_scaled(v.lo, k);
+}
+
 // Canonical double spinor ([h][3] complex128) read and written as double-floats.
 struct SpinorF64asDF {
     typedef DF real;

@@ -16,6 +16,7 @@
 #include <new>
 
 #include "cg_kernels.cuh"
+#include "df64.cuh"
 #include "workspace.h"
 
 namespace stag {
@@ -125,6 +126,140 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
     }
 }
 
+// The same force with the projected P formed in double-float arithmetic (the
+// FP32 pipe: GB300 runs FP64 at 1/64 of the FP32 rate).  u and v enter
+// normalised, u' = 2^-ku sg u and v' = 2^-kv v (ku, kv the exponents of the
+// largest components of the fields they come from, so that every product stays
+// inside the float range), W' = U v' u'^dagger and P' = TA(W') in double-float,
+// and P = 2^(ku + kv) P' in double with an exact scaling.  G = sg u v^dagger,
+// when asked for, is formed in IEEE double as in k_force (18 products of
+// doubles cost less than converting 18 double-float results).  kexp[0] and
+// kexp[1]: the exponents of X and Y.
+__global__ void __launch_bounds__(F_BS) k_force_df(Geom g, LinkFieldDF<18> U, const double2* X, const double2* Y,
+                                                   double2* P, double2* G, double scale, int accumulate,
+                                                   const int* kexp)
+{
+    const long long idx = (long long)blockIdx.x * F_BS + threadIdx.x;
+    if (idx >= 8LL * g.Vh) return;
+    const long long i = idx >> 2;
+    const int mu = (int)(idx & 3);
+    const int x = (int)(i % g.L[0]);
+    long long r = i / g.L[0];
+    const int y = (int)(r % g.L[1]);
+    r /= g.L[1];
+    const int z = (int)(r % g.L[2]);
+    const int t = (int)(r / g.L[2]);
+    const int par = (x + y + z + t) & 1;
+    const int h = (int)(i >> 1);
+    int hf;
+    uint32_t sfb;
+    fwd_nbr(g, par, h, mu, hf, sfb);
+    const double sg = (par == 0 ? 2.0 : -2.0) * (sfb ? -1.0 : 1.0) * scale;
+    const double2* up = par == 0 ? X + (size_t)h * 3 : Y + (size_t)h * 3;
+    const double2* vp = par == 0 ? Y + (size_t)hf * 3 : X + (size_t)hf * 3;
+    const int ku = kexp[par], kv = kexp[1 - par];
+    double2 uq[3], vq[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        uq[a] = __ldg(up + a);
+        vq[a] = __ldg(vp + a);
+    }
+    if (G) {
+        double2* Gp = G + (size_t)idx * 9;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double ure = sg * uq[a].x, uim = sg * uq[a].y;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                double2 o = make_double2(fma(ure, vq[b].x, uim * vq[b].y), fma(uim, vq[b].x, -(ure * vq[b].y)));
+                if (accumulate) {
+                    const double2 q = Gp[a * 3 + b];
+                    o.x += q.x;
+                    o.y += q.y;
+                }
+                Gp[a * 3 + b] = o;
+            }
+        }
+    }
+    if (!P) return;
+    const int ks = ilogb(sg);
+    const DF sgd = split_double_scaled(sg, ks);   // sg = sgd 2^ks, |sgd| in [1, 2)
+    Cplx<DF> u[3], v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const DF ur = split_double_scaled(uq[a].x, ku), ui = split_double_scaled(uq[a].y, ku);
+        u[a] = {DF(0), DF(0)};
+        df_mac(u[a].re, sgd, ur);
+        df_mac(u[a].im, sgd, ui);
+        v[a] = {split_double_scaled(vq[a].x, kv), split_double_scaled(vq[a].y, kv)};
+    }
+    const Mat3<DF> Um = U.load(par, mu, h);
+    Cplx<DF> w[3];   // U v'
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        DF re(0), im(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            df_mac(re, Um.m[a * 3 + c].re, v[c].re);
+            df_mac(re, df_neg(Um.m[a * 3 + c].im), v[c].im);
+            df_mac(im, Um.m[a * 3 + c].re, v[c].im);
+            df_mac(im, Um.m[a * 3 + c].im, v[c].re);
+        }
+        w[a] = {re, im};
+    }
+    // with W = 2 w u^dagger / 2 = w u^dagger (the 2 of P = (W - W^dagger)/2 cancels):
+    //   P_ab = (w_a conj(u_b) - u_a conj(w_b)) / 2 ... written with w halved below
+    // diagonal: P_aa = i (Im(w_a conj(u_a)) - (1/3) sum_c Im(w_c conj(u_c))) times 2 / 2
+    DF d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        DF q(0);
+        df_mac(q, w[a].im, u[a].re);
+        df_mac(q, df_neg(w[a].re), u[a].im);
+        d[a] = q;
+    }
+    const DF tr = df_add(df_add(d[0], d[1]), d[2]);
+    const DF third = split_double(1.0 / 3.0);
+    DF trim(0);
+    df_mac(trim, tr, third);
+    auto offd = [&](int a, int b) {
+        DF re(0), im(0);
+        df_mac(re, w[a].re, u[b].re);
+        df_mac(re, w[a].im, u[b].im);
+        df_mac(re, df_neg(u[a].re), w[b].re);
+        df_mac(re, df_neg(u[a].im), w[b].im);
+        df_mac(im, w[a].im, u[b].re);
+        df_mac(im, df_neg(w[a].re), u[b].im);
+        df_mac(im, df_neg(u[a].im), w[b].re);
+        df_mac(im, u[a].re, w[b].im);
+        return Cplx<DF>{re, im};
+    };
+    const Cplx<DF> p01 = offd(0, 1), p02 = offd(0, 2), p12 = offd(1, 2);
+    // P_ab = (w_a conj(u_b) - u_a conj(w_b)) / 2, P_aa = i (d_a - trim): the
+    // halving and 2^(ku + kv + ks) are one exact scaling of the double result
+    const int k = ku + kv + ks - 1;
+    auto out = [&](const DF& v_) { return df_to_double_scaled(v_, k); };
+    const double d0 = df_to_double_scaled(df_add(d[0], df_neg(trim)), k + 1),
+                 d1 = df_to_double_scaled(df_add(d[1], df_neg(trim)), k + 1),
+                 d2 = df_to_double_scaled(df_add(d[2], df_neg(trim)), k + 1);
+    const double r01 = out(p01.re), i01 = out(p01.im), r02 = out(p02.re), i02 = out(p02.im), r12 = out(p12.re),
+                 i12 = out(p12.im);
+    const double2 Pm[9] = {make_double2(0.0, d0),    make_double2(r01, i01),   make_double2(r02, i02),
+                           make_double2(-r01, i01),  make_double2(0.0, d1),    make_double2(r12, i12),
+                           make_double2(-r02, i02),  make_double2(-r12, i12),  make_double2(0.0, d2)};
+    double2* Pp = P + (size_t)idx * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        double2 o = Pm[e];
+        if (accumulate) {
+            const double2 q = Pp[e];
+            o.x += q.x;
+            o.y += q.y;
+        }
+        Pp[e] = o;
+    }
+}
+
 // out = c X (the gradient 2 dS X of S with respect to phi), canonical half field.
 __global__ void k_scale_copy(long long n, const double2* X, double2* out, double c)
 {
@@ -181,8 +316,19 @@ int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2
     // operator (~1e-14 relative; the IEEE-double one is FP64-bound on GB300)
     STAG_TRY(launch_dslash(ctx, STAG_F64X, 18, 1, ctx->tmp_odd, X, ctx->stream));
     const long long n = 8LL * g.Vh;
-    k_force<LinkField<double2, 18>><<<(unsigned)((n + F_BS - 1) / F_BS), F_BS, 0, ctx->stream>>>(
-        g, U, X, ctx->tmp_odd, P, G, scale, accumulate);
+    const unsigned grid = (unsigned)((n + F_BS - 1) / F_BS);
+    if (P && ctx->df_link_exp == 0 && scale != 0.0 && isfinite(scale)) {
+        // P in double-float arithmetic on the double-float links, X and Y normalised
+        const void* lkdf = nullptr;
+        STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lkdf));
+        STAG_TRY(field_exponents(ctx, X, 1, (size_t)3 * g.Vh, SLOT_FORCE, ctx->stream));
+        STAG_TRY(field_exponents(ctx, ctx->tmp_odd, 1, (size_t)3 * g.Vh, SLOT_FORCE + 1, ctx->stream));
+        k_force_df<<<grid, F_BS, 0, ctx->stream>>>(g, LinkFieldDF<18>{(const float4*)lkdf, g.Vh}, X, ctx->tmp_odd, P,
+                                                   G, scale, accumulate, ctx->scale_k + SLOT_FORCE);
+    } else {
+        k_force<LinkField<double2, 18>><<<grid, F_BS, 0, ctx->stream>>>(g, U, X, ctx->tmp_odd, P, G, scale,
+                                                                        accumulate);
+    }
     if (phi_grad) {
         const long long m = 3LL * g.Vh;
         k_scale_copy<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(m, X, phi_grad, 2.0 * scale);
