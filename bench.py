@@ -374,9 +374,12 @@ def profile_kernel(args, stag, torch):
     parts = kern.split("_")
     w = li.WORKLOADS[WORKLOAD_INDEX]
     dims = tuple(int(v) for v in dtxt.split("x")) if dtxt else w["dims"]
-    U = li.random_links(dims, "smooth", eps=w["eps"], seed=li.workload_seed(WORKLOAD_INDEX, 0))
-    ctx = stag.Context(dims)
-    ctx.upload_gauge(torch.from_numpy(U).cuda())
+    if parts[0] in ("multi", "multishift", "mixed", "force") or (parts[0] == "dslash" and parts[1] == "all"):
+        U = None   # these modes generate their inputs on the device
+    else:
+        U = li.random_links(dims, "smooth", eps=w["eps"], seed=li.workload_seed(WORKLOAD_INDEX, 0))
+        ctx = stag.Context(dims)
+        ctx.upload_gauge(torch.from_numpy(U).cuda())
     if parts[0] in ("multi", "multishift"):
         # the 32^3 x 16 batched (16 RHS) or multi-shift (12 shifts) solve, host-driven
         w3 = li.WORKLOADS[3]
@@ -421,6 +424,40 @@ def profile_kernel(args, stag, torch):
             ctx.cg_solve(x, b, w["mass"], tol=TOL, use_graph=0, f64_arith=arith, temporal_gauge=tg)
         torch.cuda.synchronize()
         print(json.dumps({"profile_kernel": name, "workload": w["name"], "solves": args.warmup + args.steps}))
+        return 0
+    if parts[0] == "dslash" and parts[1] == "all":
+        # one bare operator launch per storage (IEEE double, double-float, float/12,
+        # half/12) on torch-generated inputs of the headline recipe, after
+        # warm-up launches of each
+        ctx = stag.Context(dims)
+        ctx.upload_gauge(li.random_links_torch(dims, "smooth", w["eps"], seed=li.workload_seed(WORKLOAD_INDEX, 0)))
+        psi = li.gaussian_half_torch(dims, seed=99)
+        for prec, recon in ((stag.F64, 18), (stag.F64X, 18), (stag.F32, 12), (stag.F16, 12)):
+            ctx.dslash_prepare(psi, prec)
+            for _ in range(args.warmup):
+                ctx.dslash_repeat(prec, recon, 1)
+        torch.cuda.synchronize()
+        for prec, recon in ((stag.F64, 18), (stag.F64X, 18), (stag.F32, 12), (stag.F16, 12)):
+            ctx.dslash_prepare(psi, prec)
+            ctx.dslash_repeat(prec, recon, 1)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_kernel": name, "dims": list(dims), "launches": 4 * (args.warmup + 1)}))
+        return 0
+    if parts[0] == "force":
+        # the projected force on 32^3 x 16 (64^3 x 16 recipe, eps = 0.3, m = 0.01): X from a solve,
+        # then warm-up and one measured stag_fermion_force call (P only)
+        w5 = li.WORKLOADS[5]
+        dimsf = tuple(int(v) for v in dtxt.split("x")) if dtxt else (32, 32, 32, 16)
+        ctx = stag.Context(dimsf)
+        U5 = li.random_links_torch(dimsf, "smooth", w5["eps"], seed=li.workload_seed(5, 0))
+        ctx.upload_gauge(U5)
+        phi = li.gaussian_half_torch(dimsf, seed=li.workload_seed(5, 1))
+        _, X, _ = ctx.fermion_action(phi, w5["mass"], tol=TOL)
+        P = torch.empty_like(U5)
+        for _ in range(args.warmup + args.steps):
+            ctx.fermion_force(X, P=P)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_kernel": name, "dims": list(dimsf), "calls": args.warmup + args.steps}))
         return 0
     prec = {"f64": stag.F64, "f32": stag.F32, "f16": stag.F16, "f64x": stag.F64X}[parts[1]]
     recon = int(parts[2])
@@ -616,9 +653,10 @@ def main():
                     help="arithmetic of the headline solve (0 IEEE double, the default; 3 double-float)")
     ap.add_argument("--profile-kernel", default=None,
                     help="only run a few launches of one operator on the workload (for ncu): "
-                         "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., or whole host-driven "
-                         "solves cg_f64 / cg_f64x, multi_f32_12 / multishift_f32_12 (32^3 x 16), mixed_f16_12 / "
-                         "mixed_f32_12 (48^3 x 12); optional @LXxLYxLZxLT")
+                         "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., dslash_all (one launch "
+                         "of each storage), or whole host-driven solves cg_f64 / cg_f64x, multi_f32_12 / "
+                         "multishift_f32_12 (32^3 x 16), mixed_f16_12 / mixed_f32_12 (48^3 x 12), or force "
+                         "(32^3 x 16); optional @LXxLYxLZxLT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

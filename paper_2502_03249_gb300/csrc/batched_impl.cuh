@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(BBS, (MultiMinBlocks<LF, NB>::value)) k_b_Mp_d
     const int k0 = blockIdx.y * NB;
     const unsigned mask = mask_active<NB>(bs, k0);
     const int h = blockIdx.x * BBS + threadIdx.x;
-    double d[NB];
+    real d[NB];
 #pragma unroll
-    for (int k = 0; k < NB; ++k) d[k] = 0.0;
+    for (int k = 0; k < NB; ++k) d[k] = real(0);
     if (mask && h < g.Vh) {
         Vec3<real> acc[NB];
         dslash_site_multi<LF, S, NB>(g, 0, h, U, t, stride, k0, mask, acc);
@@ -287,9 +287,9 @@ __global__ void __launch_bounds__(32 * TileSW<G>::value * G, TileMinBlocks<32 * 
     site_nbrs(g, 0, h < g.Vh ? h : g.Vh - 1, s);
     Vec3<real> acc[NBT];
     tile_site_multi<LF, S, G, NBT>(g, 0, h, s, U, t, stride, k0, mask, sm, acc);
-    double d[NBT];
+    real d[NBT];
 #pragma unroll
-    for (int k = 0; k < NBT; ++k) d[k] = 0.0;
+    for (int k = 0; k < NBT; ++k) d[k] = real(0);
     if (h < g.Vh) {
 #pragma unroll
         for (int k = 0; k < NBT; ++k) {
@@ -308,9 +308,7 @@ __global__ void __launch_bounds__(32 * TileSW<G>::value * G, TileMinBlocks<32 * 
     }
 #pragma unroll
     for (int k = 0; k < NBT; ++k) {
-        double x = d[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        const double x = warp_sum(d[k]);
         if (lane == 0) wsum[w * NBT + k] = x;
     }
     __syncthreads();
@@ -432,7 +430,7 @@ __global__ void __launch_bounds__(BBS) k_b_update(int Vh, SX x, size_t sx_stride
     typedef typename S::real real;
     const int k = blockIdx.y, h = blockIdx.x * BBS + threadIdx.x;
     const bool on = active(bs.sc[k]);
-    double d = 0.0;
+    real d = real(0);
     if (on && h < Vh) {
         const real alpha = (real)bs.sc[k].alpha;
         const SX xk = x.at(k, sx_stride);

@@ -14,14 +14,16 @@
 #pragma once
 
 #include "ctx.h"
+#include "df64.cuh"
 #include "dslash.cuh"
 
 namespace stag {
 
-// Site contribution to a real inner product; float sites are summed in float
-// first (six terms) and enter the block sum in double.
+// Site contribution to a real inner product in the storage's arithmetic
+// (float sites: six terms in float; the block sums of float values run in
+// float-float and end in double, df64.cuh).
 template <typename T>
-__device__ __forceinline__ double site_dot(const Vec3<T>& a, const Vec3<T>& b)
+__device__ __forceinline__ T site_dot(const Vec3<T>& a, const Vec3<T>& b)
 {
     T s = T(0);
 #pragma unroll
@@ -29,7 +31,7 @@ __device__ __forceinline__ double site_dot(const Vec3<T>& a, const Vec3<T>& b)
         s = fma(a.c[c].re, b.c[c].re, s);
         s = fma(a.c[c].im, b.c[c].im, s);
     }
-    return (double)s;
+    return s;
 }
 
 // Minimum resident blocks of an operator kernel of BS threads: the 128-thread
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SD>::value)) k_Mp_dot(Ge
     typedef typename S::real real;
     const real m2s = (real)(sc->m2 + sc->sigma);
     const int h = blockIdx.x * BS + threadIdx.x;
-    double d = 0.0;
+    real d = real(0);
     if (h < g.Vh) {
         const Vec3<real> Dt = vconv<real>(dslash_site(g, 0, h, U, t));
         const Vec3<real> pv = p.load(h);
@@ -105,11 +107,11 @@ __global__ void __launch_bounds__(BS) k_cg_update(int Vh, S x, S r, S p, S Ap, C
     }
     typedef typename S::real real;
     const real alpha = (real)sc->alpha;
-    double d[SPT];
+    real d[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
         const int h = (blockIdx.x * SPT + j) * BS + threadIdx.x;
-        d[j] = 0.0;
+        d[j] = real(0);
         if (h < Vh) {
             Vec3<real> xv = x.load_rw(h), rv = r.load_rw(h);
             const Vec3<real> pv = p.load(h), av = Ap.load(h);

@@ -310,6 +310,87 @@ struct LinkFieldDF {
     }
 };
 
+// ------------------------------------------- sums of float site values
+//
+// The reductions of the float kernels (the mixed and batched solvers' inner
+// iterations) add float site values across the warp in float-float
+// arithmetic (Knuth's TwoSum, FP32 pipe) and convert the warp sum to double
+// once: no FP64 addition per lane, which on GB300 (FP64 at 1/64 of the FP32
+// rate) cost a sizable part of those kernels.  Same fixed butterfly shape as
+// the double sums, so the results do not depend on the launch shape.
+
+// Warp sum of one float per lane, in double (every lane gets the same bits).
+__device__ __forceinline__ double warp_sum(float v)
+{
+    DF x(v, 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DF y(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
+        x = df_add(x, y);
+    }
+    return df_to_double_scaled(x, 0);
+}
+
+// block_sum (common.cuh) of float values
+template <int BS>
+__device__ __forceinline__ double block_sum(float v, double* smem)
+{
+    const double x = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) smem[w] = x;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (l < BS / 32) ? smem[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;
+}
+
+// block_sum_n (common.cuh) of float values
+template <int BS, int NB>
+__device__ __forceinline__ double block_sum_n(const float* v, unsigned mask, double* smem)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (!(mask & (1u << k))) continue;
+        const double x = warp_sum(v[k]);
+        if (l == 0) smem[w * NB + k] = x;
+    }
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < NB && (mask & (1u << threadIdx.x))) {
+#pragma unroll
+        for (int ww = 0; ww < BS / 32; ++ww) s += smem[ww * NB + threadIdx.x];
+    }
+    __syncthreads();
+    return s;
+}
+
+// chunk_partials (common.cuh) of float values
+template <int BS, int SPT>
+__device__ __forceinline__ void chunk_partials(const float* v, double* part, int nchunks, double* smem)
+{
+    static_assert((BS * SPT) % RCHUNK == 0 && BS % 32 == 0, "chunks of 128 sites");
+    constexpr int NW = BS / 32, NCH = BS * SPT / RCHUNK;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        const double s = warp_sum(v[j]);
+        if (lane == 0) smem[j * NW + w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NCH) {
+        const int c = threadIdx.x, ch = blockIdx.x * NCH + c;
+        const double x = ((smem[4 * c] + smem[4 * c + 1]) + smem[4 * c + 2]) + smem[4 * c + 3];
+        if (ch < nchunks) part[ch] = x;
+    }
+    __syncthreads();
+}
+
 template <int R> struct OpMinBlocks<LinkFieldDF<R>> { static constexpr int value = 5; };
 // on double-float vectors (no conversions) the operator fits 72 registers:
 // 7 blocks per SM, 32^3 x 8 in 1.2 waves (measured 30.4 against 32.3 us;

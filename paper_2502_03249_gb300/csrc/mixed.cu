@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(BS) k_mixed_update(int Vh, SX x, S r, S p, S A
     }
     typedef typename S::real real;
     const real alpha = (real)sc->alpha;
-    double d[SPT];
+    real d[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
         const int h = (blockIdx.x * SPT + j) * BS + threadIdx.x;
-        d[j] = 0.0;
+        d[j] = real(0);
         if (h < Vh) {
             Vec3<typename SX::real> xv = x.load_rw(h);
             Vec3<real> rv = r.load_rw(h);

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(BS) k_ms_update(int Vh, S r, S Ap, S P, S X, s
     __syncthreads();
     const real alpha = (real)sc->alpha;
     const int h = blockIdx.x * BS + threadIdx.x;
-    double d = 0.0;
+    real d = real(0);
     if (h < Vh) {
         Vec3<real> rv = r.load_rw(h);
         const Vec3<real> av = Ap.load(h);
