@@ -471,6 +471,43 @@ def profile_kernel(args, stag, torch):
     return 0
 
 
+MULTI_CONFIGS = [(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 2), (4, 1), (2, 4), (4, 2), (8, 1), (2, 8), (4, 4),
+                 (8, 2), (16, 1)]   # (G warp groups sharing a link tile, NBT right-hand sides per thread)
+
+
+def sweep_multi(args, stag, torch):
+    """Every multi-vector configuration on the paper's Table 2 lattice recipe
+    (smooth links eps = 0.3): TFLOP/s (570 flop per site per vector) and the
+    fraction of the HBM roof of the compulsory bytes, (384 + 48 n) / n B per
+    site-vector for float/12 and (192 + 32 n) / n for half/12."""
+    dims = tuple(int(v) for v in args.sweep_multi.split("x"))
+    Vh = li.volume(dims) // 2
+    hbm = float(load_peaks()[0]["hbm_gbs"])
+    ctx = stag.Context(dims)
+    ctx.upload_gauge(li.random_links_torch(dims, "smooth", 0.3, seed=li.workload_seed(6, 0)))
+    psi = li.gaussian_half_torch(dims, seed=li.workload_seed(6, 1), nvec=16)
+    timer = Timer(torch, L2Flush(torch, torch.device("cuda", torch.cuda.current_device())))
+    for label, prec, lb, sb in (("f32_12", stag.F32, 384, 48), ("f16_12", stag.F16, 192, 32)):
+        for n in (1, 2, 4, 8, 16):
+            ctx.dslash_prepare_multi(psi[:n].contiguous(), prec)
+            cap = 1
+            while cap < n:
+                cap *= 2
+            roof = hbm * 1e9 / ((lb + sb * n) / n) * FLOP_PER_SITE * 1e-12
+            row = {}
+            for G, N in MULTI_CONFIGS:
+                if G * N > cap:
+                    continue
+                ms, _ = timer(lambda: ctx.dslash_repeat_multi(prec, 12, (G << 8) | N, 1), reps=7, warm=2)
+                tf = FLOP_PER_SITE * Vh * n / (ms * 1e-3) * 1e-12
+                row[f"{G}x{N}"] = {"us": round(ms * 1e3, 1), "tflops": round(tf, 2), "frac": round(tf / roof, 3)}
+            ctx.dslash_repeat_multi(prec, 12, 0, 1)
+            best = max(row.items(), key=lambda kv: kv[1]["tflops"])
+            print(json.dumps({"storage": label, "dims": list(dims), "n": n, "roof_tflops": round(roof, 2),
+                              "autotuned_block": ctx.last_rhs_block(), "best": best, "configs": row}), flush=True)
+    return 0
+
+
 def half_dslash(st):
     # two half-Dslashes per M application, one more M per true-residual check
     return 2 * (st["iters"] + st["restarts"] + 1)
@@ -651,6 +688,10 @@ def main():
                     help="1: device-side loop in one CUDA graph; 0: host-driven loop (per-kernel profiling)")
     ap.add_argument("--f64-arith", type=int, default=F64_IEEE, choices=[F64_IEEE, F64X],
                     help="arithmetic of the headline solve (0 IEEE double, the default; 3 double-float)")
+    ap.add_argument("--sweep-multi", default=None, metavar="LXxLYxLZxLT",
+                    help="time every multi-vector configuration (the link-tile split G x NBT and the "
+                         "register-blocked blocks) for n = 1, 2, 4, 8, 16 vectors, float and half 12-real, one "
+                         "JSON line per (storage, n); CUDA events, L2 flushed before each launch")
     ap.add_argument("--profile-kernel", default=None,
                     help="only run a few launches of one operator on the workload (for ncu): "
                          "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., dslash_all (one launch "
@@ -672,6 +713,8 @@ def main():
     stag.load()
     if args.profile_kernel:
         return profile_kernel(args, stag, torch)
+    if args.sweep_multi:
+        return sweep_multi(args, stag, torch)
 
     w = li.WORKLOADS[WORKLOAD_INDEX]
     dims, mass = w["dims"], w["mass"]

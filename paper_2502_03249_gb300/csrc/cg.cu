@@ -213,7 +213,7 @@ struct F64Plan {
         k_hop<LF, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(g, 1, U, SpinorF64{ws->x},
                                                                                     SpinorF64{ws->t}, nullptr, 0);
         k_true_resid_f64<LF, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, ctx->stream>>>(
-            g, U, ws->t, ws->x, ws->b, ws->r, ws->sc, ctx->partials, ctx->counters, 0);
+            g, U, SpinorF64{ws->t}, ws->x, ws->b, ws->r, ws->sc, ctx->partials, ctx->counters, 0);
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }

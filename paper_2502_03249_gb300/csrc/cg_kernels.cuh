@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, S>::value)) k_hop(Geom g
 // r = b - (m^2 + sigma) x + D_eo t  (t = D_oe x), rr_true = |r|^2, double precision.
 // With guard set, only when a reliable update is due.
 template <class LF, class SD, int BS>
-__global__ void __launch_bounds__(BS) k_true_resid_f64(Geom g, LF U, const double2* t, const double2* x,
+__global__ void __launch_bounds__(BS) k_true_resid_f64(Geom g, LF U, SD t, const double2* x,
                                                        const double2* b, double2* r, CgScalars* sc, double* part,
                                                        unsigned* cnt, int guard)
 {
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(BS) k_true_resid_f64(Geom g, LF U, const doubl
     double d = 0.0;
     const double m2s = sc->m2 + sc->sigma;
     if (h < g.Vh) {
-        const Vec3<double> Dt = vconv<double>(dslash_site(g, 0, h, U, SD{(double2*)t}));
+        const Vec3<double> Dt = vconv<double>(dslash_site(g, 0, h, U, t));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double2 xv = x[(size_t)h * 3 + c], bv = b[(size_t)h * 3 + c];

@@ -142,8 +142,11 @@ __global__ void __launch_bounds__(BS) k_mixed_update(int Vh, SX x, S r, S p, S A
 }
 
 // x_hi += xlo (double), xlo = 0.
+// x_df (double-float arithmetic only, else NULL) keeps x_hi split into
+// double-float pairs, the storage the reliable update's operator reads.
 template <class SX, int BS>
-__global__ void __launch_bounds__(BS) k_accum_x(int Vh, double2* x_hi, SX xlo, const CgScalars* sc, int guard)
+__global__ void __launch_bounds__(BS) k_accum_x(int Vh, double2* x_hi, SX xlo, const CgScalars* sc, int guard,
+                                                float4* x_df)
 {
     if (guard && !sc->reliable) return;
     const int h = blockIdx.x * BS + threadIdx.x;
@@ -156,6 +159,10 @@ __global__ void __launch_bounds__(BS) k_accum_x(int Vh, double2* x_hi, SX xlo, c
         xv.x += (double)v.c[c].re;
         xv.y += (double)v.c[c].im;
         x_hi[(size_t)h * 3 + c] = xv;
+        if (x_df) {
+            const DF re = split_double(xv.x), im = split_double(xv.y);
+            x_df[(size_t)h * 3 + c] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
         z.c[c].re = z.c[c].im = 0;
     }
     xlo.store(h, z);
@@ -295,11 +302,16 @@ struct MixedPlan {
         Workspace* ws = ctx->ws;
         SX x = m.template spinor<SX>(m.xlo);
         S r = m.template spinor<S>(m.r);
-        k_accum_x<SX, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(g.Vh, ws->x, x, m.sc, guard);
-        k_hop<LF64T, SD64, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, 1, U64, SD64{ws->x},
-                                                                                SD64{ws->t}, m.sc, guard);
+        // double-float arithmetic reads x as double-float pairs kept in the
+        // workspace's p (unused by this solver), and t in the same storage
+        constexpr bool DFX = std::is_same<SD64, SpinorDF>::value;
+        typedef typename std::conditional<DFX, float4, double2>::type VT;
+        const SD64 xin{(VT*)(DFX ? ws->p : ws->x)}, tv{(VT*)ws->t};
+        k_accum_x<SX, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(g.Vh, ws->x, x, m.sc, guard,
+                                                                           DFX ? (float4*)ws->p : nullptr);
+        k_hop<LF64T, SD64, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, 1, U64, xin, tv, m.sc, guard);
         k_true_resid_f64<LF64T, SD64, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(
-            g, U64, ws->t, ws->x, ws->b, ws->r, m.sc, ctx->partials, ctx->counters, guard);
+            g, U64, tv, ws->x, ws->b, ws->r, m.sc, ctx->partials, ctx->counters, guard);
         k_reliable_finish<S, MBLAS_BS><<<nblk_m(g.Vh, MBLAS_BS), MBLAS_BS, 0, s>>>(g.Vh, ws->r, r, m.sc,
                                                                                   lg ? lg->w : 0, use_cond, guard);
         STAG_CUDA_TRY(cudaGetLastError());
@@ -435,7 +447,7 @@ int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mas
     STAG_TRY(ensure_links(ctx, prec, recon, &lk));
     int arith = STAG_F64;
     STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &arith));
-    if (arith == STAG_F64X) return dispatch_inner<LinkFieldDF<18>, SpinorF64asDF>(ctx, *m, lk, x_out, b_in, mass, prm, st);
+    if (arith == STAG_F64X) return dispatch_inner<LinkFieldDF<18>, SpinorDF>(ctx, *m, lk, x_out, b_in, mass, prm, st);
     return dispatch_inner<LinkField<double2, 18>, SpinorF64>(ctx, *m, lk, x_out, b_in, mass, prm, st);
 }
 
