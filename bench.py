@@ -60,6 +60,13 @@ def dslash_bytes_per_site(prec_bytes: int, recon: int) -> int:
     return 8 * recon * prec_bytes + 2 * 6 * prec_bytes
 
 
+# the same in temporal gauge (Sec. 4.3): the 6 spatial links, and a time link
+# only where it is not the identity (the forward one on the last slice, the
+# backward one on slice 0: 2 / Lt links per site on average)
+def dslash_bytes_per_site_tg(prec_bytes: int, recon: int, lt: int) -> float:
+    return (6 + 2.0 / lt) * recon * prec_bytes + 2 * 6 * prec_bytes
+
+
 def paper_float_count(n: int = 1) -> int:
     """Floats per site in the paper's model (Sec. 4.3): 6 links x 12 + n x 9 vectors x 6."""
     return 6 * 12 + n * 9 * 6
@@ -356,15 +363,23 @@ class Timer:
         return statistics.median(ts), out
 
 
-def dslash_kernel_entry(timer, ctx, psi, out, prec, recon, vh, hbm):
-    """The bare operator kernel (internal storage, no conversions), one launch per timing."""
+def dslash_kernel_entry(timer, ctx, psi, out, prec, recon, vh, hbm, tg=False):
+    """The bare operator kernel (internal storage, no conversions), one launch per timing.
+    tg: on the temporal-gauge links, identity time links skipped (GFLOP/s then
+    counts the paper's 570 flop per site although the skipped hops do less)."""
+    import paper_2502_03249_gb300 as stag
+    ctx.set_operator_links(stag.LINKS_TEMPORAL if tg else stag.LINKS_UPLOADED)
     ctx.dslash_prepare(psi, prec)
     ms, _ = timer(lambda: ctx.dslash_repeat(prec, recon, 1), reps=20, warm=3)
+    ctx.set_operator_links(stag.LINKS_UPLOADED)
     pb = {0: 8, 3: 8, 1: 4, 2: 2}[prec]
-    per_site = dslash_bytes_per_site(pb, recon) + (8 if prec == 2 else 0)
+    lt = ctx.dims[3]
+    per_site = (dslash_bytes_per_site_tg(pb, recon, lt) if tg else dslash_bytes_per_site(pb, recon)) + \
+        (8 if prec == 2 else 0)
     gbs = per_site * vh / (ms * 1e-3) * 1e-9
     return {"ms": ms, "gflops": FLOP_PER_SITE * vh / (ms * 1e-3) * 1e-9, "achieved_gbs": gbs,
-            "frac_of_hbm": gbs / hbm, "algorithmic_bytes_per_site": per_site}
+            "frac_of_hbm": gbs / hbm, "algorithmic_bytes_per_site": per_site,
+            "links": "temporal gauge (6 + 2/Lt link reads per site)" if tg else "as uploaded (8 per site)"}
 
 
 def profile_kernel(args, stag, torch):
@@ -564,6 +579,11 @@ def section_32c16(stag, torch, timer):
     res["batched_16rhs_f32_12"] = {"time_to_solution_ms": ms_b, "rhs_block": ctx.last_rhs_block(),
                                    "max_iters": max(s["iters"] for s in st),
                                    "max_true_rel_residual": max(s["true_rel_residual"] for s in st)}
+    ms_t, st = timer(lambda: ctx.cg_solve_multi(X, B, mass, tol=TOL, inner_prec=stag.F32, inner_recon=12,
+                                                temporal_gauge=1), reps=2)
+    res["batched_16rhs_f32_12_temporal_gauge"] = {"time_to_solution_ms": ms_t, "rhs_block": ctx.last_rhs_block(),
+                                                  "max_iters": max(s["iters"] for s in st),
+                                                  "max_true_rel_residual": max(s["true_rel_residual"] for s in st)}
     xs = ctx.new_half()
 
     def seq_f64():
@@ -577,6 +597,9 @@ def section_32c16(stag, torch, timer):
     ms_m, st = timer(lambda: ctx.cg_solve_multishift(Xs, b, SHIFTS12, mass, tol=TOL), reps=2)
     res["multishift_12"] = {"time_to_solution_ms": ms_m, "krylov_iters": st[0]["restarts"],
                             "max_true_rel_residual": max(s["true_rel_residual"] for s in st)}
+    ms_mt, st = timer(lambda: ctx.cg_solve_multishift(Xs, b, SHIFTS12, mass, tol=TOL, temporal_gauge=1), reps=2)
+    res["multishift_12_temporal_gauge"] = {"time_to_solution_ms": ms_mt, "krylov_iters": st[0]["restarts"],
+                                           "max_true_rel_residual": max(s["true_rel_residual"] for s in st)}
 
     def seq_shifted():
         return [ctx.cg_solve_shifted(xs, b, mass, s, tol=TOL) for s in SHIFTS12]
@@ -609,7 +632,9 @@ def section_paper_tables(stag, torch, timer, hbm):
     ctx.upload_gauge(li.random_links_torch(dims, w6["links"], w6["eps"], seed=li.workload_seed(6, 0)))
     psi = li.gaussian_half_torch(dims, seed=li.workload_seed(6, 1), nvec=16)
     scan = {}
-    for label, prec, recon in (("f32_12", stag.F32, 12), ("f64x_18", stag.F64X, 18), ("f64_12", stag.F64, 12)):
+    for label, prec, recon in (("f32_12", stag.F32, 12), ("f32_12_temporal_gauge", stag.F32, 12),
+                               ("f16_12", stag.F16, 12), ("f64x_18", stag.F64X, 18), ("f64_12", stag.F64, 12)):
+        ctx.set_operator_links(stag.LINKS_TEMPORAL if label.endswith("temporal_gauge") else stag.LINKS_UPLOADED)
         row, blocks = {}, {}
         for n in sorted(PAPER_TABLE2_A100):
             ctx.dslash_prepare_multi(psi[:n].contiguous(), prec)
@@ -618,11 +643,13 @@ def section_paper_tables(stag, torch, timer, hbm):
             ms, _ = timer(lambda: ctx.dslash_repeat_multi(prec, recon, blocks[n], 1), reps=5, warm=2)
             row[n] = FLOP_PER_SITE * Vh * n / (ms * 1e-3) * 1e-12
         scan[label] = {"tflops_by_nmulti": row, "rhs_block": blocks, "best": max(row.values())}
+    ctx.set_operator_links(stag.LINKS_UPLOADED)
     res["nmulti_32x4"] = {"unit": "TFLOP/s (570 flop per site per vector)", "scan": scan,
                           "paper_a100_fp32_fp64": PAPER_TABLE2_A100,
-                          "note": "n vectors per launch, each link loaded once per rhs_block of them (autotuned: "
-                                  "larger register blocks spill); paper: 12-real links with temporal gauge (6 links "
-                                  "read per site); here 8 links per site, no gauge fixing"}
+                          "note": "n vectors per launch, each link loaded once per block of them (the autotuner's "
+                                  "choice of the link-tile split); the paper's Table 2 uses 12-real links in "
+                                  "temporal gauge (6 links read per site): the *_temporal_gauge row; the others "
+                                  "read 8 links per site"}
     ctx.close()
     dims = li.WORKLOADS[7]["dims"]
     Vh = li.volume(dims) // 2
@@ -775,17 +802,22 @@ def main():
                        "time_to_solution_ms": ms_df, "iters": st_df["iters"],
                        "true_rel_residual": st_df["true_rel_residual"], "speedup_vs_ieee_f64": ms_per_step / ms_df,
                        "rel_diff_to_ieee_solution": float(torch.linalg.norm(x - x_ieee) / torch.linalg.norm(x_ieee))}
-    ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, temporal_gauge=1)   # builds the transform once
-    ms_tg, st_tg = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, temporal_gauge=1), reps=3)
-    arms["cg_f64x_temporal_gauge"] = {
-        "arithmetic": "as cg_f64x, links gauge-transformed so that the time links are 1 off the last slice",
-        "time_to_solution_ms": ms_tg, "iters": st_tg["iters"], "true_rel_residual": st_tg["true_rel_residual"],
-        "speedup_vs_ieee_f64": ms_per_step / ms_tg}
-    for name, prec in (("mixed_f32_12", stag.F32), ("mixed_f16_12", stag.F16)):
+    tg_note = ("; links in temporal gauge (Sec. 4.3): U' = g U g^dagger with the time links 1 off the last "
+               "slice, 6 + 2/Lt link reads per site, solving M' x' = g b and returning g^dagger x'")
+    for name, a in (("cg_f64x_temporal_gauge", F64X), ("cg_f64_temporal_gauge", F64_IEEE)):
+        ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, f64_arith=a, temporal_gauge=1)   # builds the transform once
+        ms_tg, st_tg = timer(lambda: ctx.cg_solve(x, b, mass, tol=TOL, use_graph=ug, f64_arith=a,
+                                                  temporal_gauge=1), reps=3)
+        arms[name] = {
+            "arithmetic": ("as cg_f64x" if a == F64X else "IEEE double as the headline") + tg_note,
+            "time_to_solution_ms": ms_tg, "iters": st_tg["iters"], "true_rel_residual": st_tg["true_rel_residual"],
+            "speedup_vs_ieee_f64": ms_per_step / ms_tg}
+    for name, prec, tg in (("mixed_f32_12", stag.F32, 0), ("mixed_f16_12", stag.F16, 0),
+                           ("mixed_f32_12_temporal_gauge", stag.F32, 1), ("mixed_f16_12_temporal_gauge", stag.F16, 1)):
         m, sm = timer(lambda: ctx.cg_solve_mixed(x, b, mass, tol=TOL, inner_prec=prec, inner_recon=12,
-                                                 use_graph=ug), reps=3)
+                                                 use_graph=ug, temporal_gauge=tg), reps=3)
         arms[name] = {"arithmetic": f"{'float' if prec == stag.F32 else 'half + per-site norm'} 12-real inner "
-                                    "iteration, double-float reliable updates, double solution",
+                                    "iteration, double-float reliable updates, double solution" + (tg_note if tg else ""),
                       "time_to_solution_ms": m, "iters": sm["iters"], "reliable_updates": sm["reliable_updates"],
                       "true_rel_residual": sm["true_rel_residual"], "speedup_vs_ieee_f64": ms_per_step / m}
 
@@ -795,7 +827,11 @@ def main():
     kern = {"f64_18": dslash_kernel_entry(timer, ctx, psi, out, F64_IEEE, 18, Vh, hbm),
             "f64x_18": dslash_kernel_entry(timer, ctx, psi, out, F64X, 18, Vh, hbm),
             "f32_12": dslash_kernel_entry(timer, ctx, psi, out, stag.F32, 12, Vh, hbm),
-            "f16_12": dslash_kernel_entry(timer, ctx, psi, out, stag.F16, 12, Vh, hbm)}
+            "f16_12": dslash_kernel_entry(timer, ctx, psi, out, stag.F16, 12, Vh, hbm),
+            "f64_18_temporal_gauge": dslash_kernel_entry(timer, ctx, psi, out, F64_IEEE, 18, Vh, hbm, tg=True),
+            "f64x_18_temporal_gauge": dslash_kernel_entry(timer, ctx, psi, out, F64X, 18, Vh, hbm, tg=True),
+            "f32_12_temporal_gauge": dslash_kernel_entry(timer, ctx, psi, out, stag.F32, 12, Vh, hbm, tg=True),
+            "f16_12_temporal_gauge": dslash_kernel_entry(timer, ctx, psi, out, stag.F16, 12, Vh, hbm, tg=True)}
     traffic = load_traffic()
     fp64_probe = stag.fma_probe(stag.F64) * 1e3
     fp32_probe = stag.fma_probe(stag.F32) * 1e3

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define STAG_ABI_VERSION 2
+#define STAG_ABI_VERSION 3
 #define STAG_MAX_RHS 64   /* largest batch of right-hand sides or shifts */
 
 typedef struct stag_ctx_s *stag_ctx;
@@ -108,6 +108,24 @@ int stag_get_dims(stag_ctx ctx, int dims[4], long long *volume);
 int stag_upload_gauge(stag_ctx ctx, const double *U, int on_device);
 
 /* ------------------------------------------------------- operator (Eq. staggered) */
+
+/* Link field of the operator entry points (Sec. 4.3, temporal gauge).  The
+ * paper reads 6 links per site by fixing the temporal gauge: with the gauge
+ * matrices g(x, t = 0) = 1, g(x, t + 1) = g(x, t) U_t(x, t), the transformed
+ * links U' = g U g^dagger (U'_mu(x) = g(x) U_mu(x) g(x + mu)^dagger) have
+ * U'_t = 1 except on the last time slice.  The library computes g and U' in
+ * double from the uploaded field on first use (unitary links: SU(3) or U(3)).
+ *   STAG_LINKS_UPLOADED       (default) the operator entry points apply D[U];
+ *   STAG_LINKS_TEMPORAL       they apply D[U'] reading 6 links per site: a time
+ *                             hop off the last slice adds the neighbour spinor
+ *                             with no link load or product;
+ *   STAG_LINKS_TEMPORAL_FULL  they apply D[U'] reading all 8 links (the identity
+ *                             links as stored): the same values, for checks.
+ * Affects stag_dslash_eo/oe, stag_dslash_multi and stag_dslash_repeat(_multi);
+ * solvers, stag_apply_M and the force always act on D[U] (the solvers'
+ * temporal_gauge parameter uses U' internally).  Errors: STAG_EINVAL. */
+enum stag_links { STAG_LINKS_UPLOADED = 0, STAG_LINKS_TEMPORAL = 1, STAG_LINKS_TEMPORAL_FULL = 2 };
+int stag_set_operator_links(stag_ctx ctx, int links);
 
 /* out_even = D_eo in_odd: the operator restricted to even output sites acting
  * on a field living on odd sites (both canonical half fields, device).
@@ -230,14 +248,14 @@ typedef struct {
                               outside the double-float range, see STAG_F64X).  Every solver
                               solves for 2^-k b (largest component in [1, 2)) and returns
                               2^k x, exactly, so any double-range b is served alike */
-    int temporal_gauge;    /* double-precision CG with f64_arith = STAG_F64X: 1 solves in temporal
-                              gauge (Sec. 4.3: the links of the time direction fixed to 1 except
-                              on the last slice, 6 link reads per site instead of 8), M' x' = g b
-                              with the gauge matrices g computed from the uploaded field, and
-                              returns x = g^dagger x'; the same system, the same residual norm.
-                              Needs unitary links (SU(3) or U(3): g U g^dagger is a gauge
-                              transformation only then).  0 (default): the links as uploaded.
-                              STAG_EINVAL with STAG_F64. */
+    int temporal_gauge;    /* 1: solve in temporal gauge (Sec. 4.3, see stag_set_operator_links):
+                              M' x' = g b on the links U' = g U g^dagger, reading 6 links per
+                              site in every operator pass (inner iterations, reliable updates,
+                              multi-vector passes), and return x = g^dagger x'.  M' = g M
+                              g^dagger: the same spectrum and iteration; g is unitary, so the
+                              same residual norm.  Needs unitary links (SU(3) or U(3)).  All
+                              solvers: stag_cg_solve (either f64_arith), _mixed, _multi,
+                              _multishift, and the action.  0 (default): the links as uploaded. */
 } stag_solver_params;
 
 typedef struct {

@@ -22,13 +22,16 @@ import threading
 
 __all__ = [
     "F64", "F32", "F16", "F64X", "RECON_18", "RECON_12", "StagError", "NotConverged",
+    "LINKS_UPLOADED", "LINKS_TEMPORAL", "LINKS_TEMPORAL_FULL",
     "load", "build", "Context", "SolverParams", "SolverStats", "StaggeredAction", "fermion_force",
     "apply_M_noalloc", "NOALLOC_MAX_VH", "fma_probe", "tuner",
 ]
 
 F64, F32, F16, F64X = 0, 1, 2, 3
-ABI_VERSION = 2   # include/stag.h STAG_ABI_VERSION: the struct layouts below
+ABI_VERSION = 3   # include/stag.h STAG_ABI_VERSION: the struct layouts below
 RECON_18, RECON_12 = 18, 12
+# include/stag.h enum stag_links: the link field of the operator entry points
+LINKS_UPLOADED, LINKS_TEMPORAL, LINKS_TEMPORAL_FULL = 0, 1, 2
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 NOALLOC_MAX_VH = 1 << 17   # include/stag.h STAG_NOALLOC_MAX_VH
 
@@ -83,6 +86,7 @@ def _declare(lib):
         "stag_create": ([ctypes.POINTER(P), ctypes.POINTER(I), P], I),
         "stag_destroy": ([P], I),
         "stag_set_stream": ([P, P], I),
+        "stag_set_operator_links": ([P, I], I),
         "stag_get_dims": ([P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)], I),
         "stag_upload_gauge": ([P, P, I], I),
         "stag_dslash_eo": ([P, P, P, I, I], I),
@@ -224,6 +228,12 @@ class Context:
         else:
             _check(self._lib.stag_upload_gauge(self._h, ctypes.c_void_p(U.data_ptr()), 0))
         self._U_keepalive = U if U.is_cuda else None
+
+    def set_operator_links(self, links):
+        """stag_set_operator_links: the link field the operator entry points apply
+        (LINKS_UPLOADED, LINKS_TEMPORAL: the temporal-gauge transform read with 6
+        links per site, LINKS_TEMPORAL_FULL: the same field read in full)."""
+        _check(self._lib.stag_set_operator_links(self._h, int(links)))
 
     def dslash_eo(self, out, inp, prec=F64, recon=RECON_18):
         """stag_dslash_eo: out (even) = D_eo inp (odd)."""

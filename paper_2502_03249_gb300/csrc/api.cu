@@ -97,10 +97,11 @@ static int dslash_entry(stag_ctx ctx, double* out, const double* in, int prec, i
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
-    if (prec == STAG_F64 || prec == STAG_F64X) return launch_dslash(ctx, prec, recon, par_out, out, in, ctx->stream);
+    if (prec == STAG_F64 || prec == STAG_F64X)
+        return launch_dslash(ctx, prec, recon, par_out, out, in, ctx->stream, ctx->op_links);
     STAG_TRY(ensure_lo_tmp(ctx, lo_spinor_bytes(ctx->g, prec)));
     STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, 1, ctx->stream));
-    STAG_TRY(launch_dslash(ctx, prec, recon, par_out, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream));
+    STAG_TRY(launch_dslash(ctx, prec, recon, par_out, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream, ctx->op_links));
     return convert_lo_to_f64(ctx, prec, ctx->tmp_lo_out, (double2*)out, 1, ctx->stream);
 }
 
@@ -194,7 +195,8 @@ int stag_destroy(stag_ctx ctx)
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->tg_g) cudaFree(ctx->tg_g);
-    if (ctx->tg_links) cudaFree(ctx->tg_links);
+    for (int s = 0; s < 8; ++s)
+        if (ctx->tg_links[s]) cudaFree(ctx->tg_links[s]);
     if (ctx->tg_tmp) cudaFree(ctx->tg_tmp);
     if (ctx->tmp_odd) cudaFree(ctx->tmp_odd);
     if (ctx->tmp_lo_in) cudaFree(ctx->tmp_lo_in);
@@ -212,6 +214,17 @@ int stag_set_stream(stag_ctx ctx, void* stream)
 {
     STAG_TRY(check_ctx(ctx));
     ctx->stream = (cudaStream_t)stream;
+    return STAG_OK;
+}
+
+int stag_set_operator_links(stag_ctx ctx, int links)
+{
+    STAG_TRY(check_ctx(ctx));
+    if (links != STAG_LINKS_UPLOADED && links != STAG_LINKS_TEMPORAL && links != STAG_LINKS_TEMPORAL_FULL) {
+        set_error("links must be STAG_LINKS_UPLOADED, STAG_LINKS_TEMPORAL or STAG_LINKS_TEMPORAL_FULL");
+        return STAG_EINVAL;
+    }
+    ctx->op_links = links;
     return STAG_OK;
 }
 
@@ -300,7 +313,7 @@ int stag_dslash_repeat_multi(stag_ctx ctx, int prec, int recon, int rhs_block, i
     int nb = rhs_block;
     for (int k = 0; k < nrep; ++k)
         STAG_TRY(multi_dslash_internal(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->prepared_nrhs,
-                                       rhs_block, &nb));
+                                       rhs_block, &nb, ctx->op_links));
     ctx->last_rhs_block = nb;
     ctx->repeat_done = 1;
     return STAG_OK;
@@ -339,7 +352,8 @@ int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep)
         return STAG_ENOGAUGE;
     }
     for (int k = 0; k < nrep; ++k)
-        STAG_TRY(launch_dslash_internal(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream));
+        STAG_TRY(launch_dslash_internal(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream,
+                                        ctx->op_links));
     ctx->repeat_done = 1;
     return STAG_OK;
 }

@@ -54,8 +54,10 @@ static int ensure_batch(stag_ctx ctx, int prec, int recon, int nrhs, BatchSlot**
 
 // X (device, [nrhs][Vh][3] complex128) = solutions of (M + shifts_k) X_k = B_k.
 // shifts_host: NULL (all zero) or nrhs host values; X0: NULL or initial guesses.
+// tg = 1: every operator pass on the temporal-gauge links U' (M' = g M g^dagger);
+// B, X0 and X are then the transformed fields (the caller applies g and g^dagger).
 int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double mass, const double* shifts_host,
-                  const double2* X0, const stag_solver_params& prm, stag_solver_stats* stats)
+                  const double2* X0, const stag_solver_params& prm, stag_solver_stats* stats, int tg)
 {
     const auto t0 = std::chrono::steady_clock::now();
     const int prec = prm.inner_prec, recon = prm.inner_recon;
@@ -68,7 +70,8 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
     STAG_TRY(ensure_batch(ctx, prec, recon, nrhs, &mp));
     BatchSlot& m = *mp;
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    STAG_TRY(tg ? ensure_links_tg(ctx, prec, recon, &lk) : ensure_links(ctx, prec, recon, &lk));
+    m.tg = tg;
     const double delta = prec == STAG_F64 ? 0.0 : (prm.delta > 0 ? prm.delta : 0.1);
     const size_t vbytes = (size_t)nrhs * m.f64_stride;
     stag_solver_params prm2 = prm;
@@ -90,7 +93,7 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
     // the configuration (multi_tile.cuh) of a given block, or the autotuner's
     // choice for the inner operator on these buffers
     int cfg = multi_cfg_for(prec, nb);
-    if (nb == 0) STAG_TRY(multi_dslash(ctx, prec, recon, 1, m.t, m.p, nrhs, 0, &nb, &cfg));
+    if (nb == 0) STAG_TRY(multi_dslash(ctx, prec, recon, 1, m.t, m.p, nrhs, 0, &nb, &cfg, tg));
     int rc;
     if (prec == STAG_F64) rc = batched_run_f64(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, cfg);
     else if (prec == STAG_F32) rc = batched_run_f32(ctx, m, recon, lk, X0, mass, shifts_dev, prm2, delta, cfg);
@@ -174,7 +177,19 @@ int stag_cg_solve_multi(stag_ctx ctx, double* X, const double* B, int nrhs, doub
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
-    return batched_solve(ctx, (double2*)X, (const double2*)B, nrhs, mass, nullptr, nullptr, prm, stats);
+    if (!prm.temporal_gauge)
+        return batched_solve(ctx, (double2*)X, (const double2*)B, nrhs, mass, nullptr, nullptr, prm, stats, 0);
+    // temporal gauge: M' X' = g B on U', X = g^dagger X'
+    const double2* G = nullptr;
+    double2* gb = nullptr;
+    STAG_TRY(ensure_tg_gauge(ctx, &G));
+    STAG_TRY(ensure_tg_tmp(ctx, nrhs, &gb));
+    STAG_TRY(tg_apply(ctx, G, (const double2*)B, gb, nrhs, 0));
+    const int rc = batched_solve(ctx, (double2*)X, gb, nrhs, mass, nullptr, nullptr, prm, stats, 1);
+    if (rc < 0) return rc;
+    STAG_TRY(tg_apply(ctx, G, (const double2*)X, (double2*)X, nrhs, 1));
+    STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return rc;
 }
 
 int stag_last_rhs_block(stag_ctx ctx)

@@ -37,14 +37,27 @@ __device__ __forceinline__ void dslash_site_multi(const Geom& g, int p, int h, c
         for (int a = 0; a < 3; ++a) acc[k].c[a].re = acc[k].c[a].im = real(0);
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-        const Mat3<real> Uf = U.load(p, mu, h);
+        // identity time links of temporal-gauge fields (U.tg): plain sums
+        if (mu == 3 && unit_fwd_time(U, s)) {
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-            if (mask & (1u << k)) mv_acc(acc[k], Uf, load_flipped(in.at(k0 + k, stride), s.fwd[mu], s.sf[mu]));
-        const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
+            for (int k = 0; k < NB; ++k)
+                if (mask & (1u << k)) hop_add(acc[k], load_flipped(in.at(k0 + k, stride), s.fwd[mu], s.sf[mu]));
+        } else {
+            const Mat3<real> Uf = U.load(p, mu, h);
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-            if (mask & (1u << k)) mdv_acc(acc[k], Ub, load_flipped(in.at(k0 + k, stride), s.bwd[mu], s.sb[mu]));
+            for (int k = 0; k < NB; ++k)
+                if (mask & (1u << k)) mv_acc(acc[k], Uf, load_flipped(in.at(k0 + k, stride), s.fwd[mu], s.sf[mu]));
+        }
+        if (mu == 3 && unit_bwd_time(U, s)) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (mask & (1u << k)) hop_add(acc[k], load_flipped(in.at(k0 + k, stride), s.bwd[mu], s.sb[mu]));
+        } else {
+            const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (mask & (1u << k)) mdv_acc(acc[k], Ub, load_flipped(in.at(k0 + k, stride), s.bwd[mu], s.sb[mu]));
+        }
     }
 }
 

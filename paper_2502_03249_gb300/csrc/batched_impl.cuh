@@ -703,13 +703,13 @@ struct BatchPlan {
                    const double* shifts_dev, const stag_solver_params& prm, double delta, int arith)
     {
         const void* lk64 = nullptr;
-        STAG_TRY(ensure_links(ctx, arith, 18, &lk64));
-        const LF U{(const typename LF::store*)lk, ctx->g.Vh};
-        const LF64 U64{(const typename LF64::store*)lk64, ctx->g.Vh};
+        STAG_TRY(m.tg ? ensure_links_tg(ctx, arith, 18, &lk64) : ensure_links(ctx, arith, 18, &lk64));
+        const LF U{(const typename LF::store*)lk, ctx->g.Vh, m.tg};
+        const LF64 U64{(const typename LF64::store*)lk64, ctx->g.Vh, m.tg};
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
         STAG_TRY(enqueue_start(ctx, m, U64, ctx->stream, x0, prm.tol, maxiter, mass, shifts_dev, delta));
         if (prm.use_graph) {
-            if (!m.lg.exec || m.graph_nb != CFG || m.graph_arith != arith) {
+            if (!m.lg.exec || m.graph_nb != CFG || m.graph_arith != arith || m.graph_tg != m.tg) {
                 LoopGraph& lg = m.lg;
                 STAG_TRY(build_loop_graph(
                     ctx->cap_stream, lg, true, [&](cudaStream_t s) { return enqueue_main(ctx, m, U, s, &lg, 1); },
@@ -717,6 +717,7 @@ struct BatchPlan {
                     [&](cudaStream_t s) { return enqueue_p(ctx, m, s); }));
                 m.graph_nb = CFG;
                 m.graph_arith = arith;
+                m.graph_tg = m.tg;
             }
             STAG_CUDA_TRY(cudaGraphLaunch(m.lg.exec, ctx->stream));
         } else {

@@ -7,7 +7,6 @@
 #include <new>
 
 #include "cg_df.cuh"
-#include "tgauge.cuh"
 #include "tune.h"
 #include "workspace.h"
 
@@ -150,9 +149,11 @@ int ensure_cg_f64(stag_ctx ctx)
 //             (SpinorDF over the same buffers), double-float links, every
 //             per-site operation on the FP32 pipe (cg_df.cuh).
 // Each provides start / enqueue_iter / true_residual / restart / finish.
-struct F64Plan {
+template <int SLOT>
+struct F64PlanT {
     typedef LF64 LF;
-    static constexpr int slot = 0;
+    static constexpr int slot = SLOT;
+    static constexpr int prec = STAG_F64;
     static int prepare(stag_ctx) { return STAG_OK; }
     static int start(stag_ctx ctx, const double2* b_in, double mass, double sigma, double tol, int maxiter)
     {
@@ -165,7 +166,7 @@ struct F64Plan {
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
-    static constexpr const char* name = "cg_f64";
+    static constexpr const char* name = SLOT == 0 ? "cg_f64" : "cg_f64_tg";
     static int launch_hop(stag_ctx ctx, const LF& U, int bs, cudaStream_t s, const CgScalars* sc)
     {
         Workspace* ws = ctx->ws;
@@ -248,6 +249,7 @@ template <class LFT, int SLOT>
 struct DFPlanT {
     typedef LFT LF;
     static constexpr int slot = SLOT;
+    static constexpr int prec = STAG_F64X;
     static SpinorDF v(double2* p) { return SpinorDF{reinterpret_cast<float4*>(p)}; }
     static int prepare(stag_ctx ctx) { return decide_df_dir(ctx); }
     static int start(stag_ctx ctx, const double2* b_in, double mass, double sigma, double tol, int maxiter)
@@ -332,9 +334,13 @@ struct DFPlanT {
     }
 };
 
+// The plans by slot: IEEE double 0, double-float 1, and the same on
+// temporal-gauge links (U.tg = 1, M' = g M g^dagger: tgauge.cu) 3 and 2.  A
+// slot owns its graph, which holds the link field it was captured with.
+typedef F64PlanT<0> F64Plan;
+typedef F64PlanT<3> F64PlanTG;
 typedef DFPlanT<LinkFieldDF<18>, 1> DFPlan;
-// the same on temporal-gauge links (M' = g M g^dagger, see tgauge.cuh)
-typedef DFPlanT<LinkFieldTG, 2> DFPlanTG;
+typedef DFPlanT<LinkFieldDF<18>, 2> DFPlanTG;
 
 // the graph  while (cond) { GRAPH_UNROLL CG iterations }, built once per context and plan
 template <class Plan>
@@ -432,9 +438,10 @@ static int tune_cg_plan(stag_ctx ctx, const typename Plan::LF& U)
     k_update_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
     STAG_CUDA_TRY(cudaGetLastError());
     CgShape sh;
-    const int prec = Plan::slot == 0 ? STAG_F64 : STAG_F64X;
+    const int prec = Plan::prec;
     char kname[64];
-    snprintf(kname, sizeof(kname), "%s_hop%s", Plan::name, ws->df_dir == 1 && Plan::slot ? "_dir" : "");
+    snprintf(kname, sizeof(kname), "%s_hop%s", Plan::name,
+             ws->df_dir == 1 && Plan::prec == STAG_F64X ? "_dir" : "");
     STAG_TRY(tune_choice(ctx, tune_key(ctx, kname, prec, 18, 1), HOP_CANDS, &sh.hop,
                          [&](int c) { return Plan::launch_hop(ctx, U, c, ctx->stream, tsc); }));
     snprintf(kname, sizeof(kname), "%s_update", Plan::name);
@@ -501,23 +508,27 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
 {
     const auto t0 = std::chrono::steady_clock::now();
     STAG_TRY(ensure_cg_f64(ctx));
-    if (prm.temporal_gauge && prm.f64_arith != STAG_F64X) {
-        set_error("temporal_gauge needs f64_arith = STAG_F64X");
-        return STAG_EINVAL;
-    }
     int arith = STAG_F64;
     STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &arith));
-    if (arith == STAG_F64X && prm.temporal_gauge) {
+    if (prm.temporal_gauge) {
         // M x = b as M' x' = g b, x = g^dagger x' (same residual norm: g is unitary)
         const double2* G = nullptr;
-        const float4* lk = nullptr;
-        STAG_TRY(ensure_tg(ctx, &G, &lk));
-        if (!ctx->tg_tmp) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_tmp, (size_t)3 * ctx->g.Vh * sizeof(double2)));
-        STAG_TRY(tg_apply(ctx, G, b_in, ctx->tg_tmp, 0));
-        const LinkFieldTG U{lk, ctx->g.Vh, ctx->g.Vh / ctx->g.L[3], ctx->g.L[3]};
-        const int rc = cg_solve_plan<DFPlanTG>(ctx, U, x_out, ctx->tg_tmp, mass, sigma, prm, st, t0);
+        const void* lk = nullptr;
+        double2* gb = nullptr;
+        STAG_TRY(ensure_links_tg(ctx, arith, 18, &lk));
+        STAG_TRY(ensure_tg_gauge(ctx, &G));
+        STAG_TRY(ensure_tg_tmp(ctx, 1, &gb));
+        STAG_TRY(tg_apply(ctx, G, b_in, gb, 1, 0));
+        int rc;
+        if (arith == STAG_F64X) {
+            const LinkFieldDF<18> U{(const float4*)lk, ctx->g.Vh, 1};
+            rc = cg_solve_plan<DFPlanTG>(ctx, U, x_out, gb, mass, sigma, prm, st, t0);
+        } else {
+            const LF64 U{(const double2*)lk, ctx->g.Vh, 1};
+            rc = cg_solve_plan<F64PlanTG>(ctx, U, x_out, gb, mass, sigma, prm, st, t0);
+        }
         if (rc < 0) return rc;
-        STAG_TRY(tg_apply(ctx, G, x_out, x_out, 1));
+        STAG_TRY(tg_apply(ctx, G, x_out, x_out, 1, 1));
         STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         return rc;
     }
@@ -527,8 +538,7 @@ int cg_solve_f64(stag_ctx ctx, double2* x_out, const double2* b_in, double mass,
         const LinkFieldDF<18> U{(const float4*)lk, ctx->g.Vh};
         return cg_solve_plan<DFPlan>(ctx, U, x_out, b_in, mass, sigma, prm, st, t0);
     }
-    // IEEE double: requested, or links outside the double-float range (the
-    // temporal-gauge path needs unitary links, which never are)
+    // IEEE double: requested, or links outside the double-float range
     const void* lk = nullptr;
     STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
     const LF64 U{(const double2*)lk, ctx->g.Vh};
@@ -539,7 +549,7 @@ void free_workspace(stag_ctx ctx)
 {
     Workspace* ws = ctx->ws;
     if (!ws) return;
-    for (int i = 0; i < 3; ++i) free_graph_pair(ws->f64_graph[i], ws->f64_exec[i]);
+    for (int i = 0; i < 4; ++i) free_graph_pair(ws->f64_graph[i], ws->f64_exec[i]);
     free_mixed(ws);
     free_batches(ws);
     for (auto& m : ws->ms) m.release();

@@ -3,6 +3,9 @@
 // internal storage layouts of links and spinors, and block reductions.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -326,6 +329,7 @@ struct LinkField {
     static constexpr int NE = (RECON == 12) ? 6 : 9;
     const S* base;
     int Vh;
+    int tg = 0;   // 1: temporal-gauge links, identity time links skipped (see below)
     __device__ __forceinline__ Mat3<real> load(int par, int mu, int h) const
     {
         Mat3<real> U;
@@ -391,6 +395,7 @@ struct LinkField<float2, RECON> {
     typedef LinkChunks<8, NE> C;
     const float2* base;
     int Vh;
+    int tg = 0;
     __device__ __forceinline__ Mat3<float> load(int par, int mu, int h) const
     {
         uint32_t w[C::WORDS];
@@ -411,6 +416,7 @@ struct LinkField<__half2, RECON> {
     typedef LinkChunks<4, NE> C;
     const __half2* base;
     int Vh;
+    int tg = 0;
     __device__ __forceinline__ Mat3<float> load(int par, int mu, int h) const
     {
         uint32_t w[C::WORDS];
@@ -563,6 +569,64 @@ __device__ __forceinline__ Vec3<typename S::real> load_flipped(const S& in, int 
 __device__ __forceinline__ Vec3<float> load_flipped(const SpinorF16& in, int h, uint32_t sbit)
 {
     return in.load_signed(h, sbit);
+}
+
+// ------------------------------------------------------ temporal gauge
+//
+// The paper reads 6 links per site by fixing the temporal gauge (Sec. 4.3):
+// with g(x, t = 0) = 1 and g(x, t + 1) = g(x, t) U_t(x, t), the links
+// U'_mu(x) = g(x) U_mu(x) g(x + mu)^dagger have U'_t = 1 except on the last
+// time slice, where U'_t(x, Lt - 1) = g(x, Lt - 1) U_t(x, Lt - 1).  Gauge
+// covariance gives D[U'] = g D[U] g^dagger, so M x = b is solved as
+// M' x' = g b, x = g^dagger x' (tgauge.cu builds g and U').
+//
+// U' is stored in the usual layout of its storage, the time planes holding
+// U'_t exactly (the identity off the last slice), so every kernel computes
+// D[U'] correctly from it.  A link field with tg = 1 tells the operator
+// kernels to skip the identity time links: a time hop off the last slice
+// adds the neighbour's spinor with no link load and no product.  The flag is
+// a kernel argument, not a template parameter, so every kernel serves both.
+
+// Link fields without the flag (used by code paths that never see
+// temporal-gauge links) are always read in full.
+template <class LF, class = void> struct HasTG : std::false_type {};
+template <class LF> struct HasTG<LF, std::void_t<decltype(std::declval<LF>().tg)>> : std::true_type {};
+
+// The time hops of output site s.h through identity links (tg = 1 only):
+// forward unless the site is on the last slice (x + t wraps: s.fwd[3] < h),
+// backward unless it is on slice 0 (x - t wraps: s.bwd[3] > h).
+template <class LF>
+__device__ __forceinline__ bool unit_fwd_time(const LF& U, const SiteNbrs& s)
+{
+    if constexpr (HasTG<LF>::value) return U.tg && s.fwd[3] > s.h;
+    else return false;
+}
+template <class LF>
+__device__ __forceinline__ bool unit_bwd_time(const LF& U, const SiteNbrs& s)
+{
+    if constexpr (HasTG<LF>::value) return U.tg && s.bwd[3] < s.h;
+    else return false;
+}
+// hop number 2 mu + back (0..7) through an identity link
+template <class LF>
+__device__ __forceinline__ bool unit_hop(const LF& U, const SiteNbrs& s, int hop)
+{
+    return hop == 6 ? unit_fwd_time(U, s) : (hop == 7 ? unit_bwd_time(U, s) : false);
+}
+
+// acc += v (a hop through an identity link), one rounding per component:
+// the sum the product with the identity matrix forms (mv_acc), and never
+// contracted with a multiplication inside v's load (the half spinors' norm)
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+template <typename T>
+__device__ __forceinline__ void hop_add(Vec3<T>& acc, const Vec3<T>& v)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc.c[a].re = add_rn(acc.c[a].re, v.c[a].re);
+        acc.c[a].im = add_rn(acc.c[a].im, v.c[a].im);
+    }
 }
 
 // ------------------------------------------------------------ reductions

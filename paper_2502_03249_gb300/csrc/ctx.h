@@ -81,9 +81,13 @@ struct stag_ctx_s {
     size_t link_bytes[8];
     bool link_stale[8];        // derived copy older than the last upload (re-derived in place)
     double2* tg_g;             // temporal gauge: g per site [par][V/2][9] (tgauge.cu)
-    float4* tg_links;          // temporal gauge: transformed double-float links
-    double2* tg_tmp;           // temporal gauge: g b for a solve
-    bool tg_stale;             // tg_g / tg_links older than the last upload
+    void* tg_links[8];         // temporal gauge: the transformed links U' in every storage,
+                               // index link_slot(prec, recon); slot 0 (F64/18) is the source
+    size_t tg_link_bytes[8];
+    bool tg_link_stale[8];
+    double2* tg_tmp;           // temporal gauge: g b for a solve (nrhs_cap fields)
+    int tg_tmp_fields;
+    bool tg_stale;             // tg_g older than the last upload
     // reduction scratch: partial sums (one double per block) and arrival counters
     double* partials;
     unsigned int* counters;    // 64 counters, each used by one reduction site
@@ -113,6 +117,7 @@ struct stag_ctx_s {
     bool link_exp_known;       // cleared by every upload
     void* dfx_tmp;             // double-float operator on canonical fields: input and output storage
     size_t dfx_tmp_bytes;
+    int op_links;              // link field of the operator entry points (stag_set_operator_links)
 };
 
 namespace stag {
@@ -125,22 +130,34 @@ int convert_lo_to_f64(stag_ctx ctx, int prec, const void* in, double2* out, int 
 size_t lo_spinor_bytes(const Geom& g, int prec);
 
 int ensure_lo_tmp_public(stag_ctx ctx, size_t bytes);
+// links: which link field the operator applies (op_links_for below).
 int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs, int nb,
-                 int* nb_used, int* cfg_used = nullptr);
+                 int* nb_used, int* cfg_used = nullptr, int links = 0);
 // multi-vector configuration (multi_tile.cuh) used for an explicit rhs block
 int multi_cfg_for(int prec, int block);
 
 // dslash.cu: out = D_{par_out, 1-par_out} in, storage chosen by prec/recon.
 // in/out are in the internal storage of prec (F64: canonical AoS).
+// links: the link field applied (STAG_LINKS_*, op_links_for below); the
+// operator entry points pass ctx->op_links, internal callers the uploaded field.
 int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
-                  cudaStream_t s);
+                  cudaStream_t s, int links = STAG_LINKS_UPLOADED);
 int launch_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
-                           cudaStream_t s);
+                           cudaStream_t s, int links = STAG_LINKS_UPLOADED);
 int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs,
-                          int nb, int* nb_used);
-int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int nb,
-                          int* nb_used, cudaStream_t s);
-int ensure_tg(stag_ctx ctx, const double2** G, const float4** links);
+                          int nb, int* nb_used, int links = STAG_LINKS_UPLOADED);
+int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int links,
+                          int nb, int* nb_used, cudaStream_t s);
+// tgauge.cu: the temporal-gauge matrices g and the links U' = g U g^dagger
+// (dslash.cuh, TGLinks) in the storage of (prec, recon), built on first use
+// after an upload; g b and g^dagger x for nfield even-site fields.
+int ensure_tg_gauge(stag_ctx ctx, const double2** G);
+int ensure_links_tg(stag_ctx ctx, int prec, int recon, const void** out);
+int ensure_tg_tmp(stag_ctx ctx, int nfield, double2** out);
+// pack.cu: (re)derive the copy (prec, recon) of the internal F64/18 field src
+// into *dst (allocated on first use, then kept at its address).  e: exponent
+// the double-float copy is scaled by (2^-e U).
+int derive_link_copy(stag_ctx ctx, const double2* src, int prec, int recon, int e, void** dst, size_t* bytes);
 
 // scale.cu
 int ensure_scale_scratch(stag_ctx ctx);
@@ -160,6 +177,15 @@ int check_float_inner_links(stag_ctx ctx);
 // The arithmetic a double-precision pass really uses: STAG_F64X unless the
 // double-float links are scaled (links outside the double-float range).
 int resolve_f64_arith(stag_ctx ctx, int requested, int* out);
-int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int dagger);
+int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int nfield, int dagger);
+// The link copy (prec, recon) of a link-field choice: STAG_LINKS_UPLOADED the
+// uploaded field, STAG_LINKS_TEMPORAL(_FULL) its temporal-gauge transform;
+// *tg = 1 where the identity time links are to be skipped.
+inline int op_links_for(stag_ctx ctx, int links, int prec, int recon, const void** out, int* tg)
+{
+    *tg = links == STAG_LINKS_TEMPORAL ? 1 : 0;
+    if (links == STAG_LINKS_UPLOADED) return ensure_links(ctx, prec, recon, out);
+    return ensure_links_tg(ctx, prec, recon, out);
+}
 
 }  // namespace stag

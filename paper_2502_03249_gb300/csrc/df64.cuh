@@ -295,6 +295,7 @@ struct LinkFieldDF {
     static_assert(RECON == 18, "double-float links are stored with 18 reals");
     const float4* base;
     int Vh;
+    int tg = 0;   // temporal-gauge links (common.cuh)
     __device__ __forceinline__ Mat3<DF> load(int par, int mu, int h) const
     {
         Mat3<DF> U;
@@ -389,6 +390,25 @@ __device__ __forceinline__ void chunk_partials(const float* v, double* part, int
         if (ch < nchunks) part[ch] = x;
     }
     __syncthreads();
+}
+
+// acc += v, exactly summed into the accumulator (the identity hops of
+// temporal-gauge links: the sum df_mac forms for the product 1 * v)
+__device__ __forceinline__ void df_acc(DF& acc, const DF& v)
+{
+    float s, e;
+    two_sum(acc.hi, v.hi, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, v.lo));
+}
+template <>
+__device__ __forceinline__ void hop_add<DF>(Vec3<DF>& acc, const Vec3<DF>& v)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        df_acc(acc.c[a].re, v.c[a].re);
+        df_acc(acc.c[a].im, v.c[a].im);
+    }
 }
 
 template <int R> struct OpMinBlocks<LinkFieldDF<R>> { static constexpr int value = 5; };

@@ -26,26 +26,28 @@ static int run_dslash(stag_ctx ctx, const LF& U, const SIn& in, const SOut& out,
 }
 
 int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
-                  cudaStream_t s)
+                  cudaStream_t s, int links)
 {
+    if (prec == STAG_F64X)
+        return dslash_f64x_canonical(ctx, par_out, (double2*)out, (const double2*)in, 1, links, 1, nullptr, s);
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    int tg = 0;
+    STAG_TRY(op_links_for(ctx, links, prec, recon, &lk, &tg));
     const int Vh = ctx->g.Vh;
     if (prec == STAG_F64) {
         SpinorF64 si{(double2*)in}, so{(double2*)out};
-        if (recon == 18) return run_dslash(ctx, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, par_out, s);
-        return run_dslash(ctx, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, par_out, s);
+        if (recon == 18) return run_dslash(ctx, LinkField<double2, 18>{(const double2*)lk, Vh, tg}, si, so, par_out, s);
+        return run_dslash(ctx, LinkField<double2, 12>{(const double2*)lk, Vh, tg}, si, so, par_out, s);
     }
-    if (prec == STAG_F64X) return dslash_f64x_canonical(ctx, par_out, (double2*)out, (const double2*)in, 1, 1, nullptr, s);
     if (prec == STAG_F32) {
         SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
-        if (recon == 18) return run_dslash(ctx, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, par_out, s);
-        return run_dslash(ctx, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, par_out, s);
+        if (recon == 18) return run_dslash(ctx, LinkField<float2, 18>{(const float2*)lk, Vh, tg}, si, so, par_out, s);
+        return run_dslash(ctx, LinkField<float2, 12>{(const float2*)lk, Vh, tg}, si, so, par_out, s);
     }
     if (prec == STAG_F16) {
         SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
-        if (recon == 18) return run_dslash(ctx, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, par_out, s);
-        return run_dslash(ctx, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, par_out, s);
+        if (recon == 18) return run_dslash(ctx, LinkField<__half2, 18>{(const __half2*)lk, Vh, tg}, si, so, par_out, s);
+        return run_dslash(ctx, LinkField<__half2, 12>{(const __half2*)lk, Vh, tg}, si, so, par_out, s);
     }
     set_error("unsupported precision %d", prec);
     return STAG_EUNSUPPORTED;
@@ -78,21 +80,23 @@ static int ensure_dfx_tmp(stag_ctx ctx, int nfield, float4** in, float4** out)
 // float range (outputs stay below 2^61 * 48 * 2^41 < 2^127), so that
 // components down to 2^-134 of it keep their full 48 bits as well.
 constexpr int DFX_TOP = 60;
-int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int nb,
-                          int* nb_used, cudaStream_t s)
+int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int links,
+                          int nb, int* nb_used, cudaStream_t s)
 {
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lk));
+    int tg = 0;
+    STAG_TRY(op_links_for(ctx, links, STAG_F64X, 18, &lk, &tg));
     float4 *ti = nullptr, *to = nullptr;
     STAG_TRY(ensure_dfx_tmp(ctx, nfield, &ti, &to));
     const size_t elems = (size_t)3 * ctx->g.Vh;
     STAG_TRY(field_exponents(ctx, in, nfield, elems, SLOT_OPER, s));
     STAG_TRY(split_fields_scaled(ctx, in, ti, nfield, elems, SLOT_OPER, -DFX_TOP, s));
     if (nfield == 1) {
-        STAG_TRY(run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh}, SpinorDF{ti}, SpinorDF{to}, par_out, s));
+        STAG_TRY(run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh, tg}, SpinorDF{ti}, SpinorDF{to},
+                            par_out, s));
         if (nb_used) *nb_used = 1;
     } else {
-        STAG_TRY(multi_dslash_internal(ctx, STAG_F64X, 18, par_out, to, ti, nfield, nb, nb_used));
+        STAG_TRY(multi_dslash_internal(ctx, STAG_F64X, 18, par_out, to, ti, nfield, nb, nb_used, links));
     }
     return join_fields_scaled(ctx, to, out, nfield, elems, SLOT_OPER, 1, ctx->df_link_exp - DFX_TOP, s);
 }
@@ -101,12 +105,13 @@ int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2
 // that STAG_F64X reads and writes double-float vectors (the storage of the
 // double-float solver) instead of converting canonical doubles on the fly.
 int launch_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in,
-                           cudaStream_t s)
+                           cudaStream_t s, int links)
 {
-    if (prec != STAG_F64X) return launch_dslash(ctx, prec, recon, par_out, out, in, s);
+    if (prec != STAG_F64X) return launch_dslash(ctx, prec, recon, par_out, out, in, s, links);
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
-    return run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh}, SpinorDF{(float4*)in},
+    int tg = 0;
+    STAG_TRY(op_links_for(ctx, links, prec, recon, &lk, &tg));
+    return run_dslash(ctx, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh, tg}, SpinorDF{(float4*)in},
                       SpinorDF{(float4*)out}, par_out, s);
 }
 

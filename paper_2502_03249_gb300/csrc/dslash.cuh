@@ -22,12 +22,23 @@ __device__ __forceinline__ Vec3<typename LF::real> dslash_site(const Geom& g, in
     for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = real(0);
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-        const Mat3<real> Uf = U.load(p, mu, h);
-        const Vec3<real> vf = load_flipped(in, s.fwd[mu], s.sf[mu]);
-        mv_acc(acc, Uf, vf);
-        const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
-        const Vec3<real> vb = load_flipped(in, s.bwd[mu], s.sb[mu]);
-        mdv_acc(acc, Ub, vb);
+        // temporal-gauge links (U.tg): the time hops through identity links
+        // are plain sums (warp-uniform wherever Vs/2 is a multiple of 32: a
+        // warp's sites then share one time slice)
+        if (mu == 3 && unit_fwd_time(U, s)) {
+            hop_add(acc, load_flipped(in, s.fwd[mu], s.sf[mu]));
+        } else {
+            const Mat3<real> Uf = U.load(p, mu, h);
+            const Vec3<real> vf = load_flipped(in, s.fwd[mu], s.sf[mu]);
+            mv_acc(acc, Uf, vf);
+        }
+        if (mu == 3 && unit_bwd_time(U, s)) {
+            hop_add(acc, load_flipped(in, s.bwd[mu], s.sb[mu]));
+        } else {
+            const Mat3<real> Ub = U.load(1 - p, mu, s.bwd[mu]);
+            const Vec3<real> vb = load_flipped(in, s.bwd[mu], s.sb[mu]);
+            mdv_acc(acc, Ub, vb);
+        }
     }
     return acc;
 }

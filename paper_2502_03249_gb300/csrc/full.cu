@@ -107,13 +107,13 @@ static int axpby(stag_ctx ctx, const double2* x, const double2* y, double2* out,
 // goes to the output buffer first, then the axpby.
 static int schur_pre_df(stag_ctx ctx, double2* const* B, double mass)
 {
-    STAG_TRY(dslash_f64x_canonical(ctx, 0, B[2], B[1], 1, 1, nullptr, ctx->stream));   // D_eo b_o
+    STAG_TRY(dslash_f64x_canonical(ctx, 0, B[2], B[1], 1, STAG_LINKS_UPLOADED, 1, nullptr, ctx->stream));   // D_eo b_o
     return axpby(ctx, B[0], B[2], B[2], mass, -1.0);                                   // m b_e - D_eo b_o
 }
 
 static int schur_post_df(stag_ctx ctx, double2* const* B, double2* psi_o, double mass)
 {
-    STAG_TRY(dslash_f64x_canonical(ctx, 1, psi_o, B[3], 1, 1, nullptr, ctx->stream));   // D_oe psi_e
+    STAG_TRY(dslash_f64x_canonical(ctx, 1, psi_o, B[3], 1, STAG_LINKS_UPLOADED, 1, nullptr, ctx->stream));   // D_oe psi_e
     return axpby(ctx, B[1], psi_o, psi_o, 1.0 / mass, -1.0 / mass);                      // (b_o - D_oe psi_e)/m
 }
 

@@ -268,30 +268,33 @@ struct MixedPlan {
     // slot's vectors with a scalar record that never converges)
     static int tune(stag_ctx ctx, MixedSlot& m, const LF& U, int prec, int recon)
     {
-        if (m.tuned) return STAG_OK;
+        const int tg = U.tg;
+        if (m.tuned[tg]) return STAG_OK;
         CgScalars* tsc = ctx->ws->sc + 62;
         k_mixed_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
         STAG_CUDA_TRY(cudaGetLastError());
         CgShape sh;
-        STAG_TRY(tune_choice(ctx, tune_key(ctx, "mixed_hop", prec, recon, 1), {128, 64, 256}, &sh.hop,
+        STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "mixed_hop_tg" : "mixed_hop", prec, recon, 1), {128, 64, 256},
+                             &sh.hop,
                              [&](int c) { return launch_hop(ctx, m, U, c, ctx->stream, tsc); }));
         const std::vector<int> vc = {vcfg(256, 1), vcfg(128, 1), vcfg(256, 2), vcfg(128, 2)};
         STAG_TRY(tune_choice(ctx, tune_key(ctx, "mixed_update", prec, recon, 1), vc, &sh.upd,
                              [&](int c) { return launch_update(ctx, m, c, ctx->stream, tsc, nullptr, 0); }));
         STAG_TRY(tune_choice(ctx, tune_key(ctx, "mixed_p", prec, recon, 1), vc, &sh.pk,
                              [&](int c) { return launch_p(ctx, m, c, ctx->stream, tsc); }));
-        m.shape = sh;
-        m.tuned = true;
+        m.shape[tg] = sh;
+        m.tuned[tg] = true;
         return STAG_OK;
     }
     static int enqueue_main(stag_ctx ctx, MixedSlot& m, const LF& U, cudaStream_t s, LoopGraph* lg, int use_cond)
     {
         const Geom g = ctx->g;
         S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap);
-        STAG_TRY(launch_hop(ctx, m, U, m.shape.hop, s, m.sc));
+        const CgShape& sh = m.shape[U.tg];
+        STAG_TRY(launch_hop(ctx, m, U, sh.hop, s, m.sc));
         k_Mp_dot<LF, S, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, m.sc, ctx->partials,
                                                                            ctx->counters);
-        STAG_TRY(launch_update(ctx, m, m.shape.upd, s, m.sc, lg, use_cond));
+        STAG_TRY(launch_update(ctx, m, sh.upd, s, m.sc, lg, use_cond));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
@@ -317,24 +320,26 @@ struct MixedPlan {
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
-    static int enqueue_p(stag_ctx ctx, MixedSlot& m, cudaStream_t s)
+    static int enqueue_p(stag_ctx ctx, MixedSlot& m, int tg, cudaStream_t s)
     {
-        STAG_TRY(launch_p(ctx, m, m.shape.pk, s, m.sc));
+        STAG_TRY(launch_p(ctx, m, m.shape[tg].pk, s, m.sc));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;
     }
 
-    static int solve(stag_ctx ctx, MixedSlot& m, const void* lk, double2* x_out, const double2* b_in, double mass,
-                     const stag_solver_params& prm, stag_solver_stats* st)
+    // tg: the links lk (and the reliable update's) are the temporal-gauge
+    // copies; the caller transforms b and x
+    static int solve(stag_ctx ctx, MixedSlot& m, const void* lk, int tg, double2* x_out, const double2* b_in,
+                     double mass, const stag_solver_params& prm, stag_solver_stats* st)
     {
         const auto t0 = std::chrono::steady_clock::now();
         Workspace* ws = ctx->ws;
         const Geom g = ctx->g;
         const void* lk64 = nullptr;
         const int p64 = std::is_same<typename LF64T::real, DF>::value ? STAG_F64X : STAG_F64;
-        STAG_TRY(ensure_links(ctx, p64, 18, &lk64));
-        const LF U{(const typename LF::store*)lk, g.Vh};
-        const LF64T U64{(const typename LF64T::store*)lk64, g.Vh};
+        STAG_TRY(tg ? ensure_links_tg(ctx, p64, 18, &lk64) : ensure_links(ctx, p64, 18, &lk64));
+        const LF U{(const typename LF::store*)lk, g.Vh, tg};
+        const LF64T U64{(const typename LF64T::store*)lk64, g.Vh, tg};
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
         const double delta = prm.delta > 0 ? prm.delta : 0.1;
         STAG_TRY(tune(ctx, m, U, prm.inner_prec, prm.inner_recon));
@@ -346,23 +351,23 @@ struct MixedPlan {
             m.template spinor<SX>(m.xlo), m.sc, prm.tol, maxiter, mass * mass, delta, ctx->partials, ctx->counters);
         STAG_CUDA_TRY(cudaGetLastError());
         if (prm.use_graph) {
-            if (!m.lg.exec || m.graph_arith != p64) {
-                LoopGraph& lg = m.lg;
+            if (!m.lg[tg].exec || m.graph_arith[tg] != p64) {
+                LoopGraph& lg = m.lg[tg];
                 STAG_TRY(build_loop_graph(
                     ctx->cap_stream, lg, true,
                     [&](cudaStream_t s) { return enqueue_main(ctx, m, U, s, &lg, 1); },
                     [&](cudaStream_t s) { return enqueue_reliable(ctx, m, U64, s, &lg, 1, 0); },
-                    [&](cudaStream_t s) { return enqueue_p(ctx, m, s); }));
-                m.graph_arith = p64;
+                    [&](cudaStream_t s) { return enqueue_p(ctx, m, tg, s); }));
+                m.graph_arith[tg] = p64;
             }
-            STAG_CUDA_TRY(cudaGraphLaunch(m.lg.exec, ctx->stream));
+            STAG_CUDA_TRY(cudaGraphLaunch(m.lg[tg].exec, ctx->stream));
         } else {
             const int every = prm.check_every > 0 ? prm.check_every : 25;
             for (;;) {
                 for (int k = 0; k < every; ++k) {
                     STAG_TRY(enqueue_main(ctx, m, U, ctx->stream, nullptr, 0));
                     STAG_TRY(enqueue_reliable(ctx, m, U64, ctx->stream, nullptr, 0, 1));
-                    STAG_TRY(enqueue_p(ctx, m, ctx->stream));
+                    STAG_TRY(enqueue_p(ctx, m, tg, ctx->stream));
                 }
                 STAG_CUDA_TRY(cudaMemcpyAsync(ws->sc_host, m.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                                               ctx->stream));
@@ -414,22 +419,32 @@ static int ensure_mixed(stag_ctx ctx, int prec, int recon, MixedSlot** out)
 }
 
 template <class LF64T, class SD64>
-static int dispatch_inner(stag_ctx ctx, MixedSlot& m, const void* lk, double2* x_out, const double2* b_in,
+static int dispatch_inner(stag_ctx ctx, MixedSlot& m, const void* lk, int tg, double2* x_out, const double2* b_in,
                           double mass, const stag_solver_params& prm, stag_solver_stats* st)
 {
     const int prec = prm.inner_prec, recon = prm.inner_recon;
     if (prec == STAG_F32) {
         if (recon == 12)
-            return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 12>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in,
-                                                                                             mass, prm, st);
-        return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 18>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in, mass,
-                                                                                         prm, st);
+            return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 12>, LF64T, SD64>::solve(ctx, m, lk, tg, x_out,
+                                                                                             b_in, mass, prm, st);
+        return MixedPlan<SpinorF32, SpinorF32, LinkField<float2, 18>, LF64T, SD64>::solve(ctx, m, lk, tg, x_out, b_in,
+                                                                                         mass, prm, st);
     }
     if (recon == 12)
-        return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 12>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in,
-                                                                                          mass, prm, st);
-    return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 18>, LF64T, SD64>::solve(ctx, m, lk, x_out, b_in, mass,
-                                                                                      prm, st);
+        return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 12>, LF64T, SD64>::solve(ctx, m, lk, tg, x_out,
+                                                                                          b_in, mass, prm, st);
+    return MixedPlan<SpinorF16, SpinorF32, LinkField<__half2, 18>, LF64T, SD64>::solve(ctx, m, lk, tg, x_out, b_in,
+                                                                                      mass, prm, st);
+}
+
+static int mixed_arith(stag_ctx ctx, MixedSlot& m, const void* lk, int tg, double2* x_out, const double2* b_in,
+                       double mass, const stag_solver_params& prm, stag_solver_stats* st)
+{
+    int arith = STAG_F64;
+    STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &arith));
+    if (arith == STAG_F64X)
+        return dispatch_inner<LinkFieldDF<18>, SpinorDF>(ctx, m, lk, tg, x_out, b_in, mass, prm, st);
+    return dispatch_inner<LinkField<double2, 18>, SpinorF64>(ctx, m, lk, tg, x_out, b_in, mass, prm, st);
 }
 
 int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mass, const stag_solver_params& prm,
@@ -444,18 +459,31 @@ int cg_solve_mixed(stag_ctx ctx, double2* x_out, const double2* b_in, double mas
     MixedSlot* m = nullptr;
     STAG_TRY(ensure_mixed(ctx, prec, recon, &m));
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
-    int arith = STAG_F64;
-    STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &arith));
-    if (arith == STAG_F64X) return dispatch_inner<LinkFieldDF<18>, SpinorDF>(ctx, *m, lk, x_out, b_in, mass, prm, st);
-    return dispatch_inner<LinkField<double2, 18>, SpinorF64>(ctx, *m, lk, x_out, b_in, mass, prm, st);
+    if (!prm.temporal_gauge) {
+        STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+        return mixed_arith(ctx, *m, lk, 0, x_out, b_in, mass, prm, st);
+    }
+    // temporal gauge: M' x' = g b with every operator pass on U' (the inner
+    // iteration and the reliable updates), x = g^dagger x'
+    const double2* G = nullptr;
+    double2* gb = nullptr;
+    STAG_TRY(ensure_links_tg(ctx, prec, recon, &lk));
+    STAG_TRY(ensure_tg_gauge(ctx, &G));
+    STAG_TRY(ensure_tg_tmp(ctx, 1, &gb));
+    STAG_TRY(tg_apply(ctx, G, b_in, gb, 1, 0));
+    const int rc = mixed_arith(ctx, *m, lk, 1, x_out, gb, mass, prm, st);
+    if (rc < 0) return rc;
+    STAG_TRY(tg_apply(ctx, G, x_out, x_out, 1, 1));
+    STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return rc;
 }
 
 void free_mixed(Workspace* ws)
 {
     for (auto& row : ws->mixed)
         for (auto& m : row) {
-            m.lg.destroy();
+            m.lg[0].destroy();
+            m.lg[1].destroy();
             void* bufs[] = {m.r, m.p, m.Ap, m.t, m.xlo, m.sc};
             for (void* b : bufs)
                 if (b) cudaFree(b);

@@ -130,18 +130,22 @@ int multi_cfg_for(int prec, int block)
 }
 
 int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs, int nb,
-                 int* nb_used, int* cfg_used)
+                 int* nb_used, int* cfg_used, int links)
 {
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    int tg = 0;
+    STAG_TRY(op_links_for(ctx, links, prec, recon, &lk, &tg));
     const int Vh = ctx->g.Vh;
+    // the autotuner's key names the link field (6 or 8 link reads per site)
+    const char* tag = links == STAG_LINKS_UPLOADED ? "multi_dslash"
+                      : links == STAG_LINKS_TEMPORAL ? "multi_dslash_tg" : "multi_dslash_tgfull";
     const size_t stride = lo_spinor_bytes(ctx->g, prec);
     if (prec == STAG_F64) {
         SpinorF64 si{(double2*)in}, so{(double2*)out};
         if (recon == 18)
-            return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<double2, 18>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+            return multi_dslash_tuned(ctx, tag, prec, recon, LinkField<double2, 18>{(const double2*)lk, Vh, tg}, si, so, stride, nrhs,
                                       par_out, nb, nb_used, cfg_used);
-        return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<double2, 12>{(const double2*)lk, Vh}, si, so, stride, nrhs,
+        return multi_dslash_tuned(ctx, tag, prec, recon, LinkField<double2, 12>{(const double2*)lk, Vh, tg}, si, so, stride, nrhs,
                                   par_out, nb, nb_used, cfg_used);
     }
     if (prec == STAG_F64X) {
@@ -154,28 +158,31 @@ int multi_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, cons
     if (prec == STAG_F32) {
         SpinorF32 si{(float2*)in, Vh}, so{(float2*)out, Vh};
         if (recon == 18)
-            return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<float2, 18>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+            return multi_dslash_tuned(ctx, tag, prec, recon, LinkField<float2, 18>{(const float2*)lk, Vh, tg}, si, so, stride, nrhs,
                                       par_out, nb, nb_used, cfg_used);
-        return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<float2, 12>{(const float2*)lk, Vh}, si, so, stride, nrhs,
+        return multi_dslash_tuned(ctx, tag, prec, recon, LinkField<float2, 12>{(const float2*)lk, Vh, tg}, si, so, stride, nrhs,
                                   par_out, nb, nb_used, cfg_used);
     }
     SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
     if (recon == 18)
-        return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<__half2, 18>{(const __half2*)lk, Vh}, si, so, stride, nrhs,
+        return multi_dslash_tuned(ctx, tag, prec, recon, LinkField<__half2, 18>{(const __half2*)lk, Vh, tg}, si, so, stride, nrhs,
                                   par_out, nb, nb_used, cfg_used);
-    return multi_dslash_tuned(ctx, "multi_dslash", prec, recon, LinkField<__half2, 12>{(const __half2*)lk, Vh}, si, so, stride, nrhs, par_out,
+    return multi_dslash_tuned(ctx, tag, prec, recon, LinkField<__half2, 12>{(const __half2*)lk, Vh, tg}, si, so, stride, nrhs, par_out,
                               nb, nb_used, cfg_used);
 }
 
 // The multi operator on a precision's internal storage (as multi_dslash,
 // except that STAG_F64X reads and writes double-float vectors).
 int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* out, const void* in, int nrhs,
-                          int nb, int* nb_used)
+                          int nb, int* nb_used, int links)
 {
-    if (prec != STAG_F64X) return multi_dslash(ctx, prec, recon, par_out, out, in, nrhs, nb, nb_used);
+    if (prec != STAG_F64X) return multi_dslash(ctx, prec, recon, par_out, out, in, nrhs, nb, nb_used, nullptr, links);
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
-    return multi_dslash_tuned(ctx, "multi_dslash_df", prec, recon, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh},
+    int tg = 0;
+    STAG_TRY(op_links_for(ctx, links, prec, recon, &lk, &tg));
+    const char* tag = links == STAG_LINKS_UPLOADED ? "multi_dslash_df"
+                      : links == STAG_LINKS_TEMPORAL ? "multi_dslash_df_tg" : "multi_dslash_df_tgfull";
+    return multi_dslash_tuned(ctx, tag, prec, recon, LinkFieldDF<18>{(const float4*)lk, ctx->g.Vh, tg},
                               SpinorDF{(float4*)in}, SpinorDF{(float4*)out}, lo_spinor_bytes(ctx->g, prec), nrhs,
                               par_out, nb, nb_used);
 }
@@ -216,14 +223,16 @@ int stag_dslash_multi(stag_ctx ctx, double* out, const double* in, int nrhs, int
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
-    if (prec == STAG_F64) return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr);
+    if (prec == STAG_F64)
+        return multi_dslash(ctx, prec, recon, out_parity, out, in, nrhs, rhs_block, nullptr, nullptr, ctx->op_links);
     if (prec == STAG_F64X)
-        return dslash_f64x_canonical(ctx, out_parity, (double2*)out, (const double2*)in, nrhs,
+        return dslash_f64x_canonical(ctx, out_parity, (double2*)out, (const double2*)in, nrhs, ctx->op_links,
                                      rhs_block ? rhs_block : 0, nullptr, ctx->stream);
     const size_t lo = lo_spinor_bytes(ctx->g, prec) * nrhs;
     STAG_TRY(ensure_lo_tmp_public(ctx, lo));
     STAG_TRY(convert_f64_to_lo(ctx, prec, (const double2*)in, ctx->tmp_lo_in, nrhs, ctx->stream));
-    STAG_TRY(multi_dslash(ctx, prec, recon, out_parity, ctx->tmp_lo_out, ctx->tmp_lo_in, nrhs, rhs_block, nullptr));
+    STAG_TRY(multi_dslash(ctx, prec, recon, out_parity, ctx->tmp_lo_out, ctx->tmp_lo_in, nrhs, rhs_block, nullptr,
+                          nullptr, ctx->op_links));
     return convert_lo_to_f64(ctx, prec, ctx->tmp_lo_out, (double2*)out, nrhs, ctx->stream);
 }
 

@@ -187,7 +187,8 @@ __device__ __forceinline__ void tile_site_multi(const Geom& g, int p, int h, con
     // neighbour arrays are indexed statically (registers, not local memory)
 #pragma unroll
     for (int hop = 0; hop < 8; ++hop)
-        if (on && hop % G == grp) HopStore<real>::put(sm, TS, hop, sl, hop_matrix(U, p, h, s, hop));
+        if (on && hop % G == grp && !unit_hop(U, s, hop))
+            HopStore<real>::put(sm, TS, hop, sl, hop_matrix(U, p, h, s, hop));
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NBT; ++k)
@@ -196,10 +197,26 @@ __device__ __forceinline__ void tile_site_multi(const Geom& g, int p, int h, con
     if (!on || !mask) return;
 #pragma unroll
     for (int hop = 0; hop < 8; ++hop) {
-        const Mat3<real> H = HopStore<real>::get(sm, TS, hop, sl);
         const int nb = (hop & 1) ? s.bwd[hop >> 1] : s.fwd[hop >> 1];
         // the neighbour spinors in batches of up to four loads in flight
         constexpr int NL = NBT < 4 ? NBT : 4;
+        if (unit_hop(U, s, hop)) {
+            // identity time link of a temporal-gauge field: the signed spinor
+            // is added (what the product with the hop matrix +-1 gives)
+            const uint32_t sb = (hop & 1) ? s.sb[3] : s.sf[3];
+#pragma unroll
+            for (int kb = 0; kb < NBT; kb += NL) {
+                Vec3<real> v[NL];
+#pragma unroll
+                for (int k = 0; k < NL; ++k)
+                    if (mask & (1u << (kb + k))) v[k] = load_flipped(in.at(k0 + kb + k, stride), nb, sb);
+#pragma unroll
+                for (int k = 0; k < NL; ++k)
+                    if (mask & (1u << (kb + k))) hop_add(acc[kb + k], v[k]);
+            }
+            continue;
+        }
+        const Mat3<real> H = HopStore<real>::get(sm, TS, hop, sl);
 #pragma unroll
         for (int kb = 0; kb < NBT; kb += NL) {
             Vec3<real> v[NL];

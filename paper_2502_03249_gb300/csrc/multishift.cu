@@ -239,18 +239,18 @@ struct MsPlan {
         return STAG_OK;
     }
 
-    static int run(stag_ctx ctx, MsSlot& m, const void* lk, const double2* b, double mass, const double* shifts_dev,
-                   double tol, int maxiter, const stag_solver_params& prm)
+    static int run(stag_ctx ctx, MsSlot& m, const void* lk, int tg, const double2* b, double mass,
+                   const double* shifts_dev, double tol, int maxiter, const stag_solver_params& prm)
     {
         const Geom g = ctx->g;
-        const LF U{(const typename LF::store*)lk, g.Vh};
+        const LF U{(const typename LF::store*)lk, g.Vh, tg};
         const S P = m.template spinor<S>(m.P), X = m.template spinor<S>(m.X), r = m.template spinor<S>(m.r);
         k_ms_start<S, MS_BLAS><<<(g.Vh + MS_BLAS - 1) / MS_BLAS, MS_BLAS, 0, ctx->stream>>>(
             g.Vh, b, r, P, X, m.stride, m.nshift, m.sc, m.ms, shifts_dev, m.base, tol, maxiter, mass * mass,
             ctx->partials, ctx->counters + 2);
         STAG_CUDA_TRY(cudaGetLastError());
         if (prm.use_graph) {
-            if (!m.lg.exec || m.graph_n != m.nshift || m.graph_base != m.base) {
+            if (!m.lg.exec || m.graph_n != m.nshift || m.graph_base != m.base || m.graph_tg != tg) {
                 LoopGraph& lg = m.lg;
                 auto none = [](cudaStream_t) { return STAG_OK; };
                 STAG_TRY(build_loop_graph(ctx->cap_stream, lg, false,
@@ -258,6 +258,7 @@ struct MsPlan {
                                           none));
                 m.graph_n = m.nshift;
                 m.graph_base = m.base;
+                m.graph_tg = tg;
             }
             STAG_CUDA_TRY(cudaGraphLaunch(m.lg.exec, ctx->stream));
         } else {
@@ -284,7 +285,7 @@ void MsSlot::release()
 }
 
 int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double mass, const double* shifts_host,
-                  const double2* X0, const stag_solver_params& prm, stag_solver_stats* stats);
+                  const double2* X0, const stag_solver_params& prm, stag_solver_stats* stats, int tg);
 
 int multishift_solve(stag_ctx ctx, double2* X, const double2* b, const double* shifts, int nshift, double mass,
                      const stag_solver_params& prm, stag_solver_stats* stats)
@@ -321,8 +322,18 @@ int multishift_solve(stag_ctx ctx, double2* X, const double2* b, const double* s
     m.nshift = nshift;
     m.base = base;
     STAG_CUDA_TRY(cudaMemcpyAsync(m.shifts, shifts, nshift * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    // temporal gauge: both phases on U' for b' = g b; X = g^dagger X' at the end
+    const int tg = prm.temporal_gauge ? 1 : 0;
     const void* lk = nullptr;
-    STAG_TRY(ensure_links(ctx, prec, recon, &lk));
+    const double2* G = nullptr;
+    STAG_TRY(tg ? ensure_links_tg(ctx, prec, recon, &lk) : ensure_links(ctx, prec, recon, &lk));
+    if (tg) {
+        double2* gb = nullptr;
+        STAG_TRY(ensure_tg_gauge(ctx, &G));
+        STAG_TRY(ensure_tg_tmp(ctx, 1, &gb));
+        STAG_TRY(tg_apply(ctx, G, b, gb, 1, 0));
+        b = gb;
+    }
     const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
     // b' = 2^-k b (largest component in [1, 2)) in the first replica: the Krylov
     // phase and the refinement solve for b', the solutions are scaled by 2^k
@@ -333,11 +344,11 @@ int multishift_solve(stag_ctx ctx, double2* X, const double2* b, const double* s
     // the Krylov phase stops at the inner precision's reach; refinement does the rest
     const double tol1 = prec == STAG_F64 ? prm.tol : (prm.tol > 1e-6 ? prm.tol : 1e-6);
     if (prec == STAG_F64) {
-        if (recon == 18) STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 18>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
-        else STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 12>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
+        if (recon == 18) STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 18>>::run(ctx, m, lk, tg, bn, mass, m.shifts, tol1, maxiter, prm)));
+        else STAG_TRY((MsPlan<SpinorF64, LinkField<double2, 12>>::run(ctx, m, lk, tg, bn, mass, m.shifts, tol1, maxiter, prm)));
     } else {
-        if (recon == 18) STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 18>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
-        else STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 12>>::run(ctx, m, lk, bn, mass, m.shifts, tol1, maxiter, prm)));
+        if (recon == 18) STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 18>>::run(ctx, m, lk, tg, bn, mass, m.shifts, tol1, maxiter, prm)));
+        else STAG_TRY((MsPlan<SpinorF32, LinkField<float2, 12>>::run(ctx, m, lk, tg, bn, mass, m.shifts, tol1, maxiter, prm)));
     }
     CgScalars hs;
     STAG_CUDA_TRY(cudaMemcpyAsync(&hs, m.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->stream));
@@ -359,9 +370,10 @@ int multishift_solve(stag_ctx ctx, double2* X, const double2* b, const double* s
     p2.inner_prec = prec == STAG_F64 ? STAG_F64 : prm.inner_prec;
     p2.inner_recon = prm.inner_recon;
     p2.maxiter = maxiter > ms_iters ? maxiter - ms_iters : 1;
-    const int rc = batched_solve(ctx, X, (const double2*)m.brep, nshift, mass, shifts, X, p2, stats);
+    const int rc = batched_solve(ctx, X, (const double2*)m.brep, nshift, mass, shifts, X, p2, stats, tg);
     if (rc < 0) return rc;
     STAG_TRY(scale_fields_out(ctx, X, X, nshift, (size_t)3 * g.Vh, SLOT_OUTER, 0, ctx->stream));
+    if (tg) STAG_TRY(tg_apply(ctx, G, X, X, nshift, 1));
     STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     if (stats) {
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

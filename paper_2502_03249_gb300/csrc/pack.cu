@@ -95,6 +95,7 @@ int upload_gauge(stag_ctx ctx, const double* U, int on_device)
     // Derived copies are kept at their addresses and re-derived in place on
     // their next use: CUDA graphs captured by the solvers hold these pointers.
     for (int s = 1; s < 8; ++s) ctx->link_stale[s] = ctx->links[s] != nullptr;
+    for (int s = 0; s < 8; ++s) ctx->tg_link_stale[s] = ctx->tg_links[s] != nullptr;
     ctx->tg_stale = true;
     ctx->link_exp_known = false;
     if (!ctx->links[0]) {
@@ -111,6 +112,29 @@ int upload_gauge(stag_ctx ctx, const double* U, int on_device)
     return STAG_OK;
 }
 
+int derive_link_copy(stag_ctx ctx, const double2* src, int prec, int recon, int e, void** dst, size_t* bytes_out)
+{
+    const int NE = recon == 12 ? 6 : 9;
+    const size_t esz = (prec == STAG_F64 || prec == STAG_F64X) ? 16 : (prec == STAG_F32 ? 8 : 4);
+    const size_t bytes = (size_t)8 * ctx->g.Vh * NE * esz;
+    void* p = *dst;
+    if (!p) STAG_CUDA_TRY(cudaMalloc(&p, bytes));
+    *dst = p;
+    *bytes_out = bytes;
+    const long long work = 8LL * ctx->g.Vh;
+    const int BS = 256;
+    const unsigned grid = (unsigned)((work + BS - 1) / BS);
+    const int Vh = ctx->g.Vh;
+    if (prec == STAG_F64X) k_split_links<<<grid, BS, 0, ctx->stream>>>(Vh, src, (float4*)p, e);
+    else if (prec == STAG_F64) k_derive_links_f64_12<<<grid, BS, 0, ctx->stream>>>(Vh, src, (double2*)p);
+    else if (prec == STAG_F32 && NE == 9) k_derive_links_vec<8, 9><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
+    else if (prec == STAG_F32) k_derive_links_vec<8, 6><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
+    else if (NE == 9) k_derive_links_vec<4, 9><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
+    else k_derive_links_vec<4, 6><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return STAG_OK;
+}
+
 int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
 {
     if (!ctx->have_gauge) {
@@ -123,36 +147,16 @@ int ensure_links(stag_ctx ctx, int prec, int recon, const void** out)
     }
     const int slot = link_slot(prec, recon);
     if (!ctx->links[slot] || ctx->link_stale[slot]) {
-        const int NE = recon == 12 ? 6 : 9;
-        const size_t esz = (prec == STAG_F64 || prec == STAG_F64X) ? 16 : (prec == STAG_F32 ? 8 : 4);
-        const size_t bytes = (size_t)8 * ctx->g.Vh * NE * esz;
-        void* p = ctx->links[slot];
-        if (!p) STAG_CUDA_TRY(cudaMalloc(&p, bytes));
-        const long long work = 8LL * ctx->g.Vh;
-        const int BS = 256;
-        const unsigned grid = (unsigned)((work + BS - 1) / BS);
-        const double2* src = (const double2*)ctx->links[0];
-        const int Vh = ctx->g.Vh;
+        int e = 0;
         if (prec == STAG_F64X) {
             // links whose largest element leaves the double-float range are
             // stored as 2^-e U (operator results scaled back by 2^e)
-            int e = 0;
-            const int rc = link_max_exponent(ctx, &e);
-            if (rc < 0) {
-                if (!ctx->links[slot]) cudaFree(p);   // allocated just above
-                return rc;
-            }
+            STAG_TRY(link_max_exponent(ctx, &e));
             ctx->df_link_exp = (e > DF_LINK_SAFE_EXP || e < -DF_LINK_SAFE_EXP) ? e : 0;
-            k_split_links<<<grid, BS, 0, ctx->stream>>>(Vh, src, (float4*)p, ctx->df_link_exp);
+            e = ctx->df_link_exp;
         }
-        else if (prec == STAG_F64) k_derive_links_f64_12<<<grid, BS, 0, ctx->stream>>>(Vh, src, (double2*)p);
-        else if (prec == STAG_F32 && NE == 9) k_derive_links_vec<8, 9><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
-        else if (prec == STAG_F32) k_derive_links_vec<8, 6><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
-        else if (NE == 9) k_derive_links_vec<4, 9><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
-        else k_derive_links_vec<4, 6><<<grid, BS, 0, ctx->stream>>>(Vh, src, (char*)p);
-        STAG_CUDA_TRY(cudaGetLastError());
-        ctx->links[slot] = p;
-        ctx->link_bytes[slot] = bytes;
+        STAG_TRY(derive_link_copy(ctx, (const double2*)ctx->links[0], prec, recon, e, &ctx->links[slot],
+                                  &ctx->link_bytes[slot]));
         ctx->link_stale[slot] = false;
     }
     *out = ctx->links[slot];

@@ -1,9 +1,11 @@
-// tgauge.cu -- the temporal-gauge transform (see tgauge.cuh): the gauge
-// matrices g, the transformed double-float links, and g / g^dagger applied to
-// even-site vectors.  Computed in IEEE double from the internal F64/18 links
-// once per gauge upload, on first use.
+// tgauge.cu -- the temporal-gauge transform (Sec. 4.3; the layout and the
+// operator's use of it are described in common.cuh): the gauge matrices g,
+// the transformed links U' = g U g^dagger in every storage, and g / g^dagger
+// applied to even-site vectors.  Computed in IEEE double from the internal
+// F64/18 links once per gauge upload, on first use; the reduced-precision
+// and double-float copies are derived from the double U' like the untransformed
+// copies are from U.
 #include "ctx.h"
-#include "tgauge.cuh"
 
 namespace stag {
 
@@ -101,19 +103,18 @@ __device__ __forceinline__ Mat3<double> load_g(const double2* G, int Vh, int par
     return M;
 }
 
-__device__ __forceinline__ void store_df(float4* q, size_t stride, const Mat3<double>& U)
+__device__ __forceinline__ void store_link64(double2* q, size_t stride, const Mat3<double>& U)
 {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const DF re = split_double(U.m[k].re), im = split_double(U.m[k].im);
-        q[(size_t)k * stride] = make_float4(re.hi, re.lo, im.hi, im.lo);
-    }
+    for (int k = 0; k < 9; ++k) q[(size_t)k * stride] = make_double2(U.m[k].re, U.m[k].im);
 }
 
-// U'_mu(x) = g(x) U_mu(x) g(x + mu)^dagger for the spatial directions, and
-// U'_t(x) = g(x) U_t(x) on the last time slice; one thread per (par, h).
+// U'_mu(x) = g(x) U_mu(x) g(x + mu)^dagger for the spatial directions;
+// U'_t(x) = g(x) U_t(x) on the last time slice (g = 1 at t = 0) and exactly
+// the identity elsewhere.  F64/18 layout [((par*4 + mu)*9 + k)*V/2 + h]; one
+// thread per (par, h).
 __global__ void k_tg_links(Geom g, const double2* __restrict__ L, const double2* __restrict__ G,
-                           float4* __restrict__ out)
+                           double2* __restrict__ out)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 2LL * g.Vh) return;
@@ -125,25 +126,33 @@ __global__ void k_tg_links(Geom g, const double2* __restrict__ L, const double2*
     for (int mu = 0; mu < 3; ++mu) {
         const Mat3<double> U = load_link64(L, g.Vh, par, mu, h);
         const Mat3<double> Up = mmd(mm(gx, U), load_g(G, g.Vh, 1 - par, s.fwd[mu]));
-        store_df(out + ((size_t)(par * 3 + mu) * 9) * g.Vh + h, g.Vh, Up);
+        store_link64(out + ((size_t)(par * 4 + mu) * 9) * g.Vh + h, g.Vh, Up);
     }
     const int Vsh = g.Vh / g.L[3];
     const int t = h / Vsh;
-    if (t == g.L[3] - 1)
-        store_df(out + (size_t)54 * g.Vh + ((size_t)par * 9) * Vsh + (h - t * Vsh), Vsh,
-                 mm(gx, load_link64(L, g.Vh, par, 3, h)));
+    Mat3<double> Ut;
+    if (t == g.L[3] - 1) {
+        Ut = mm(gx, load_link64(L, g.Vh, par, 3, h));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ut.m[k] = {(k % 4 == 0) ? 1.0 : 0.0, 0.0};
+    }
+    store_link64(out + ((size_t)(par * 4 + 3) * 9) * g.Vh + h, g.Vh, Ut);
 }
 
-// out = g v (dagger = 0) or g^dagger v (dagger = 1) on even sites; in place allowed.
-__global__ void k_tg_apply(int Vh, const double2* __restrict__ G, const double2* in, double2* out, int dagger)
+// out = g v (dagger = 0) or g^dagger v (dagger = 1) on even sites, for
+// nfield fields of V/2 sites back to back; in place allowed.
+__global__ void k_tg_apply(int Vh, int nfield, const double2* __restrict__ G, const double2* in, double2* out,
+                           int dagger)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= Vh) return;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nfield * Vh) return;
+    const int h = (int)(idx % Vh);
     const Mat3<double> M = load_g(G, Vh, 0, h);
     Cplx<double> v[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double2 q = in[(size_t)h * 3 + c];
+        const double2 q = in[(size_t)idx * 3 + c];
         v[c] = {q.x, q.y};
     }
 #pragma unroll
@@ -156,13 +165,13 @@ __global__ void k_tg_apply(int Vh, const double2* __restrict__ G, const double2*
             s.re += p.re;
             s.im += p.im;
         }
-        out[(size_t)h * 3 + a] = make_double2(s.re, s.im);
+        out[(size_t)idx * 3 + a] = make_double2(s.re, s.im);
     }
 }
 
-// The gauge matrices and the temporal-gauge links for the current gauge
-// field, computed on first use after an upload (kept at their addresses).
-int ensure_tg(stag_ctx ctx, const double2** G, const float4** links)
+// The gauge matrices g for the current gauge field, computed on first use
+// after an upload (kept at their address).
+int ensure_tg_gauge(stag_ctx ctx, const double2** G)
 {
     if (!ctx->have_gauge) {
         set_error("no gauge field uploaded");
@@ -170,27 +179,78 @@ int ensure_tg(stag_ctx ctx, const double2** G, const float4** links)
     }
     const Geom g = ctx->g;
     if (!ctx->tg_g || ctx->tg_stale) {
-        const size_t gbytes = (size_t)2 * g.Vh * 9 * sizeof(double2);
-        const size_t lbytes = ((size_t)54 * g.Vh + (size_t)18 * (g.Vh / g.L[3])) * sizeof(float4);
-        if (!ctx->tg_g) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_g, gbytes));
-        if (!ctx->tg_links) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_links, lbytes));
-        const double2* L = (const double2*)ctx->links[0];
+        if (!ctx->tg_g) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_g, (size_t)2 * g.Vh * 9 * sizeof(double2)));
         const long long Vs = (long long)g.L[0] * g.L[1] * g.L[2];
-        k_tg_gauge<<<(unsigned)((Vs + 127) / 128), 128, 0, ctx->stream>>>(g, L, ctx->tg_g);
-        const long long n = 2LL * g.Vh;
-        k_tg_links<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, L, ctx->tg_g, ctx->tg_links);
+        k_tg_gauge<<<(unsigned)((Vs + 127) / 128), 128, 0, ctx->stream>>>(g, (const double2*)ctx->links[0],
+                                                                        ctx->tg_g);
         STAG_CUDA_TRY(cudaGetLastError());
         ctx->tg_stale = false;
+        // every transformed copy was made from the previous g
+        for (int s = 0; s < 8; ++s) ctx->tg_link_stale[s] = ctx->tg_links[s] != nullptr;
     }
     *G = ctx->tg_g;
-    *links = ctx->tg_links;
     return STAG_OK;
 }
 
-int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int dagger)
+// U' in the storage (prec, recon): the F64/18 copy (slot 0) from g and U, the
+// others derived from it (allocated on first use, re-derived in place after an
+// upload: graphs hold these addresses).
+int ensure_links_tg(stag_ctx ctx, int prec, int recon, const void** out)
 {
-    const int Vh = ctx->g.Vh;
-    k_tg_apply<<<(Vh + 255) / 256, 256, 0, ctx->stream>>>(Vh, G, in, out, dagger);
+    const double2* G = nullptr;
+    STAG_TRY(ensure_tg_gauge(ctx, &G));
+    const Geom g = ctx->g;
+    if (!ctx->tg_links[0] || ctx->tg_link_stale[0]) {
+        const size_t bytes = (size_t)8 * g.Vh * 9 * sizeof(double2);
+        if (!ctx->tg_links[0]) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_links[0], bytes));
+        ctx->tg_link_bytes[0] = bytes;
+        const long long n = 2LL * g.Vh;
+        k_tg_links<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, (const double2*)ctx->links[0], G,
+                                                                       (double2*)ctx->tg_links[0]);
+        STAG_CUDA_TRY(cudaGetLastError());
+        ctx->tg_link_stale[0] = false;
+        for (int s = 1; s < 8; ++s) ctx->tg_link_stale[s] = ctx->tg_links[s] != nullptr;
+    }
+    const int slot = link_slot(prec, recon);
+    if (slot != 0 && (!ctx->tg_links[slot] || ctx->tg_link_stale[slot])) {
+        int e = 0;
+        if (prec == STAG_F64X) {
+            // the scaling rule of the untransformed double-float copy (|U'| and
+            // |U| are bounded alike for the unitary links this path needs)
+            STAG_TRY(link_max_exponent(ctx, &e));
+            ctx->df_link_exp = (e > DF_LINK_SAFE_EXP || e < -DF_LINK_SAFE_EXP) ? e : 0;
+            e = ctx->df_link_exp;
+        }
+        STAG_TRY(derive_link_copy(ctx, (const double2*)ctx->tg_links[0], prec, recon, e, &ctx->tg_links[slot],
+                                  &ctx->tg_link_bytes[slot]));
+        ctx->tg_link_stale[slot] = false;
+    }
+    *out = ctx->tg_links[slot];
+    return STAG_OK;
+}
+
+// Room for g b of nfield even-site fields (grown on demand; not held by graphs).
+int ensure_tg_tmp(stag_ctx ctx, int nfield, double2** out)
+{
+    if (nfield > ctx->tg_tmp_fields) {
+        if (ctx->tg_tmp) {
+            STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            cudaFree(ctx->tg_tmp);
+            ctx->tg_tmp = nullptr;
+            ctx->tg_tmp_fields = 0;
+        }
+        STAG_CUDA_TRY(cudaMalloc(&ctx->tg_tmp, (size_t)nfield * 3 * ctx->g.Vh * sizeof(double2)));
+        ctx->tg_tmp_fields = nfield;
+    }
+    *out = ctx->tg_tmp;
+    return STAG_OK;
+}
+
+int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int nfield, int dagger)
+{
+    const long long n = (long long)nfield * ctx->g.Vh;
+    if (n == 0) return STAG_OK;
+    k_tg_apply<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->g.Vh, nfield, G, in, out, dagger);
     STAG_CUDA_TRY(cudaGetLastError());
     return STAG_OK;
 }

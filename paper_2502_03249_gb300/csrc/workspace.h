@@ -19,12 +19,15 @@ struct MixedSlot {
     void *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr;   // inner precision
     void* xlo = nullptr;                                             // float accumulator of x
     CgScalars* sc = nullptr;
-    LoopGraph lg;
+    // per link field [as uploaded, temporal gauge]: the loop graph (it holds
+    // the link fields it was captured with), the double arithmetic of its
+    // reliable update, and the inner kernels' launch shapes (autotuned once)
+    LoopGraph lg[2];
     int Vh = 0;
-    int graph_arith = -1;   // double arithmetic the graph's reliable update was built with
+    int graph_arith[2] = {-1, -1};
     bool ready = false;
-    CgShape shape;          // launch shapes of the inner kernels (autotuned once)
-    bool tuned = false;
+    CgShape shape[2];
+    bool tuned[2] = {false, false};
     template <class S> S spinor(void* buf) const;
 };
 template <> inline SpinorF32 MixedSlot::spinor<SpinorF32>(void* buf) const { return SpinorF32{(float2*)buf, Vh}; }
@@ -46,6 +49,7 @@ struct BatchSlot {
     unsigned* cnt_sys = nullptr;   // per-system reduction counters, zero between kernels
     size_t s_stride = 0, sx_stride = 0, f64_stride = 0;
     int Vh = 0, cap = 0, nrhs = 0, gx = 0, prec = 0, graph_nb = 0, graph_arith = -1;
+    int tg = 0, graph_tg = -1;     // temporal-gauge links (this solve's, and the graph's)
     bool ready = false;
     LoopGraph lg;
     template <class S> S spinor(void* buf) const;
@@ -68,7 +72,7 @@ struct MsSlot {
     double* shifts = nullptr;
     double2* brep = nullptr;
     size_t stride = 0;
-    int Vh = 0, cap = 0, nshift = 0, base = 0, graph_n = 0, graph_base = -1;
+    int Vh = 0, cap = 0, nshift = 0, base = 0, graph_n = 0, graph_base = -1, graph_tg = -1;
     bool ready = false;
     LoopGraph lg;
     template <class S> S spinor(void* buf) const;
@@ -84,13 +88,15 @@ struct Workspace {
     CgScalars* sc = nullptr;        // device scalar records
     CgScalars* sc_host = nullptr;   // pinned host mirror for the final read
     bool f64_ready = false;
-    cudaGraph_t f64_graph[3] = {nullptr, nullptr, nullptr};   // [IEEE double, double-float, temporal gauge]
-    cudaGraphExec_t f64_exec[3] = {nullptr, nullptr, nullptr};
+    // per plan [IEEE double, double-float, double-float in temporal gauge,
+    // IEEE double in temporal gauge]
+    cudaGraph_t f64_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t f64_exec[4] = {nullptr, nullptr, nullptr, nullptr};
     // double-float CG: 1 applies p = r + beta p inside the operator passes
     // (three launches per iteration), 0 as a pass of its own; -1 undecided
     int df_dir = -1;
-    CgShape cg_shape[3];            // per plan [IEEE double, double-float, temporal gauge]
-    bool cg_tuned[3] = {false, false, false};
+    CgShape cg_shape[4];            // per plan, as f64_graph
+    bool cg_tuned[4] = {false, false, false, false};
     MixedSlot mixed[2][2];          // [F32, F16][18, 12]
     BatchSlot batch[3][2];          // [F64, F32, F16][18, 12]
     MsSlot ms[2];                   // multi-shift [F64, F32]

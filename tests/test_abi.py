@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_strerror(lib):
-    assert lib.stag_abi_version() == 2
+    assert lib.stag_abi_version() == 3
     for code in (0, 1, 2, -1, -2, -3, -4, -5, -6):
         assert len(lib.stag_strerror(code)) > 0
     assert lib.stag_strerror(12345) == b"unknown status"
