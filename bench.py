@@ -423,8 +423,10 @@ def profile_kernel(args, stag, torch):
         b = li.gaussian_half_torch(dims2, seed=li.workload_seed(2, 1))
         x = ctx.new_half()
         prec = {"f32": stag.F32, "f16": stag.F16}[parts[1]]
+        tg = 1 if len(parts) > 3 and parts[3] == "tg" else 0   # mixed_<prec>_12_tg: in temporal gauge
         for _ in range(args.warmup + args.steps):
-            ctx.cg_solve_mixed(x, b, w2["mass"], tol=TOL, inner_prec=prec, inner_recon=int(parts[2]), use_graph=0)
+            ctx.cg_solve_mixed(x, b, w2["mass"], tol=TOL, inner_prec=prec, inner_recon=int(parts[2]), use_graph=0,
+                               temporal_gauge=tg)
         torch.cuda.synchronize()
         print(json.dumps({"profile_kernel": name, "workload": w2["name"], "solves": args.warmup + args.steps}))
         return 0
@@ -477,6 +479,9 @@ def profile_kernel(args, stag, torch):
     prec = {"f64": stag.F64, "f32": stag.F32, "f16": stag.F16, "f64x": stag.F64X}[parts[1]]
     recon = int(parts[2])
     psi = torch.from_numpy(li.gaussian_half(dims, seed=99)).cuda()
+    # dslash_<prec>_<recon>_tg: on the temporal-gauge links (identity time links skipped)
+    if len(parts) > 3 and parts[3] == "tg":
+        ctx.set_operator_links(stag.LINKS_TEMPORAL)
     # the bare kernel on the precision's internal storage, as the benchmark times it
     ctx.dslash_prepare(psi, prec)
     for _ in range(args.warmup + args.steps):
@@ -638,9 +643,11 @@ def section_paper_tables(stag, torch, timer, hbm):
         row, blocks = {}, {}
         for n in sorted(PAPER_TABLE2_A100):
             ctx.dslash_prepare_multi(psi[:n].contiguous(), prec)
-            ctx.dslash_repeat_multi(prec, recon, 0, 1)      # the autotuner picks the vectors per link load
+            ctx.dslash_repeat_multi(prec, recon, 0, 1)      # the autotuner picks the configuration (cached)
             blocks[n] = ctx.last_rhs_block()
-            ms, _ = timer(lambda: ctx.dslash_repeat_multi(prec, recon, blocks[n], 1), reps=5, warm=2)
+            # timed in the tuned configuration (rhs_block 0 reuses the cached
+            # decision; a block size alone would not name the link-tile split)
+            ms, _ = timer(lambda: ctx.dslash_repeat_multi(prec, recon, 0, 1), reps=5, warm=2)
             row[n] = FLOP_PER_SITE * Vh * n / (ms * 1e-3) * 1e-12
         scan[label] = {"tflops_by_nmulti": row, "rhs_block": blocks, "best": max(row.values())}
     ctx.set_operator_links(stag.LINKS_UPLOADED)
@@ -724,7 +731,8 @@ def main():
                          "dslash_f64_18, dslash_f64x_18, dslash_f32_12, dslash_f16_12, ..., dslash_all (one launch "
                          "of each storage), or whole host-driven solves cg_f64 / cg_f64x, multi_f32_12 / "
                          "multishift_f32_12 (32^3 x 16), mixed_f16_12 / mixed_f32_12 (48^3 x 12), or force "
-                         "(32^3 x 16); optional @LXxLYxLZxLT")
+                         "(32^3 x 16); a _tg suffix on an operator or mixed mode selects the temporal-gauge "
+                         "links; optional @LXxLYxLZxLT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

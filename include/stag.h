@@ -238,7 +238,7 @@ typedef struct {
     int use_graph;         /* 1: iterate inside one CUDA graph with a device-side loop;
                               0: host-driven loop (one stream sync per check_every iterations) */
     int check_every;       /* host-driven loop only: iterations between convergence reads */
-    double delta;          /* mixed precision: reliable update when ||r|| < delta * max ||r||; <= 0: 0.1 */
+    double delta;          /* mixed precision: reliable update when ||r|| < delta * max ||r||; <= 0: 0.01 */
     int inner_prec;        /* mixed precision: STAG_F32 or STAG_F16 */
     int inner_recon;       /* mixed precision: STAG_RECON_18 or STAG_RECON_12 */
     int rhs_block;         /* batched solves: right-hand sides per operator pass; 0: autotune */
@@ -269,7 +269,7 @@ typedef struct {
 } stag_solver_stats;
 
 /* Fill *p with defaults: tol 1e-10, maxiter 100000, use_graph 1, check_every 25,
- * delta 0.1, inner_prec STAG_F32, inner_recon STAG_RECON_12, rhs_block 0,
+ * delta 0.01, inner_prec STAG_F32, inner_recon STAG_RECON_12, rhs_block 0,
  * f64_arith STAG_F64X (double-float operator passes: on GB300 about twice as
  * fast as IEEE double ones, which are FP64-ALU-bound, with results equal to
  * ~1e-14 relative). */

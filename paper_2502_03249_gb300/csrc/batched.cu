@@ -72,7 +72,7 @@ int batched_solve(stag_ctx ctx, double2* X, const double2* B, int nrhs, double m
     const void* lk = nullptr;
     STAG_TRY(tg ? ensure_links_tg(ctx, prec, recon, &lk) : ensure_links(ctx, prec, recon, &lk));
     m.tg = tg;
-    const double delta = prec == STAG_F64 ? 0.0 : (prm.delta > 0 ? prm.delta : 0.1);
+    const double delta = prec == STAG_F64 ? 0.0 : (prm.delta > 0 ? prm.delta : DEFAULT_RELIABLE_DELTA);
     const size_t vbytes = (size_t)nrhs * m.f64_stride;
     stag_solver_params prm2 = prm;
     STAG_TRY(resolve_f64_arith(ctx, prm.f64_arith, &prm2.f64_arith));

@@ -619,7 +619,7 @@ void stag_solver_params_default(stag_solver_params* p)
     p->maxiter = 100000;
     p->use_graph = 1;
     p->check_every = 25;
-    p->delta = 0.1;
+    p->delta = DEFAULT_RELIABLE_DELTA;
     p->inner_prec = STAG_F32;
     p->inner_recon = STAG_RECON_12;
     p->rhs_block = 0;

@@ -227,16 +227,23 @@ __device__ __forceinline__ void reconstruct_row2(Mat3<T>& U)
 {
     const Cplx<T>* a = &U.m[0];
     const Cplx<T>* b = &U.m[3];
-    // c_k = conj(a_i b_j - a_j b_i) for (k,i,j) cyclic
+    // c_k = conj(a_i b_j - a_j b_i) for (k,i,j) cyclic: each part one
+    // product and three FMAs (the conjugate's sign folded into the operands)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int i = (k + 1) % 3, j = (k + 2) % 3;
-        const T re1 = fma(a[i].re, b[j].re, -mul_rn(a[i].im, b[j].im));
-        const T re2 = fma(a[j].re, b[i].re, -mul_rn(a[j].im, b[i].im));
-        const T im1 = fma(a[i].re, b[j].im, mul_rn(a[i].im, b[j].re));
-        const T im2 = fma(a[j].re, b[i].im, mul_rn(a[j].im, b[i].re));
-        U.m[6 + k].re = sub_rn(re1, re2);
-        U.m[6 + k].im = -sub_rn(im1, im2);
+        // re = a_i.re b_j.re - a_i.im b_j.im - a_j.re b_i.re + a_j.im b_i.im
+        T re = mul_rn(a[j].im, b[i].im);
+        re = fma(-a[j].re, b[i].re, re);
+        re = fma(-a[i].im, b[j].im, re);
+        re = fma(a[i].re, b[j].re, re);
+        // -im = a_j.re b_i.im + a_j.im b_i.re - a_i.re b_j.im - a_i.im b_j.re
+        T im = mul_rn(a[j].re, b[i].im);
+        im = fma(a[j].im, b[i].re, im);
+        im = fma(-a[i].re, b[j].im, im);
+        im = fma(-a[i].im, b[j].re, im);
+        U.m[6 + k].re = re;
+        U.m[6 + k].im = im;
     }
 }
 

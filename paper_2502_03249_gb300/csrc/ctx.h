@@ -36,6 +36,13 @@ void set_error(const char* fmt, ...);
 constexpr int SCALE_SLOTS = 200;
 constexpr int SLOT_SOLVE = 0, SLOT_OUTER = 64, SLOT_OPER = 128, SLOT_FORCE = 192, SLOT_LINKS = SCALE_SLOTS - 1;
 constexpr int DF_LINK_SAFE_EXP = 40;
+// Reliable-update threshold of the mixed, batched and multi-shift solvers
+// (||r|| < delta max ||r|| since the last update): 0.01 keeps the float and
+// half recurrences accurate (at most one extra iteration at 48^3 x 12,
+// m = 0.002) with half the double-precision passes of 0.1 (half inner
+// 12.7 -> 11.1 ms, float 15.3 -> 13.6 ms, 16 RHS at 32^3 x 16 73.8 -> 66.0 ms);
+// 0.003 added iterations to the half solve.
+constexpr double DEFAULT_RELIABLE_DELTA = 0.01;
 constexpr int FLOAT_INNER_LINK_EXP = 20;
 
 // Index of a (precision, compression) link copy.

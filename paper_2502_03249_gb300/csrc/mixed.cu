@@ -341,7 +341,7 @@ struct MixedPlan {
         const LF U{(const typename LF::store*)lk, g.Vh, tg};
         const LF64T U64{(const typename LF64T::store*)lk64, g.Vh, tg};
         const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
-        const double delta = prm.delta > 0 ? prm.delta : 0.1;
+        const double delta = prm.delta > 0 ? prm.delta : DEFAULT_RELIABLE_DELTA;
         STAG_TRY(tune(ctx, m, U, prm.inner_prec, prm.inner_recon));
         // b' = 2^-k b (largest component in [1, 2)): the float / half inner
         // storage and the double-float passes stay in range for any b; x = 2^k x'

@@ -69,7 +69,7 @@ def test_solver_param_defaults(lib):
     p = stag.SolverParams()
     lib.stag_solver_params_default(ctypes.byref(p))
     assert p.tol == 1e-10 and p.maxiter == 100000 and p.use_graph == 1
-    assert p.inner_prec == stag.F32 and p.inner_recon == 12 and p.delta == 0.1
+    assert p.inner_prec == stag.F32 and p.inner_recon == 12 and p.delta == 0.01
     assert p.f64_arith == stag.F64X and p.temporal_gauge == 0
 
 
