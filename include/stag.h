@@ -123,7 +123,9 @@ int stag_upload_gauge(stag_ctx ctx, const double *U, int on_device);
  *                             links as stored): the same values, for checks.
  * Affects stag_dslash_eo/oe, stag_dslash_multi and stag_dslash_repeat(_multi);
  * solvers, stag_apply_M and the force always act on D[U] (the solvers'
- * temporal_gauge parameter uses U' internally).  Errors: STAG_EINVAL. */
+ * temporal_gauge parameter uses U' internally).  Errors: STAG_EINVAL; the
+ * operator calls on U' return STAG_EUNSUPPORTED when the uploaded links are
+ * not unitary (max |U U^dagger - 1| above 1e-12, checked once per upload). */
 enum stag_links { STAG_LINKS_UPLOADED = 0, STAG_LINKS_TEMPORAL = 1, STAG_LINKS_TEMPORAL_FULL = 2 };
 int stag_set_operator_links(stag_ctx ctx, int links);
 
@@ -255,7 +257,9 @@ typedef struct {
                               g^dagger: the same spectrum and iteration; g is unitary, so the
                               same residual norm.  Needs unitary links (SU(3) or U(3)).  All
                               solvers: stag_cg_solve (either f64_arith), _mixed, _multi,
-                              _multishift, and the action.  0 (default): the links as uploaded. */
+                              _multishift, and the action; STAG_EUNSUPPORTED when the links are
+                              not unitary (max |U U^dagger - 1| above 1e-12).  0 (default): the
+                              links as uploaded. */
 } stag_solver_params;
 
 typedef struct {

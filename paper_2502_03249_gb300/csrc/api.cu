@@ -195,6 +195,7 @@ int stag_destroy(stag_ctx ctx)
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->tg_g) cudaFree(ctx->tg_g);
+    if (ctx->tg_defect) cudaFree(ctx->tg_defect);
     for (int s = 0; s < 8; ++s)
         if (ctx->tg_links[s]) cudaFree(ctx->tg_links[s]);
     if (ctx->tg_tmp) cudaFree(ctx->tg_tmp);

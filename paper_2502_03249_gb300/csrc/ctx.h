@@ -95,6 +95,7 @@ struct stag_ctx_s {
     double2* tg_tmp;           // temporal gauge: g b for a solve (nrhs_cap fields)
     int tg_tmp_fields;
     bool tg_stale;             // tg_g older than the last upload
+    unsigned long long* tg_defect;   // max |U U^dagger - 1| of the uploaded links (bits of a double)
     // reduction scratch: partial sums (one double per block) and arrival counters
     double* partials;
     unsigned int* counters;    // 64 counters, each used by one reduction site

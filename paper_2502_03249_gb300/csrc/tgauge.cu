@@ -5,6 +5,8 @@
 // F64/18 links once per gauge upload, on first use; the reduced-precision
 // and double-float copies are derived from the double U' like the untransformed
 // copies are from U.
+#include <string.h>
+
 #include "ctx.h"
 
 namespace stag {
@@ -169,8 +171,34 @@ __global__ void k_tg_apply(int Vh, int nfield, const double2* __restrict__ G, co
     }
 }
 
+// The largest |(U U^dagger - 1)_ij| over all links (its bits, atomically
+// maximised: non-negative doubles order like their bit patterns); one thread
+// per link (par, mu, h).
+__global__ void k_tg_unitarity(int Vh, const double2* __restrict__ L, unsigned long long* out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * Vh) return;
+    const int pm = (int)(idx / Vh), h = (int)(idx - (long long)pm * Vh);
+    const Mat3<double> U = load_link64(L, Vh, pm >> 2, pm & 3, h);
+    const Mat3<double> W = mmd(U, U);
+    double d = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double re = W.m[k].re - ((k % 4 == 0) ? 1.0 : 0.0);
+        d = fmax(d, fmax(fabs(re), fabs(W.m[k].im)));
+    }
+    if (!(d <= 1e300)) d = 1e300;   // NaN or infinity: as far from unitary as it gets
+    atomicMax(out, (unsigned long long)__double_as_longlong(d));
+}
+
+// The temporal-gauge transform is a gauge transformation only for unitary
+// links (g U g^dagger with U'_t = 1 needs U_t U_t^dagger = 1): links further
+// than this from unitary are refused rather than solved wrongly.
+constexpr double TG_UNITARITY_TOL = 1e-12;
+
 // The gauge matrices g for the current gauge field, computed on first use
-// after an upload (kept at their address).
+// after an upload (kept at their address), after checking that the links
+// are unitary.
 int ensure_tg_gauge(stag_ctx ctx, const double2** G)
 {
     if (!ctx->have_gauge) {
@@ -179,6 +207,22 @@ int ensure_tg_gauge(stag_ctx ctx, const double2** G)
     }
     const Geom g = ctx->g;
     if (!ctx->tg_g || ctx->tg_stale) {
+        if (!ctx->tg_defect) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_defect, sizeof(unsigned long long)));
+        STAG_CUDA_TRY(cudaMemsetAsync(ctx->tg_defect, 0, sizeof(unsigned long long), ctx->stream));
+        const long long nl = 8LL * g.Vh;
+        k_tg_unitarity<<<(unsigned)((nl + 255) / 256), 256, 0, ctx->stream>>>(g.Vh, (const double2*)ctx->links[0],
+                                                                            ctx->tg_defect);
+        STAG_CUDA_TRY(cudaGetLastError());
+        unsigned long long bits = 0;
+        STAG_CUDA_TRY(cudaMemcpyAsync(&bits, ctx->tg_defect, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+        STAG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        double defect;
+        memcpy(&defect, &bits, sizeof(defect));
+        if (!(defect <= TG_UNITARITY_TOL)) {
+            set_error("temporal gauge needs unitary links: max |U U^dagger - 1| = %.3g (limit %.0e)", defect,
+                      TG_UNITARITY_TOL);
+            return STAG_EUNSUPPORTED;
+        }
         if (!ctx->tg_g) STAG_CUDA_TRY(cudaMalloc(&ctx->tg_g, (size_t)2 * g.Vh * 9 * sizeof(double2)));
         const long long Vs = (long long)g.L[0] * g.L[1] * g.L[2];
         k_tg_gauge<<<(unsigned)((Vs + 127) / 128), 128, 0, ctx->stream>>>(g, (const double2*)ctx->links[0],

@@ -132,6 +132,31 @@ def test_operator_links_argument_checked(stag):
     assert e.value.code == -1
 
 
+def test_non_unitary_links_are_refused(stag):
+    """g U g^dagger fixes the temporal gauge only for unitary links: general
+    complex links are refused (STAG_EUNSUPPORTED), not solved wrongly; the
+    links as uploaded still work, and a unitary re-upload is accepted."""
+    dims, mass = (4, 4, 4, 4), 0.3
+    U = li.random_links(dims, "gl3", seed=1671)
+    b = li.gaussian_half(dims, seed=1672)
+    ctx = make_ctx(stag, dims, U)
+    x = ctx.new_half()
+    with pytest.raises(stag.StagError) as e:
+        ctx.cg_solve(x, dev(b), mass, tol=1e-10, temporal_gauge=1)
+    assert e.value.code == -6
+    ctx.set_operator_links(stag.LINKS_TEMPORAL)
+    with pytest.raises(stag.StagError) as e:
+        ctx.dslash_eo(ctx.new_half(), dev(b))
+    assert e.value.code == -6
+    ctx.set_operator_links(stag.LINKS_UPLOADED)
+    ctx.dslash_eo(x, dev(b))
+    assert rel(host(x), orc.dslash_eo(dims, U, b)) <= 1e-12
+    Uh = li.random_links(dims, "haar", seed=1673)
+    ctx.upload_gauge(dev(Uh))
+    ctx.cg_solve(x, dev(b), mass, tol=1e-10, temporal_gauge=1)
+    assert orc.true_residual(dims, Uh, mass, host(x), b) <= 1e-10
+
+
 @pytest.mark.parametrize("dims,recipe,mass", [((4, 4, 4, 2), "haar", 0.2), ((10, 6, 4, 6), "haar", 0.1),
                                               ((6, 4, 2, 10), "smooth", 0.05), ((8, 8, 8, 8), "smooth", 0.3)])
 @pytest.mark.parametrize("arith", [3, 0])
