@@ -171,24 +171,27 @@ __global__ void k_tg_apply(int Vh, int nfield, const double2* __restrict__ G, co
     }
 }
 
-// The largest |(U U^dagger - 1)_ij| over all links (its bits, atomically
-// maximised: non-negative doubles order like their bit patterns); one thread
-// per link (par, mu, h).
+// The largest |(U U^dagger - 1)_ij| over all links (its bits, maximised over
+// the warp by shuffles and then atomically: non-negative doubles order like
+// their bit patterns); one thread per link (par, mu, h).
 __global__ void k_tg_unitarity(int Vh, const double2* __restrict__ L, unsigned long long* out)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 8LL * Vh) return;
-    const int pm = (int)(idx / Vh), h = (int)(idx - (long long)pm * Vh);
-    const Mat3<double> U = load_link64(L, Vh, pm >> 2, pm & 3, h);
-    const Mat3<double> W = mmd(U, U);
     double d = 0.0;
+    if (idx < 8LL * Vh) {
+        const int pm = (int)(idx / Vh), h = (int)(idx - (long long)pm * Vh);
+        const Mat3<double> U = load_link64(L, Vh, pm >> 2, pm & 3, h);
+        const Mat3<double> W = mmd(U, U);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const double re = W.m[k].re - ((k % 4 == 0) ? 1.0 : 0.0);
-        d = fmax(d, fmax(fabs(re), fabs(W.m[k].im)));
+        for (int k = 0; k < 9; ++k) {
+            const double re = W.m[k].re - ((k % 4 == 0) ? 1.0 : 0.0);
+            d = fmax(d, fmax(fabs(re), fabs(W.m[k].im)));
+        }
+        if (!(d <= 1e300)) d = 1e300;   // NaN or infinity: as far from unitary as it gets
     }
-    if (!(d <= 1e300)) d = 1e300;   // NaN or infinity: as far from unitary as it gets
-    atomicMax(out, (unsigned long long)__double_as_longlong(d));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if ((threadIdx.x & 31) == 0 && d > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(d));
 }
 
 // The temporal-gauge transform is a gauge transformation only for unitary
