@@ -39,6 +39,12 @@ def test_compulsory_bytes():
     assert bench.dslash_bytes_per_site(8, 18) == 1248
     assert bench.dslash_bytes_per_site(8, 12) == 864
     assert bench.dslash_bytes_per_site(4, 12) == 432
+    # temporal gauge (Sec. 4.3): 6 + 2/Lt links per site, spinors as before
+    assert bench.dslash_bytes_per_site_tg(8, 18, 12) == 984
+    assert bench.dslash_bytes_per_site_tg(4, 12, 12) == 344
+    assert bench.dslash_bytes_per_site_tg(2, 12, 12) + 8 == 180
+    # at Lt = 2 every site sits next to the boundary: 7 links per site on average
+    assert bench.dslash_bytes_per_site_tg(4, 12, 2) == 7 * 48 + 48
 
 
 def test_weak_scaling_value():
