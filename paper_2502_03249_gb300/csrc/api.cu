@@ -172,6 +172,10 @@ int stag_create(stag_ctx* out, const int dims[4], void* stream)
         if (cudaMalloc(&ctx->partials, sizeof(double) * (size_t)ctx->max_blocks * 2) != cudaSuccess) { rc = STAG_ENOMEM; break; }
         if (cudaMalloc(&ctx->counters, sizeof(unsigned) * 64) != cudaSuccess) { rc = STAG_ENOMEM; break; }
         if (cudaMemset(ctx->counters, 0, sizeof(unsigned) * 64) != cudaSuccess) { rc = STAG_ECUDA; break; }
+        const size_t ng = (size_t)ctx->max_blocks / RGROUP + 2;
+        if (cudaMalloc(&ctx->gsum_part, sizeof(double) * ng) != cudaSuccess) { rc = STAG_ENOMEM; break; }
+        if (cudaMalloc(&ctx->gsum_cnt, sizeof(unsigned) * ng) != cudaSuccess) { rc = STAG_ENOMEM; break; }
+        if (cudaMemset(ctx->gsum_cnt, 0, sizeof(unsigned) * ng) != cudaSuccess) { rc = STAG_ECUDA; break; }
         if (cudaMalloc(&ctx->tmp_odd, sizeof(double2) * 3 * (size_t)ctx->g.Vh) != cudaSuccess) { rc = STAG_ENOMEM; break; }
     } while (0);
     if (rc != STAG_OK) {
@@ -194,6 +198,8 @@ int stag_destroy(stag_ctx ctx)
         if (ctx->links[s]) cudaFree(ctx->links[s]);
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->counters) cudaFree(ctx->counters);
+    if (ctx->gsum_part) cudaFree(ctx->gsum_part);
+    if (ctx->gsum_cnt) cudaFree(ctx->gsum_cnt);
     if (ctx->tg_g) cudaFree(ctx->tg_g);
     if (ctx->tg_defect) cudaFree(ctx->tg_defect);
     for (int s = 0; s < 8; ++s)

@@ -180,7 +180,7 @@ struct F64PlanT {
         Workspace* ws = ctx->ws;
         STAG_VEC_SWITCH(cfg, (k_cg_update<SpinorF64, BS, SPT><<<vgrid(ctx->g.Vh, cfg), BS, 0, s>>>(
                                  ctx->g.Vh, SpinorF64{ws->x}, SpinorF64{ws->r}, SpinorF64{ws->p}, SpinorF64{ws->Ap},
-                                 sc, ctx->partials, ctx->counters, cond, use_cond)));
+                                 sc, ctx->partials, ctx->counters, grid_sum_of(ctx), cond, use_cond)));
         return STAG_OK;
     }
     static int launch_p(stag_ctx ctx, int cfg, cudaStream_t s, const CgScalars* sc)
@@ -200,7 +200,8 @@ struct F64PlanT {
         SpinorF64 p{ws->p}, Ap{ws->Ap}, t{ws->t};
         STAG_TRY(launch_hop(ctx, U, sh.hop, s, ws->sc));
         k_Mp_dot<LF, SpinorF64, SpinorF64, HOP_BS><<<nblk(g.Vh, HOP_BS), HOP_BS, 0, s>>>(g, U, t, p, Ap, ws->sc,
-                                                                                       ctx->partials, ctx->counters);
+                                                                                       ctx->partials, ctx->counters,
+                                                                                       grid_sum_of(ctx));
         STAG_TRY(launch_update(ctx, sh.upd, s, ws->sc, cond, use_cond));
         STAG_TRY(launch_p(ctx, sh.pk, s, ws->sc));
         STAG_CUDA_TRY(cudaGetLastError());
@@ -286,7 +287,7 @@ struct DFPlanT {
         Workspace* ws = ctx->ws;
         STAG_VEC_SWITCH(cfg, (k_dfcg_update<BS, SPT><<<vgrid(ctx->g.Vh, cfg), BS, 0, s>>>(
                                  ctx->g.Vh, v(ws->x), v(ws->r), v(ws->p), v(ws->Ap), sc, ctx->partials,
-                                 ctx->counters, cond, use_cond)));
+                                 ctx->counters, grid_sum_of(ctx), cond, use_cond)));
         return STAG_OK;
     }
     static int launch_p(stag_ctx ctx, int cfg, cudaStream_t s, const CgScalars* sc)
@@ -307,10 +308,12 @@ struct DFPlanT {
         STAG_TRY(launch_hop(ctx, U, sh.hop, s, ws->sc));
         if (ws->df_dir == 1)
             k_dfcg_Mp_dot<LF, HOP_BS, true><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->r), v(ws->p), v(ws->Ap),
-                                                                  ws->sc, ctx->partials, ctx->counters);
+                                                                  ws->sc, ctx->partials, ctx->counters,
+                                                                  grid_sum_of(ctx));
         else
             k_dfcg_Mp_dot<LF, HOP_BS, false><<<gh, HOP_BS, 0, s>>>(g, U, v(ws->t), v(ws->r), v(ws->p), v(ws->Ap),
-                                                                   ws->sc, ctx->partials, ctx->counters);
+                                                                   ws->sc, ctx->partials, ctx->counters,
+                                                                   grid_sum_of(ctx));
         STAG_TRY(launch_update(ctx, sh.upd, s, ws->sc, cond, use_cond));
         if (ws->df_dir != 1) STAG_TRY(launch_p(ctx, sh.pk, s, ws->sc));
         STAG_CUDA_TRY(cudaGetLastError());
@@ -588,11 +591,12 @@ int stag_cg_update_time(stag_ctx ctx, int f64_arith, int nrep, double* ms_per_la
         if (f64_arith == STAG_F64X)
             k_dfcg_update<BLAS_BS, 1><<<gb, BLAS_BS, 0, ctx->stream>>>(Vh, DFPlan::v(ws->x), DFPlan::v(ws->r),
                                                                    DFPlan::v(ws->p), DFPlan::v(ws->Ap), ws->sc,
-                                                                   ctx->partials, ctx->counters, 0, 0);
+                                                                   ctx->partials, ctx->counters,
+                                                                   grid_sum_of(ctx), 0, 0);
         else
             k_cg_update<SpinorF64, BLAS_BS, 1><<<gb, BLAS_BS, 0, ctx->stream>>>(
                 Vh, SpinorF64{ws->x}, SpinorF64{ws->r}, SpinorF64{ws->p}, SpinorF64{ws->Ap}, ws->sc, ctx->partials,
-                ctx->counters, 0, 0);
+                ctx->counters, grid_sum_of(ctx), 0, 0);
     };
     for (int k = 0; k < 2; ++k) launch();
     cudaEvent_t e0, e1;

@@ -106,10 +106,9 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksBS<LF, SpinorDF, BS>::value)) 
 template <class LF, int BS, bool DIR>
 __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfcg_Mp_dot(Geom g, LF U, SpinorDF t, SpinorDF r,
                                                                           SpinorDF p, SpinorDF Ap, CgScalars* sc,
-                                                                          double* part, unsigned* cnt)
+                                                                          double* part, unsigned* cnt, GridSum gs)
 {
     __shared__ double red[BS / 32];
-    __shared__ bool last;
     if (sc->done) return;
     const DF m2s = split_double(sc->m2 + sc->sigma);
     const int h = blockIdx.x * BS + threadIdx.x;
@@ -134,10 +133,9 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SpinorDF>::value)) k_dfc
     }
     const double bs = block_sum_df<BS>(d, red);
     if (threadIdx.x == 0) part[blockIdx.x] = bs;
-    if (!arrive_last(cnt, &last)) return;
-    const double pAp = sum_partials<BS>(part, gridDim.x, red);
+    double pAp;
+    if (!grid_sum_finish<BS>(part, gridDim.x, blockIdx.x, 1, gs, cnt, red, &pAp)) return;
     if (threadIdx.x == 0) {
-        *cnt = 0;
         sc->pAp = pAp;
         if (!(pAp > 0.0) || !isfinite(pAp)) {
             sc->status = STAG_BREAKDOWN;
@@ -180,11 +178,10 @@ __device__ __forceinline__ void chunk_partials_df(const DF* v, double* part, int
 // sets beta, the convergence flag and the graph loop's condition.
 template <int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_dfcg_update(int Vh, SpinorDF x, SpinorDF r, SpinorDF p, SpinorDF Ap,
-                                                    CgScalars* sc, double* part, unsigned* cnt,
+                                                    CgScalars* sc, double* part, unsigned* cnt, GridSum gs,
                                                     cudaGraphConditionalHandle cond, int use_cond)
 {
     __shared__ double red[BS / 32 * SPT];
-    __shared__ bool last;
     if (sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
         return;
@@ -212,10 +209,11 @@ __global__ void __launch_bounds__(BS) k_dfcg_update(int Vh, SpinorDF x, SpinorDF
     }
     const int nch = (Vh + RCHUNK - 1) / RCHUNK;
     chunk_partials_df<BS, SPT>(d, part, nch, red);
-    if (!arrive_last(cnt, &last)) return;
-    const double rr_new = sum_chunks<BS>(part, nch, red);
+    constexpr int NCH = BS * SPT / RCHUNK;
+    const int u0 = blockIdx.x * NCH;
+    double rr_new;
+    if (!grid_sum_finish<BS>(part, nch, u0, min(NCH, nch - u0), gs, cnt, red, &rr_new)) return;
     if (threadIdx.x == 0) {
-        *cnt = 0;
         sc->beta = rr_new / sc->rr;
         sc->rr = rr_new;
         sc->iter += 1;

@@ -54,10 +54,9 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksBS<LF, S, BS>::value)) k_hop_g
 // double-float view of double storage); the epilogue runs in S's arithmetic.
 template <class LF, class SD, class S, int BS>
 __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SD>::value)) k_Mp_dot(Geom g, LF U, SD t, S p, S Ap, CgScalars* sc,
-                                               double* part, unsigned* cnt)
+                                               double* part, unsigned* cnt, GridSum gs)
 {
     __shared__ double red[BS / 32];
-    __shared__ bool last;
     if (sc->done) return;
     typedef typename S::real real;
     const real m2s = (real)(sc->m2 + sc->sigma);
@@ -77,10 +76,9 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SD>::value)) k_Mp_dot(Ge
     }
     const double bs = block_sum<BS>(d, red);
     if (threadIdx.x == 0) part[blockIdx.x] = bs;
-    if (!arrive_last(cnt, &last)) return;
-    const double pAp = sum_partials<BS>(part, gridDim.x, red);
+    double pAp;
+    if (!grid_sum_finish<BS>(part, gridDim.x, blockIdx.x, 1, gs, cnt, red, &pAp)) return;
     if (threadIdx.x == 0) {
-        *cnt = 0;
         sc->pAp = pAp;
         if (!(pAp > 0.0) || !isfinite(pAp)) {
             sc->status = STAG_BREAKDOWN;
@@ -97,10 +95,10 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SD>::value)) k_Mp_dot(Ge
 // condition.
 template <class S, int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_cg_update(int Vh, S x, S r, S p, S Ap, CgScalars* sc, double* part,
-                                                  unsigned* cnt, cudaGraphConditionalHandle cond, int use_cond)
+                                                  unsigned* cnt, GridSum gs, cudaGraphConditionalHandle cond,
+                                                  int use_cond)
 {
     __shared__ double red[BS / 32 * SPT];
-    __shared__ bool last;
     if (sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
         return;
@@ -129,10 +127,11 @@ __global__ void __launch_bounds__(BS) k_cg_update(int Vh, S x, S r, S p, S Ap, C
     }
     const int nch = (Vh + RCHUNK - 1) / RCHUNK;
     chunk_partials<BS, SPT>(d, part, nch, red);
-    if (!arrive_last(cnt, &last)) return;
-    const double rr_new = sum_chunks<BS>(part, nch, red);
+    constexpr int NCH = BS * SPT / RCHUNK;
+    const int u0 = blockIdx.x * NCH;
+    double rr_new;
+    if (!grid_sum_finish<BS>(part, nch, u0, min(NCH, nch - u0), gs, cnt, red, &rr_new)) return;
     if (threadIdx.x == 0) {
-        *cnt = 0;
         sc->beta = rr_new / sc->rr;
         sc->rr = rr_new;
         sc->iter += 1;

@@ -785,6 +785,61 @@ __device__ __forceinline__ double sum_chunks(const double* part, int n, double* 
     return r;
 }
 
+// Two-level finish of a grid-wide sum over n unit partials part[0 .. n)
+// (128-site chunks or one per block), in a fixed order, without a long serial
+// tail.  Units form groups of RGROUP: the block that completes a group (an
+// atomic count of the units written) sums the group's partials with one
+// warp's butterfly into gpart[group] and resets the group's counter; the
+// block that completes the last group sums the group partials in the fixed
+// 128-lane pattern of sum_chunks.  Which block does a step does not change
+// the bits.  Replaces "the last block to arrive sums all n partials", whose
+// serial sum kept one SM busy for several microseconds after the others had
+// finished (48^3 x 12: 5184 partials).
+constexpr int RGROUP = 32;
+struct GridSum {
+    double* gpart;    // one partial per group
+    unsigned* gcnt;   // units arrived per group: zero between uses (reset by each group's finisher)
+};
+
+// Called by all threads of every block after the block wrote its units
+// part[u0 .. u0 + nu) (nu >= 1, all in one group: RGROUP is a multiple of
+// the units per block).  True in the one block that finishes the sum, with
+// the total in *total for every thread of that block; *cnt counts finished
+// groups and is reset there.
+template <int BS>
+__device__ __forceinline__ bool grid_sum_finish(const double* part, int n, int u0, int nu, GridSum gs,
+                                                unsigned* cnt, double* red, double* total)
+{
+    static_assert(BS >= 128, "the final sum uses 128 lanes");
+    __shared__ int gs_flag;
+    const int grp = u0 / RGROUP, ngroups = (n + RGROUP - 1) / RGROUP;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned gsz = (unsigned)min(RGROUP, n - grp * RGROUP);
+        const unsigned prev = atomicAdd(gs.gcnt + grp, (unsigned)nu);
+        gs_flag = (prev + (unsigned)nu == gsz) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!gs_flag) return false;
+    if (threadIdx.x < 32) {
+        const int j = grp * RGROUP + (int)threadIdx.x;
+        const double v = warp_sum(j < n ? __ldcg(part + j) : 0.0);
+        if (threadIdx.x == 0) {
+            gs.gpart[grp] = v;
+            gs.gcnt[grp] = 0;
+            __threadfence();
+            const unsigned prev = atomicAdd(cnt, 1u);
+            gs_flag = (prev == (unsigned)ngroups - 1) ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (!gs_flag) return false;
+    *total = sum_chunks<BS>(gs.gpart, ngroups, red);
+    if (threadIdx.x == 0) *cnt = 0;
+    return true;
+}
+
 // Launch shape of a vector kernel: block size and sites per thread, coded
 // (BS << 4) | SPT for the autotuner.
 constexpr int vcfg(int BS, int SPT) { return (BS << 4) | SPT; }

@@ -100,6 +100,10 @@ struct stag_ctx_s {
     double* partials;
     unsigned int* counters;    // 64 counters, each used by one reduction site
     int max_blocks;
+    // two-level grid sums (common.cuh GridSum): group partials and group
+    // arrival counters (zero between uses), max_blocks / 32 + 2 of each
+    double* gsum_part;
+    unsigned int* gsum_cnt;
     // temporaries of the operator entry points
     double2* tmp_odd;          // V/2 x 3 complex
     void* tmp_lo_in;           // reduced-precision conversions of an API input/output
@@ -186,6 +190,8 @@ int check_float_inner_links(stag_ctx ctx);
 // double-float links are scaled (links outside the double-float range).
 int resolve_f64_arith(stag_ctx ctx, int requested, int* out);
 int tg_apply(stag_ctx ctx, const double2* G, const double2* in, double2* out, int nfield, int dagger);
+inline GridSum grid_sum_of(stag_ctx ctx) { return GridSum{ctx->gsum_part, ctx->gsum_cnt}; }
+
 // The link copy (prec, recon) of a link-field choice: STAG_LINKS_UPLOADED the
 // uploaded field, STAG_LINKS_TEMPORAL(_FULL) its temporal-gauge transform;
 // *tg = 1 where the identity time links are to be skipped.

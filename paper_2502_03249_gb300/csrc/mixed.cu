@@ -80,11 +80,10 @@ __global__ void __launch_bounds__(BS) k_mixed_start(int Vh, const double2* b, do
 // decide whether a reliable update is due.
 template <class S, class SX, int BS, int SPT>
 __global__ void __launch_bounds__(BS) k_mixed_update(int Vh, SX x, S r, S p, S Ap, CgScalars* sc, double* part,
-                                                     unsigned* cnt, cudaGraphConditionalHandle wh,
+                                                     unsigned* cnt, GridSum gs, cudaGraphConditionalHandle wh,
                                                      cudaGraphConditionalHandle ih, int use_cond)
 {
     __shared__ double red[BS / 32 * SPT];
-    __shared__ bool last;
     if (sc->done) {
         // iterations launched after convergence (host-driven loop) must not
         // repeat the final reliable update
@@ -122,10 +121,11 @@ __global__ void __launch_bounds__(BS) k_mixed_update(int Vh, SX x, S r, S p, S A
     }
     const int nch = (Vh + RCHUNK - 1) / RCHUNK;
     chunk_partials<BS, SPT>(d, part, nch, red);
-    if (!arrive_last(cnt, &last)) return;
-    const double rr_new = sum_chunks<BS>(part, nch, red);
+    constexpr int NCH = BS * SPT / RCHUNK;
+    const int u0 = blockIdx.x * NCH;
+    double rr_new;
+    if (!grid_sum_finish<BS>(part, nch, u0, min(NCH, nch - u0), gs, cnt, red, &rr_new)) return;
     if (threadIdx.x == 0) {
-        *cnt = 0;
         sc->rr_prev = sc->rr;
         sc->beta = rr_new / sc->rr;
         sc->rr = rr_new;
@@ -254,8 +254,8 @@ struct MixedPlan {
         S p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap), r = m.template spinor<S>(m.r);
         SX x = m.template spinor<SX>(m.xlo);
         STAG_VEC_SWITCH(cfg, (k_mixed_update<S, SX, BS, SPT><<<nblk_m(g.Vh, BS * SPT), BS, 0, s>>>(
-                                 g.Vh, x, r, p, Ap, sc, ctx->partials, ctx->counters, lg ? lg->w : 0,
-                                 lg ? lg->i : 0, use_cond)));
+                                 g.Vh, x, r, p, Ap, sc, ctx->partials, ctx->counters, grid_sum_of(ctx),
+                                 lg ? lg->w : 0, lg ? lg->i : 0, use_cond)));
         return STAG_OK;
     }
     static int launch_p(stag_ctx ctx, MixedSlot& m, int cfg, cudaStream_t s, const CgScalars* sc)
@@ -293,7 +293,7 @@ struct MixedPlan {
         const CgShape& sh = m.shape[U.tg];
         STAG_TRY(launch_hop(ctx, m, U, sh.hop, s, m.sc));
         k_Mp_dot<LF, S, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, m.sc, ctx->partials,
-                                                                           ctx->counters);
+                                                                           ctx->counters, grid_sum_of(ctx));
         STAG_TRY(launch_update(ctx, m, sh.upd, s, m.sc, lg, use_cond));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;

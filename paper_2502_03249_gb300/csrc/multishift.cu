@@ -231,7 +231,8 @@ struct MsPlan {
         const S t = m.template spinor<S>(m.t), Ap = m.template spinor<S>(m.Ap), r = m.template spinor<S>(m.r);
         const int gh = (g.Vh + MS_BS - 1) / MS_BS, gb = (g.Vh + MS_BLAS - 1) / MS_BLAS;
         k_hop_guarded<LF, S, MS_BS><<<gh, MS_BS, 0, s>>>(g, 1, U, pb, t, m.sc);
-        k_Mp_dot<LF, S, S, MS_BS><<<gh, MS_BS, 0, s>>>(g, U, t, pb, Ap, m.sc, ctx->partials, ctx->counters + 2);
+        k_Mp_dot<LF, S, S, MS_BS><<<gh, MS_BS, 0, s>>>(g, U, t, pb, Ap, m.sc, ctx->partials, ctx->counters + 2,
+                                                       grid_sum_of(ctx));
         k_ms_update<S, MS_BLAS><<<gb, MS_BLAS, 0, s>>>(g.Vh, r, Ap, P, X, m.stride, m.sc, m.ms, ctx->partials,
                                                        ctx->counters + 2, lg ? lg->w : 0, use_cond);
         k_ms_p<S, MS_BLAS><<<gb, MS_BLAS, 0, s>>>(g.Vh, r, P, m.stride, m.sc, m.ms);
