@@ -160,6 +160,7 @@ int stag_create(stag_ctx* out, const int dims[4], void* stream)
     ctx->V = V;
     ctx->stream = (cudaStream_t)stream;
     ctx->prepared_prec = -1;
+    ctx->half_stage[0] = ctx->half_stage[1] = -1;
     int rc = STAG_OK;
     do {
         if (cudaGetDevice(&ctx->device) != cudaSuccess) { rc = STAG_ECUDA; break; }
@@ -358,6 +359,8 @@ int stag_dslash_repeat(stag_ctx ctx, int prec, int recon, int nrep)
         set_error("no gauge field uploaded");
         return STAG_ENOGAUGE;
     }
+    if (prec == STAG_F16 && recon == 12)
+        STAG_TRY(tune_half_stage(ctx, ctx->op_links, ctx->tmp_lo_out, ctx->tmp_lo_in));
     for (int k = 0; k < nrep; ++k)
         STAG_TRY(launch_dslash_internal(ctx, prec, recon, 0, ctx->tmp_lo_out, ctx->tmp_lo_in, ctx->stream,
                                         ctx->op_links));

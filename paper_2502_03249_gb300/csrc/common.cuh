@@ -329,6 +329,34 @@ __device__ __forceinline__ double2 ld_stream(const double2* p, unsigned long lon
         : "l"(p), "l"(pol));
     return v;
 }
+// Asynchronous copies from global to shared memory (cp.async): the data do
+// not pass through registers, so a thread can have all of its site's links
+// in flight at once.  A thread's copies complete in the groups it commits
+// and are visible to that thread once it has waited for them (wait_group N:
+// at most the N most recent groups still pending); the links take the same
+// L2 evict-first policy as the streaming loads.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, unsigned long long pol)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, unsigned long long pol)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(sa), "l"(gmem), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, unsigned long long pol)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <typename S, int RECON>
 struct LinkField {
     typedef typename StoreTraits<S>::real real;
@@ -382,6 +410,36 @@ template <int EB, int NE> struct LinkChunks {
             w[4 * NC] = ld_stream(reinterpret_cast<const unsigned int*>(rem) + h, pol);
         }
     }
+    // Staging in shared memory (LinkStage below): chunk j of the link goes to
+    // sq[j * stride], the remainder to sr[0] (a word of RB bytes).
+    static __device__ __forceinline__ void stage(const char* block, int Vh, int h, uint4* sq, void* sr, int stride,
+                                                 unsigned long long pol)
+    {
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+            cp_async16(sq + (size_t)j * stride, reinterpret_cast<const uint4*>(block + (size_t)j * 16 * Vh) + h, pol);
+        const char* rem = block + (size_t)NC * 16 * Vh;
+        if constexpr (RB == 8) cp_async8(sr, reinterpret_cast<const uint2*>(rem) + h, pol);
+        else if constexpr (RB == 4) cp_async4(sr, reinterpret_cast<const unsigned int*>(rem) + h, pol);
+    }
+    static __device__ __forceinline__ void unstage(const uint4* sq, const void* sr, int stride, uint32_t* w)
+    {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const uint4 q = sq[(size_t)j * stride];
+            w[4 * j] = q.x;
+            w[4 * j + 1] = q.y;
+            w[4 * j + 2] = q.z;
+            w[4 * j + 3] = q.w;
+        }
+        if constexpr (RB == 8) {
+            const uint2 q = *reinterpret_cast<const uint2*>(sr);
+            w[4 * NC] = q.x;
+            w[4 * NC + 1] = q.y;
+        } else if constexpr (RB == 4) {
+            w[4 * NC] = *reinterpret_cast<const unsigned int*>(sr);
+        }
+    }
     static __device__ __forceinline__ void store(char* block, int Vh, int h, const uint32_t* w)
     {
 #pragma unroll
@@ -424,10 +482,12 @@ struct LinkField<__half2, RECON> {
     const __half2* base;
     int Vh;
     int tg = 0;
-    __device__ __forceinline__ Mat3<float> load(int par, int mu, int h) const
+    __device__ __forceinline__ const char* block(int par, int mu) const
     {
-        uint32_t w[C::WORDS];
-        C::load(reinterpret_cast<const char*>(base) + (size_t)(par * 4 + mu) * C::BYTES * Vh, Vh, h, w);
+        return reinterpret_cast<const char*>(base) + (size_t)(par * 4 + mu) * C::BYTES * Vh;
+    }
+    static __device__ __forceinline__ Mat3<float> decode(const uint32_t* w)
+    {
         Mat3<float> U;
 #pragma unroll
         for (int k = 0; k < NE; ++k) {
@@ -436,6 +496,41 @@ struct LinkField<__half2, RECON> {
         }
         if (RECON == 12) reconstruct_row2(U);
         return U;
+    }
+    __device__ __forceinline__ Mat3<float> load(int par, int mu, int h) const
+    {
+        uint32_t w[C::WORDS];
+        C::load(block(par, mu), Vh, h, w);
+        return decode(w);
+    }
+};
+
+// Shared-memory staging of the 8 links of one output site per thread
+// (dslash_site_staged): for a block of BS threads, chunk j of hop k (0..7) of
+// thread i at q[(k NC + j) BS + i], its remainder word at r[k BS + i] with r
+// after the 8 NC BS chunks; a warp reading one slot reads contiguous words.
+// Built for half 12-real links (24 bytes per link, 192 bytes per thread).
+template <class LF> struct LinkStage { static constexpr bool value = false; };
+template <> struct LinkStage<LinkField<__half2, 12>> {
+    static constexpr bool value = true;
+    typedef LinkField<__half2, 12>::C C;
+    // uint4 words of shared memory for a block of BS threads
+    static constexpr int words(int BS) { return 8 * C::NC * BS + (C::RB ? (8 * BS * C::RB + 15) / 16 : 0); }
+    static __device__ __forceinline__ uint4* chunks(uint4* st, int BS, int k) { return st + (size_t)k * C::NC * BS + threadIdx.x; }
+    static __device__ __forceinline__ void* rem(uint4* st, int BS, int k)
+    {
+        return reinterpret_cast<char*>(st + 8 * C::NC * BS) + ((size_t)k * BS + threadIdx.x) * C::RB;
+    }
+    static __device__ __forceinline__ void issue(const LinkField<__half2, 12>& U, int par, int mu, int h, uint4* st,
+                                                 int BS, int k, unsigned long long pol)
+    {
+        C::stage(U.block(par, mu), U.Vh, h, chunks(st, BS, k), rem(st, BS, k), BS, pol);
+    }
+    static __device__ __forceinline__ Mat3<float> get(uint4* st, int BS, int k)
+    {
+        uint32_t w[C::WORDS];
+        C::unstage(chunks(st, BS, k), rem(st, BS, k), BS, w);
+        return LinkField<__half2, 12>::decode(w);
     }
 };
 

@@ -130,6 +130,8 @@ struct stag_ctx_s {
     void* dfx_tmp;             // double-float operator on canonical fields: input and output storage
     size_t dfx_tmp_bytes;
     int op_links;              // link field of the operator entry points (stag_set_operator_links)
+    int half_stage[2];         // half 12-real operator entry points, links as uploaded / temporal gauge:
+                               // 1 links staged in shared memory, 0 not, -1 not decided (unstaged)
 };
 
 namespace stag {
@@ -160,6 +162,10 @@ int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* 
                           int nb, int* nb_used, int links = STAG_LINKS_UPLOADED);
 int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int links,
                           int nb, int* nb_used, cudaStream_t s);
+// dslash.cu: the staging decision of the half 12-real operator for a link
+// field (ctx->half_stage), timed once on in/out (outputs overwritten).  Only
+// outside stream capture.
+int tune_half_stage(stag_ctx ctx, int links, void* out, const void* in);
 // tgauge.cu: the temporal-gauge matrices g and the links U' = g U g^dagger
 // (dslash.cuh, TGLinks) in the storage of (prec, recon), built on first use
 // after an upload; g b and g^dagger x for nfield even-site fields.

@@ -3,24 +3,41 @@
 #include "ctx.h"
 #include "df64.cuh"
 #include "dslash.cuh"
+#include "tune.h"
 
 namespace stag {
 
-template <class LF, class SIn, class SOut, int BS>
+template <class LF, class SIn, class SOut, int BS, bool STG>
 __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SIn>::value)) k_dslash(Geom g, int p, LF U, SIn in, SOut out)
 {
     const int h = blockIdx.x * BS + threadIdx.x;
     if (h >= g.Vh) return;
-    out.store(h, dslash_site(g, p, h, U, in));
+    if constexpr (STG) {
+        __shared__ uint4 st[StageWords<LF, BS, STG>::value];
+        out.store(h, dslash_site_staged<BS>(g, p, h, U, in, st));
+    } else {
+        out.store(h, dslash_site(g, p, h, U, in));
+    }
 }
 
+// Half 12-real links are staged in shared memory (dslash_site_staged) where
+// the context's decision says so: the autotuner's choice, timed by
+// stag_dslash_repeat (an operator entry point outside stream capture) and
+// otherwise the unstaged kernel until a decision exists.
 template <class LF, class SIn, class SOut>
 static int run_dslash(stag_ctx ctx, const LF& U, const SIn& in, const SOut& out, int p,
-                      cudaStream_t s)
+                      cudaStream_t s, bool stg = false)
 {
     constexpr int BS = 128;
     const int grid = (ctx->g.Vh + BS - 1) / BS;
-    k_dslash<LF, SIn, SOut, BS><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
+    if constexpr (LinkStage<LF>::value) {
+        if (stg) {
+            k_dslash<LF, SIn, SOut, BS, true><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
+            STAG_CUDA_TRY(cudaGetLastError());
+            return STAG_OK;
+        }
+    }
+    k_dslash<LF, SIn, SOut, BS, false><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
     STAG_CUDA_TRY(cudaGetLastError());
     return STAG_OK;
 }
@@ -47,10 +64,27 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
     if (prec == STAG_F16) {
         SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
         if (recon == 18) return run_dslash(ctx, LinkField<__half2, 18>{(const __half2*)lk, Vh, tg}, si, so, par_out, s);
-        return run_dslash(ctx, LinkField<__half2, 12>{(const __half2*)lk, Vh, tg}, si, so, par_out, s);
+        return run_dslash(ctx, LinkField<__half2, 12>{(const __half2*)lk, Vh, tg}, si, so, par_out, s,
+                          ctx->half_stage[tg] == 1);
     }
     set_error("unsupported precision %d", prec);
     return STAG_EUNSUPPORTED;
+}
+
+int tune_half_stage(stag_ctx ctx, int links, void* out, const void* in)
+{
+    const void* lk = nullptr;
+    int tg = 0;
+    STAG_TRY(op_links_for(ctx, links, STAG_F16, 12, &lk, &tg));
+    if (ctx->half_stage[tg] >= 0) return STAG_OK;
+    const int Vh = ctx->g.Vh;
+    const LinkField<__half2, 12> U{(const __half2*)lk, Vh, tg};
+    const SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
+    int choice = 0;
+    STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "dslash_stage_tg" : "dslash_stage", STAG_F16, 12, 1), {0, 1},
+                         &choice, [&](int c) { return run_dslash(ctx, U, si, so, 0, ctx->stream, c == 1); }));
+    ctx->half_stage[tg] = choice;
+    return STAG_OK;
 }
 
 // Scratch of the double-float operator on canonical fields: nfield input and

@@ -43,6 +43,78 @@ __device__ __forceinline__ Vec3<typename LF::real> dslash_site(const Geom& g, in
     return acc;
 }
 
+// dslash_site with the site's links staged in shared memory first (LinkStage;
+// st holds LinkStage<LF>::words(BS) words for a block of BS threads): every
+// link copy of the site is issued before the first product, one copy group
+// per direction, and direction mu waits only for its own group.  The hop
+// matrices and the arithmetic are those of dslash_site, so the result is the
+// same bit for bit; what changes is the depth of the link stream (192 bytes
+// in flight per thread for half 12-real links instead of the few links the
+// registers of an unstaged thread hold).
+template <int N>
+__device__ __forceinline__ void cp_async_wait_dir(int mu)
+{
+    if (mu == 0) cp_async_wait<N - 1>();
+    else if (mu == 1) cp_async_wait<(N > 2 ? N - 2 : 0)>();
+    else if (mu == 2) cp_async_wait<(N > 3 ? N - 3 : 0)>();
+    else cp_async_wait<0>();
+}
+
+template <int BS, class LF, class SIn>
+__device__ __forceinline__ Vec3<typename LF::real> dslash_site_staged(const Geom& g, int p, int h, const LF& U,
+                                                                      const SIn& in, uint4* st)
+{
+    static_assert(LinkStage<LF>::value, "no shared-memory staging for this link field");
+    typedef typename LF::real real;
+    typedef LinkStage<LF> LS;
+    SiteNbrs s;
+    site_nbrs(g, p, h, s);
+    const unsigned long long pol = l2_evict_first_policy();
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        if (!(mu == 3 && unit_fwd_time(U, s))) LS::issue(U, p, mu, h, st, BS, 2 * mu, pol);
+        if (!(mu == 3 && unit_bwd_time(U, s))) LS::issue(U, 1 - p, mu, s.bwd[mu], st, BS, 2 * mu + 1, pol);
+        cp_async_commit();
+    }
+    Vec3<real> acc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = real(0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        cp_async_wait_dir<4>(mu);
+        if (mu == 3 && unit_fwd_time(U, s)) {
+            hop_add(acc, load_flipped(in, s.fwd[mu], s.sf[mu]));
+        } else {
+            const Mat3<real> Uf = LS::get(st, BS, 2 * mu);
+            const Vec3<real> vf = load_flipped(in, s.fwd[mu], s.sf[mu]);
+            mv_acc(acc, Uf, vf);
+        }
+        if (mu == 3 && unit_bwd_time(U, s)) {
+            hop_add(acc, load_flipped(in, s.bwd[mu], s.sb[mu]));
+        } else {
+            const Mat3<real> Ub = LS::get(st, BS, 2 * mu + 1);
+            const Vec3<real> vb = load_flipped(in, s.bwd[mu], s.sb[mu]);
+            mdv_acc(acc, Ub, vb);
+        }
+    }
+    return acc;
+}
+
+// The operator at site h through dslash_site_staged when STG is set (the
+// caller's kernel declares the staging words), through dslash_site otherwise.
+template <int BS, bool STG, class LF, class SIn>
+__device__ __forceinline__ Vec3<typename LF::real> dslash_site_sel(const Geom& g, int p, int h, const LF& U,
+                                                                   const SIn& in, uint4* st)
+{
+    if constexpr (STG) return dslash_site_staged<BS>(g, p, h, U, in, st);
+    else return dslash_site(g, p, h, U, in);
+}
+
+// Shared-memory words a kernel of BS threads declares for staging (one
+// unused word when it does not stage).
+template <class LF, int BS, bool STG> struct StageWords { static constexpr int value = 1; };
+template <class LF, int BS> struct StageWords<LF, BS, true> { static constexpr int value = LinkStage<LF>::words(BS); };
+
 // Minimum resident blocks (of 128 threads) requested from the compiler for an
 // operator kernel on link field LF: 1 (no bound) by default; double-float
 // links cap registers at 96 (5 blocks), float links at 72 (7) and half links

@@ -244,7 +244,29 @@ struct MixedPlan {
     {
         const Geom g = ctx->g;
         S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p);
+        if constexpr (LinkStage<LF>::value) {
+            if (bs & HOP_STAGED) {
+                STAG_HOP_SWITCH(bs & ~HOP_STAGED,
+                                (k_hop_guarded<LF, S, BS, true><<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
+                return STAG_OK;
+            }
+        }
         STAG_HOP_SWITCH(bs, (k_hop_guarded<LF, S, BS><<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
+        return STAG_OK;
+    }
+    static int launch_mpdot(stag_ctx ctx, MixedSlot& m, const LF& U, int stage, cudaStream_t s, CgScalars* sc)
+    {
+        const Geom g = ctx->g;
+        S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap);
+        if constexpr (LinkStage<LF>::value) {
+            if (stage) {
+                k_Mp_dot<LF, S, S, MHOP_BS, true><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(
+                    g, U, t, p, Ap, sc, ctx->partials, ctx->counters, grid_sum_of(ctx));
+                return STAG_OK;
+            }
+        }
+        k_Mp_dot<LF, S, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, sc, ctx->partials,
+                                                                           ctx->counters, grid_sum_of(ctx));
         return STAG_OK;
     }
     static int launch_update(stag_ctx ctx, MixedSlot& m, int cfg, cudaStream_t s, CgScalars* sc, LoopGraph* lg,
@@ -274,9 +296,27 @@ struct MixedPlan {
         k_mixed_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
         STAG_CUDA_TRY(cudaGetLastError());
         CgShape sh;
-        STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "mixed_hop_tg" : "mixed_hop", prec, recon, 1), {128, 64, 256},
-                             &sh.hop,
+        // block sizes, and for half 12-real links the same with the links
+        // staged in shared memory (64 and 128 threads: 12 and 24 KB a block)
+        std::vector<int> hc = {128, 64, 256};
+        if (LinkStage<LF>::value) {
+            hc.push_back(128 | HOP_STAGED);
+            hc.push_back(64 | HOP_STAGED);
+        }
+        STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "mixed_hop_tg" : "mixed_hop", prec, recon, 1), hc, &sh.hop,
                              [&](int c) { return launch_hop(ctx, m, U, c, ctx->stream, tsc); }));
+        if (LinkStage<LF>::value) {
+            // Mp_dot writes the record (on vectors that are not yet a solve's,
+            // pAp may read as a breakdown): it is reset before every launch
+            // and after the last
+            STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "mixed_mpdot_stage_tg" : "mixed_mpdot_stage", prec, recon, 1),
+                                 {0, 1}, &sh.mpdot_stage, [&](int c) {
+                                     k_mixed_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
+                                     return launch_mpdot(ctx, m, U, c, ctx->stream, tsc);
+                                 }));
+            k_mixed_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
+            STAG_CUDA_TRY(cudaGetLastError());
+        }
         const std::vector<int> vc = {vcfg(256, 1), vcfg(128, 1), vcfg(256, 2), vcfg(128, 2)};
         STAG_TRY(tune_choice(ctx, tune_key(ctx, "mixed_update", prec, recon, 1), vc, &sh.upd,
                              [&](int c) { return launch_update(ctx, m, c, ctx->stream, tsc, nullptr, 0); }));
@@ -292,8 +332,7 @@ struct MixedPlan {
         S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap);
         const CgShape& sh = m.shape[U.tg];
         STAG_TRY(launch_hop(ctx, m, U, sh.hop, s, m.sc));
-        k_Mp_dot<LF, S, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, m.sc, ctx->partials,
-                                                                           ctx->counters, grid_sum_of(ctx));
+        STAG_TRY(launch_mpdot(ctx, m, U, sh.mpdot_stage, s, m.sc));
         STAG_TRY(launch_update(ctx, m, sh.upd, s, m.sc, lg, use_cond));
         STAG_CUDA_TRY(cudaGetLastError());
         return STAG_OK;

@@ -12,7 +12,12 @@ struct CgShape {
     int hop = 128;                 // hop kernel block size
     int upd = vcfg(256, 1);        // update kernel (vcfg: block size, sites per thread)
     int pk = vcfg(256, 1);         // direction update kernel
+    int mpdot_stage = 0;           // Mp_dot with its links staged in shared memory (half 12-real)
 };
+
+// A hop-kernel block size with HOP_STAGED set: the links staged in shared
+// memory (dslash_site_staged).
+constexpr int HOP_STAGED = 1 << 12;
 
 // Buffers of one mixed-precision configuration (inner precision x compression).
 struct MixedSlot {

@@ -114,3 +114,63 @@ def test_mixed_solver_launch_shapes_identical(stag, fresh_tuner, prec):
         if ref is None:
             ref = got
         assert got[:2] == ref[:2] and np.array_equal(got[2], ref[2]), (hop, upd, pk)
+
+
+STAGED = 1 << 12   # hop block size with the links staged in shared memory
+
+
+def test_mixed_half_staged_links_identical(stag, fresh_tuner):
+    """Half 12-real inner iteration with its links staged in shared memory
+    (cp.async, the hop and Mp_dot kernels) against the unstaged kernels: the
+    same iterations, reliable updates and solution bits, as uploaded and in
+    temporal gauge (ragged lattice: V/2 = 720)."""
+    import torch
+    dims, mass = (10, 6, 4, 6), 0.1
+    U = li.random_links(dims, "smooth", eps=0.3, seed=631)
+    b = li.gaussian_half(dims, seed=632)
+    gpu = torch.cuda.get_device_name()
+    for tg in (0, 1):
+        ref = None
+        for hop, mp in [(128, 0), (128 | STAGED, 1), (64 | STAGED, 0), (64, 1)]:
+            fresh_tuner.clear()
+            sfx = "_tg" if tg else ""
+            for k, c in (("mixed_hop" + sfx, hop), ("mixed_mpdot_stage" + sfx, mp), ("mixed_update", VEC[0]),
+                         ("mixed_p", VEC[0])):
+                fresh_tuner.insert(fresh_tuner.make_key(k, dims, 2, 12, 1, gpu), c)
+            ctx = stag.Context(dims)
+            ctx.upload_gauge(dev(U))
+            x = ctx.new_half()
+            st = ctx.cg_solve_mixed(x, dev(b), mass, tol=1e-10, inner_prec=2, inner_recon=12, temporal_gauge=tg)
+            got = (st["iters"], st["reliable_updates"], x.cpu().numpy())
+            ctx.close()
+            if ref is None:
+                ref = got
+            assert got[:2] == ref[:2] and np.array_equal(got[2], ref[2]), (tg, hop, mp)
+
+
+@pytest.mark.parametrize("dims", [(10, 6, 4, 6), (6, 4, 2, 10), (16, 16, 16, 16)])
+def test_half_operator_staged_links_identical(stag, fresh_tuner, dims):
+    """stag_dslash_repeat on half 12-real storage with the links staged in
+    shared memory equals the unstaged kernel bit for bit, as uploaded and in
+    temporal gauge (identity time links skipped)."""
+    import torch
+    U = li.random_links(dims, "haar", seed=641)
+    psi = li.gaussian_half(dims, seed=642)
+    gpu = torch.cuda.get_device_name()
+    for links in (stag.LINKS_UPLOADED, stag.LINKS_TEMPORAL):
+        outs = []
+        for choice in (0, 1):
+            fresh_tuner.clear()
+            key = "dslash_stage_tg" if links == stag.LINKS_TEMPORAL else "dslash_stage"
+            fresh_tuner.insert(fresh_tuner.make_key(key, dims, 2, 12, 1, gpu), choice)
+            ctx = stag.Context(dims)
+            ctx.upload_gauge(dev(U))
+            ctx.set_operator_links(links)
+            ctx.dslash_prepare(dev(psi), stag.F16)
+            ctx.dslash_repeat(stag.F16, 12, 2)
+            out = ctx.new_half()
+            ctx.dslash_result(out)
+            outs.append(out.cpu().numpy())
+            ctx.close()
+        assert np.array_equal(outs[0], outs[1]), links
+        assert np.isfinite(outs[0]).all() and np.abs(outs[0]).max() > 0
