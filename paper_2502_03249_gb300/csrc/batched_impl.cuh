@@ -93,6 +93,16 @@ __device__ __forceinline__ unsigned mask_updating(const BatchScal& b, int k0)
     return m;
 }
 
+// mask_active of the n <= 32 systems kb ... kb + n - 1 with one load per
+// lane and a ballot (every warp of a block forms the same mask; all lanes of
+// the warp must call it).
+__device__ __forceinline__ unsigned mask_active_ballot(const BatchScal& b, int kb, int n)
+{
+    const int lane = threadIdx.x & 31;
+    const bool a = lane < n && kb + lane < b.nrhs && active(b.sc[kb + lane]);
+    return __ballot_sync(0xffffffffu, a);
+}
+
 // ------------------------------------------------------------- start
 
 // x_hi = x0 (or 0), xlo = 0, rr0 = |b|^2 per system; every system marked for a
@@ -247,10 +257,11 @@ __global__ void __launch_bounds__(32 * TileSW<G>::value * G, TileMinBlocks<32 * 
     __shared__ uint4 sm[TileSmem<LF, G>::value / 16];
     constexpr int SW = TileSW<G>::value, TS = 32 * SW;
     const int kb = blockIdx.y * G * NBT;
-    if (!mask_active<G * NBT>(bs, kb)) return;   // uniform over the block
+    const unsigned bmask = mask_active_ballot(bs, kb, G * NBT);
+    if (!bmask) return;   // uniform over the block
     const int h = blockIdx.x * TS + threadIdx.x % TS;
     const int k0 = kb + (threadIdx.x / TS) * NBT;
-    const unsigned mask = mask_active<NBT>(bs, k0);
+    const unsigned mask = (bmask >> ((threadIdx.x / TS) * NBT)) & ((1u << NBT) - 1u);
     SiteNbrs s;
     site_nbrs(g, 1, h < g.Vh ? h : g.Vh - 1, s);
     Vec3<typename LF::real> acc[NBT];
@@ -277,7 +288,7 @@ __global__ void __launch_bounds__(32 * TileSW<G>::value * G, TileMinBlocks<32 * 
     __shared__ double wsum[NW * NBT];
     typedef typename S::real real;
     const int kb = blockIdx.y * G * NBT;
-    const unsigned bmask = mask_active<G * NBT>(bs, kb);
+    const unsigned bmask = mask_active_ballot(bs, kb, G * NBT);
     if (!bmask) return;   // uniform over the block
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = blockIdx.x * TS + threadIdx.x % TS;
@@ -306,10 +317,16 @@ __global__ void __launch_bounds__(32 * TileSW<G>::value * G, TileMinBlocks<32 * 
             d[k] = site_dot(pv, a);
         }
     }
+    if constexpr (std::is_same<real, float>::value && (NBT & (NBT - 1)) == 0) {
+        const double x = warp_sum_n<NBT>(d);
+        const int k = lane / (32 / NBT);
+        if (lane == warp_sum_n_lane<NBT>(k)) wsum[w * NBT + k] = x;
+    } else {
 #pragma unroll
-    for (int k = 0; k < NBT; ++k) {
-        const double x = warp_sum(d[k]);
-        if (lane == 0) wsum[w * NBT + k] = x;
+        for (int k = 0; k < NBT; ++k) {
+            const double x = warp_sum(d[k]);
+            if (lane == 0) wsum[w * NBT + k] = x;
+        }
     }
     __syncthreads();
     if (threadIdx.x < G * NBT && (bmask & (1u << threadIdx.x))) {

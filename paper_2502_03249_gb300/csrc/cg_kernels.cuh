@@ -41,17 +41,17 @@ template <class LF, class S, int BS> struct OpMinBlocksBS {
     static constexpr int value = v > 0 ? v : 1;
 };
 
-// STG: the links staged in shared memory (dslash_site_staged; half 12-real
-// links only), the same result bit for bit.
-template <class LF, class S, int BS, bool STG = false>
+// MODE: links and/or neighbour spinors staged in shared memory
+// (dslash_site_staged, STAGE_LINKS | STAGE_SPINORS), the same result bit for bit.
+template <class LF, class S, int BS, int MODE = 0>
 __global__ void __launch_bounds__(BS, (OpMinBlocksBS<LF, S, BS>::value)) k_hop_guarded(Geom g, int p, LF U, S in, S out, const CgScalars* sc)
 {
     if (sc->done) return;
     const int h = blockIdx.x * BS + threadIdx.x;
     if (h >= g.Vh) return;
-    if constexpr (STG) {
-        __shared__ uint4 st[StageWords<LF, BS, STG>::value];
-        out.store(h, dslash_site_staged<BS>(g, p, h, U, in, st));
+    if constexpr (MODE != 0) {
+        __shared__ uint4 st[StageWords<LF, S, BS, MODE>::value];
+        out.store(h, dslash_site_staged<BS, MODE>(g, p, h, U, in, st));
     } else {
         out.store(h, dslash_site(g, p, h, U, in));
     }
@@ -59,19 +59,19 @@ __global__ void __launch_bounds__(BS, (OpMinBlocksBS<LF, S, BS>::value)) k_hop_g
 
 // SD is the storage view the operator reads t through (S itself, or a
 // double-float view of double storage); the epilogue runs in S's arithmetic.
-template <class LF, class SD, class S, int BS, bool STG = false>
+template <class LF, class SD, class S, int BS, int MODE = 0>
 __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SD>::value)) k_Mp_dot(Geom g, LF U, SD t, S p, S Ap, CgScalars* sc,
                                                double* part, unsigned* cnt, GridSum gs)
 {
     __shared__ double red[BS / 32];
-    __shared__ uint4 st[StageWords<LF, BS, STG>::value];
+    __shared__ uint4 st[StageWords<LF, SD, BS, MODE>::value];
     if (sc->done) return;
     typedef typename S::real real;
     const real m2s = (real)(sc->m2 + sc->sigma);
     const int h = blockIdx.x * BS + threadIdx.x;
     real d = real(0);
     if (h < g.Vh) {
-        const Vec3<real> Dt = vconv<real>(dslash_site_sel<BS, STG>(g, 0, h, U, t, st));
+        const Vec3<real> Dt = vconv<real>(dslash_site_sel<BS, MODE>(g, 0, h, U, t, st));
         const Vec3<real> pv = p.load(h);
         Vec3<real> a;
 #pragma unroll

@@ -353,6 +353,18 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem, unsigned
     asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "l"(pol)
                  : "memory");
 }
+// spinor copies: default L2 policy (the vectors stay L2-resident), L1 allocated
+// (neighbouring sites of a block share lines)
+__device__ __forceinline__ void cp_async16_ca(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8_ca(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -657,6 +669,53 @@ struct SpinorF16 {
             w[c] = *reinterpret_cast<const unsigned int*>(&q);
         }
         p[h] = make_uint4(w[0], w[1], w[2], __float_as_uint(n));
+    }
+};
+
+// Neighbour spinors copied to shared memory ahead of their use (cp.async):
+// a slot is one 16-byte word (a) plus, for float storage, one 8-byte word (b);
+// get returns what the storage's load returns, get_flipped what load_flipped
+// returns, from the same bytes.
+template <class S> struct SpinorStage { static constexpr bool value = false; };
+template <> struct SpinorStage<SpinorF32> {
+    static constexpr bool value = true;
+    static constexpr bool TWO = true;   // a second (8-byte) word per slot
+    static __device__ __forceinline__ void issue(const SpinorF32& in, int h, uint4* a, uint2* b)
+    {
+        cp_async16_ca(a, in.pa() + h);
+        cp_async8_ca(b, in.pb() + h);
+    }
+    static __device__ __forceinline__ Vec3<float> get(const SpinorF32& in, const uint4* a, const uint2* b)
+    {
+        const uint4 q = *a;
+        const uint2 r = *b;
+        return in.unpack(make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z),
+                                     __uint_as_float(q.w)),
+                         make_float2(__uint_as_float(r.x), __uint_as_float(r.y)));
+    }
+    static __device__ __forceinline__ Vec3<float> get_flipped(const SpinorF32& in, const uint4* a, const uint2* b,
+                                                              uint32_t sbit)
+    {
+        return vflip(get(in, a, b), sbit);
+    }
+};
+template <> struct SpinorStage<SpinorF16> {
+    static constexpr bool value = true;
+    static constexpr bool TWO = false;
+    static __device__ __forceinline__ void issue(const SpinorF16& in, int h, uint4* a, uint2*)
+    {
+        cp_async16_ca(a, in.p + h);
+    }
+    static __device__ __forceinline__ Vec3<float> get(const SpinorF16& in, const uint4* a, const uint2*)
+    {
+        return in.unpack(*a);
+    }
+    static __device__ __forceinline__ Vec3<float> get_flipped(const SpinorF16& in, const uint4* a, const uint2*,
+                                                              uint32_t sbit)
+    {
+        uint4 q = *a;
+        q.w ^= sbit;
+        return in.unpack(q);
     }
 };
 

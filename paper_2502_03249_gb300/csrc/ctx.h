@@ -131,7 +131,7 @@ struct stag_ctx_s {
     size_t dfx_tmp_bytes;
     int op_links;              // link field of the operator entry points (stag_set_operator_links)
     int half_stage[2];         // half 12-real operator entry points, links as uploaded / temporal gauge:
-                               // 1 links staged in shared memory, 0 not, -1 not decided (unstaged)
+                               // STAGE_* bits of what is staged in shared memory, -1 not decided (unstaged)
 };
 
 namespace stag {

@@ -332,6 +332,44 @@ __device__ __forceinline__ double warp_sum(float v)
     return df_to_double_scaled(x, 0);
 }
 
+// Warp sums of N float values per lane (N a power of two, at most 32), each
+// equal bit for bit to warp_sum of that value, for about the cost of one:
+// the first log2 N levels of the butterfly are transposed -- at the level of
+// offset o a lane keeps the half of its values that its lane bit o selects
+// and adds the partner's copies of them -- so every level pairs the same
+// lanes as warp_sum and df_add is commutative bit for bit (its TwoSum error
+// is exact in either order).  Value k ends in the lanes k (32 / N) ...
+// (k + 1) (32 / N) - 1; warp_sum_n_lane(k) names the first of them.
+template <int N>
+__device__ __forceinline__ double warp_sum_n(const float* v)
+{
+    static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "N a power of two <= 32");
+    const int lane = threadIdx.x & 31;
+    DF x[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = DF(v[i], 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int m = (N * o) / 16;   // values a lane holds before this level
+        if (m > 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < m / 2; ++i) {
+                const DF keep = up ? x[i + m / 2] : x[i];
+                const DF send = up ? x[i] : x[i + m / 2];
+                const DF recv(__shfl_xor_sync(0xffffffffu, send.hi, o), __shfl_xor_sync(0xffffffffu, send.lo, o));
+                x[i] = df_add(keep, recv);
+            }
+        } else {
+            const DF y(__shfl_xor_sync(0xffffffffu, x[0].hi, o), __shfl_xor_sync(0xffffffffu, x[0].lo, o));
+            x[0] = df_add(x[0], y);
+        }
+    }
+    return df_to_double_scaled(x[0], 0);
+}
+template <int N>
+__device__ __forceinline__ int warp_sum_n_lane(int k) { return k * (32 / N); }
+
 // block_sum (common.cuh) of float values
 template <int BS>
 __device__ __forceinline__ double block_sum(float v, double* smem)
@@ -355,11 +393,18 @@ template <int BS, int NB>
 __device__ __forceinline__ double block_sum_n(const float* v, unsigned mask, double* smem)
 {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if constexpr ((NB & (NB - 1)) == 0) {
+        // values outside mask are zero: summed, not stored
+        const double x = warp_sum_n<NB>(v);
+        const int k = l / (32 / NB);
+        if (l == warp_sum_n_lane<NB>(k) && (mask & (1u << k))) smem[w * NB + k] = x;
+    } else {
 #pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        if (!(mask & (1u << k))) continue;
-        const double x = warp_sum(v[k]);
-        if (l == 0) smem[w * NB + k] = x;
+        for (int k = 0; k < NB; ++k) {
+            if (!(mask & (1u << k))) continue;
+            const double x = warp_sum(v[k]);
+            if (l == 0) smem[w * NB + k] = x;
+        }
     }
     __syncthreads();
     double s = 0.0;
@@ -378,10 +423,16 @@ __device__ __forceinline__ void chunk_partials(const float* v, double* part, int
     static_assert((BS * SPT) % RCHUNK == 0 && BS % 32 == 0, "chunks of 128 sites");
     constexpr int NW = BS / 32, NCH = BS * SPT / RCHUNK;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr ((SPT & (SPT - 1)) == 0) {
+        const double s = warp_sum_n<SPT>(v);
+        const int j = lane / (32 / SPT);
+        if (lane == warp_sum_n_lane<SPT>(j)) smem[j * NW + w] = s;
+    } else {
 #pragma unroll
-    for (int j = 0; j < SPT; ++j) {
-        const double s = warp_sum(v[j]);
-        if (lane == 0) smem[j * NW + w] = s;
+        for (int j = 0; j < SPT; ++j) {
+            const double s = warp_sum(v[j]);
+            if (lane == 0) smem[j * NW + w] = s;
+        }
     }
     __syncthreads();
     if (threadIdx.x < NCH) {

@@ -7,37 +7,42 @@
 
 namespace stag {
 
-template <class LF, class SIn, class SOut, int BS, bool STG>
+template <class LF, class SIn, class SOut, int BS, int MODE>
 __global__ void __launch_bounds__(BS, (OpMinBlocksS<LF, SIn>::value)) k_dslash(Geom g, int p, LF U, SIn in, SOut out)
 {
     const int h = blockIdx.x * BS + threadIdx.x;
     if (h >= g.Vh) return;
-    if constexpr (STG) {
-        __shared__ uint4 st[StageWords<LF, BS, STG>::value];
-        out.store(h, dslash_site_staged<BS>(g, p, h, U, in, st));
+    if constexpr (MODE != 0) {
+        __shared__ uint4 st[StageWords<LF, SIn, BS, MODE>::value];
+        out.store(h, dslash_site_staged<BS, MODE>(g, p, h, U, in, st));
     } else {
         out.store(h, dslash_site(g, p, h, U, in));
     }
 }
 
-// Half 12-real links are staged in shared memory (dslash_site_staged) where
-// the context's decision says so: the autotuner's choice, timed by
-// stag_dslash_repeat (an operator entry point outside stream capture) and
-// otherwise the unstaged kernel until a decision exists.
+// Half 12-real links and half spinors can be staged in shared memory
+// (dslash_site_staged, stage = STAGE_* bits) where the context's decision says
+// so: the autotuner's choice, timed by stag_dslash_repeat (an operator entry
+// point outside stream capture), and the unstaged kernel until a decision
+// exists.
 template <class LF, class SIn, class SOut>
 static int run_dslash(stag_ctx ctx, const LF& U, const SIn& in, const SOut& out, int p,
-                      cudaStream_t s, bool stg = false)
+                      cudaStream_t s, int stage = 0)
 {
     constexpr int BS = 128;
     const int grid = (ctx->g.Vh + BS - 1) / BS;
-    if constexpr (LinkStage<LF>::value) {
-        if (stg) {
-            k_dslash<LF, SIn, SOut, BS, true><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
-            STAG_CUDA_TRY(cudaGetLastError());
-            return STAG_OK;
+    if constexpr (LinkStage<LF>::value && SpinorStage<SIn>::value) {
+        switch (stage) {
+        case STAGE_LINKS: k_dslash<LF, SIn, SOut, BS, STAGE_LINKS><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out); break;
+        case STAGE_SPINORS: k_dslash<LF, SIn, SOut, BS, STAGE_SPINORS><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out); break;
+        case STAGE_LINKS | STAGE_SPINORS:
+            k_dslash<LF, SIn, SOut, BS, STAGE_LINKS | STAGE_SPINORS><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
+            break;
+        default: k_dslash<LF, SIn, SOut, BS, 0><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out); break;
         }
+    } else {
+        k_dslash<LF, SIn, SOut, BS, 0><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
     }
-    k_dslash<LF, SIn, SOut, BS, false><<<grid, BS, 0, s>>>(ctx->g, p, U, in, out);
     STAG_CUDA_TRY(cudaGetLastError());
     return STAG_OK;
 }
@@ -65,7 +70,7 @@ int launch_dslash(stag_ctx ctx, int prec, int recon, int par_out, void* out, con
         SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
         if (recon == 18) return run_dslash(ctx, LinkField<__half2, 18>{(const __half2*)lk, Vh, tg}, si, so, par_out, s);
         return run_dslash(ctx, LinkField<__half2, 12>{(const __half2*)lk, Vh, tg}, si, so, par_out, s,
-                          ctx->half_stage[tg] == 1);
+                          ctx->half_stage[tg] > 0 ? ctx->half_stage[tg] : 0);
     }
     set_error("unsupported precision %d", prec);
     return STAG_EUNSUPPORTED;
@@ -81,8 +86,9 @@ int tune_half_stage(stag_ctx ctx, int links, void* out, const void* in)
     const LinkField<__half2, 12> U{(const __half2*)lk, Vh, tg};
     const SpinorF16 si{(uint4*)in, Vh}, so{(uint4*)out, Vh};
     int choice = 0;
-    STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "dslash_stage_tg" : "dslash_stage", STAG_F16, 12, 1), {0, 1},
-                         &choice, [&](int c) { return run_dslash(ctx, U, si, so, 0, ctx->stream, c == 1); }));
+    STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "dslash_stage_tg" : "dslash_stage", STAG_F16, 12, 1),
+                         {0, STAGE_LINKS, STAGE_SPINORS, STAGE_LINKS | STAGE_SPINORS}, &choice,
+                         [&](int c) { return run_dslash(ctx, U, si, so, 0, ctx->stream, c); }));
     ctx->half_stage[tg] = choice;
     return STAG_OK;
 }

@@ -245,10 +245,20 @@ struct MixedPlan {
         const Geom g = ctx->g;
         S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p);
         if constexpr (LinkStage<LF>::value) {
-            if (bs & HOP_STAGED) {
-                STAG_HOP_SWITCH(bs & ~HOP_STAGED,
-                                (k_hop_guarded<LF, S, BS, true><<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
+            switch (bs >> HOP_STAGE_SHIFT) {
+            case STAGE_LINKS:
+                STAG_HOP_SWITCH(bs & HOP_BS_MASK, (k_hop_guarded<LF, S, BS, STAGE_LINKS>
+                                                   <<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
                 return STAG_OK;
+            case STAGE_SPINORS:
+                STAG_HOP_SWITCH(bs & HOP_BS_MASK, (k_hop_guarded<LF, S, BS, STAGE_SPINORS>
+                                                   <<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
+                return STAG_OK;
+            case STAGE_LINKS | STAGE_SPINORS:
+                STAG_HOP_SWITCH(bs & HOP_BS_MASK, (k_hop_guarded<LF, S, BS, STAGE_LINKS | STAGE_SPINORS>
+                                                   <<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
+                return STAG_OK;
+            default: break;
             }
         }
         STAG_HOP_SWITCH(bs, (k_hop_guarded<LF, S, BS><<<nblk_m(g.Vh, BS), BS, 0, s>>>(g, 1, U, p, t, sc)));
@@ -258,15 +268,26 @@ struct MixedPlan {
     {
         const Geom g = ctx->g;
         S t = m.template spinor<S>(m.t), p = m.template spinor<S>(m.p), Ap = m.template spinor<S>(m.Ap);
+        const int nb = nblk_m(g.Vh, MHOP_BS);
+        const GridSum gs = grid_sum_of(ctx);
         if constexpr (LinkStage<LF>::value) {
-            if (stage) {
-                k_Mp_dot<LF, S, S, MHOP_BS, true><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(
-                    g, U, t, p, Ap, sc, ctx->partials, ctx->counters, grid_sum_of(ctx));
+            switch (stage) {
+            case STAGE_LINKS:
+                k_Mp_dot<LF, S, S, MHOP_BS, STAGE_LINKS><<<nb, MHOP_BS, 0, s>>>(g, U, t, p, Ap, sc, ctx->partials,
+                                                                             ctx->counters, gs);
                 return STAG_OK;
+            case STAGE_SPINORS:
+                k_Mp_dot<LF, S, S, MHOP_BS, STAGE_SPINORS><<<nb, MHOP_BS, 0, s>>>(g, U, t, p, Ap, sc, ctx->partials,
+                                                                               ctx->counters, gs);
+                return STAG_OK;
+            case STAGE_LINKS | STAGE_SPINORS:
+                k_Mp_dot<LF, S, S, MHOP_BS, STAGE_LINKS | STAGE_SPINORS><<<nb, MHOP_BS, 0, s>>>(
+                    g, U, t, p, Ap, sc, ctx->partials, ctx->counters, gs);
+                return STAG_OK;
+            default: break;
             }
         }
-        k_Mp_dot<LF, S, S, MHOP_BS><<<nblk_m(g.Vh, MHOP_BS), MHOP_BS, 0, s>>>(g, U, t, p, Ap, sc, ctx->partials,
-                                                                           ctx->counters, grid_sum_of(ctx));
+        k_Mp_dot<LF, S, S, MHOP_BS><<<nb, MHOP_BS, 0, s>>>(g, U, t, p, Ap, sc, ctx->partials, ctx->counters, gs);
         return STAG_OK;
     }
     static int launch_update(stag_ctx ctx, MixedSlot& m, int cfg, cudaStream_t s, CgScalars* sc, LoopGraph* lg,
@@ -296,12 +317,15 @@ struct MixedPlan {
         k_mixed_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
         STAG_CUDA_TRY(cudaGetLastError());
         CgShape sh;
-        // block sizes, and for half 12-real links the same with the links
-        // staged in shared memory (64 and 128 threads: 12 and 24 KB a block)
+        // block sizes, and for half 12-real storage the same with the links
+        // and / or the neighbour spinors staged in shared memory (24 and
+        // 16 KB a block of 128 threads)
         std::vector<int> hc = {128, 64, 256};
         if (LinkStage<LF>::value) {
-            hc.push_back(128 | HOP_STAGED);
-            hc.push_back(64 | HOP_STAGED);
+            for (int st : {STAGE_LINKS, STAGE_SPINORS, STAGE_LINKS | STAGE_SPINORS}) {
+                hc.push_back(128 | (st << HOP_STAGE_SHIFT));
+                hc.push_back(64 | (st << HOP_STAGE_SHIFT));
+            }
         }
         STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "mixed_hop_tg" : "mixed_hop", prec, recon, 1), hc, &sh.hop,
                              [&](int c) { return launch_hop(ctx, m, U, c, ctx->stream, tsc); }));
@@ -310,7 +334,8 @@ struct MixedPlan {
             // pAp may read as a breakdown): it is reset before every launch
             // and after the last
             STAG_TRY(tune_choice(ctx, tune_key(ctx, tg ? "mixed_mpdot_stage_tg" : "mixed_mpdot_stage", prec, recon, 1),
-                                 {0, 1}, &sh.mpdot_stage, [&](int c) {
+                                 {0, STAGE_LINKS, STAGE_SPINORS, STAGE_LINKS | STAGE_SPINORS}, &sh.mpdot_stage,
+                                 [&](int c) {
                                      k_mixed_time_init<<<1, 1, 0, ctx->stream>>>(tsc);
                                      return launch_mpdot(ctx, m, U, c, ctx->stream, tsc);
                                  }));

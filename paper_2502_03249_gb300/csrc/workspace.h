@@ -12,12 +12,13 @@ struct CgShape {
     int hop = 128;                 // hop kernel block size
     int upd = vcfg(256, 1);        // update kernel (vcfg: block size, sites per thread)
     int pk = vcfg(256, 1);         // direction update kernel
-    int mpdot_stage = 0;           // Mp_dot with its links staged in shared memory (half 12-real)
+    int mpdot_stage = 0;           // Mp_dot staging (STAGE_* bits, half 12-real)
 };
 
-// A hop-kernel block size with HOP_STAGED set: the links staged in shared
-// memory (dslash_site_staged).
-constexpr int HOP_STAGED = 1 << 12;
+// A hop-kernel candidate: the block size, with the STAGE_* bits of what the
+// kernel stages in shared memory (dslash_site_staged) above HOP_STAGE_SHIFT.
+constexpr int HOP_STAGE_SHIFT = 12;
+constexpr int HOP_BS_MASK = (1 << HOP_STAGE_SHIFT) - 1;
 
 // Buffers of one mixed-precision configuration (inner precision x compression).
 struct MixedSlot {

@@ -116,12 +116,13 @@ def test_mixed_solver_launch_shapes_identical(stag, fresh_tuner, prec):
         assert got[:2] == ref[:2] and np.array_equal(got[2], ref[2]), (hop, upd, pk)
 
 
-STAGED = 1 << 12   # hop block size with the links staged in shared memory
+STAGED = 1 << 12   # hop block size + STAGED: links staged in shared memory; 2 STAGED: neighbour
+                   # spinors; 3 STAGED: both
 
 
 def test_mixed_half_staged_links_identical(stag, fresh_tuner):
-    """Half 12-real inner iteration with its links staged in shared memory
-    (cp.async, the hop and Mp_dot kernels) against the unstaged kernels: the
+    """Half 12-real inner iteration with its links and / or neighbour spinors
+    staged in shared memory (cp.async, the hop and Mp_dot kernels) against the unstaged kernels: the
     same iterations, reliable updates and solution bits, as uploaded and in
     temporal gauge (ragged lattice: V/2 = 720)."""
     import torch
@@ -131,7 +132,8 @@ def test_mixed_half_staged_links_identical(stag, fresh_tuner):
     gpu = torch.cuda.get_device_name()
     for tg in (0, 1):
         ref = None
-        for hop, mp in [(128, 0), (128 | STAGED, 1), (64 | STAGED, 0), (64, 1)]:
+        for hop, mp in [(128, 0), (128 | STAGED, 1), (64 | STAGED, 0), (64, 1), (128 | 2 * STAGED, 2),
+                        (64 | 3 * STAGED, 3), (128 | 3 * STAGED, 2)]:
             fresh_tuner.clear()
             sfx = "_tg" if tg else ""
             for k, c in (("mixed_hop" + sfx, hop), ("mixed_mpdot_stage" + sfx, mp), ("mixed_update", VEC[0]),
@@ -150,16 +152,17 @@ def test_mixed_half_staged_links_identical(stag, fresh_tuner):
 
 @pytest.mark.parametrize("dims", [(10, 6, 4, 6), (6, 4, 2, 10), (16, 16, 16, 16)])
 def test_half_operator_staged_links_identical(stag, fresh_tuner, dims):
-    """stag_dslash_repeat on half 12-real storage with the links staged in
-    shared memory equals the unstaged kernel bit for bit, as uploaded and in
-    temporal gauge (identity time links skipped)."""
+    """stag_dslash_repeat on half 12-real storage with the links, the
+    neighbour spinors or both staged in shared memory equals the unstaged
+    kernel bit for bit, as uploaded and in temporal gauge (identity time links
+    skipped)."""
     import torch
     U = li.random_links(dims, "haar", seed=641)
     psi = li.gaussian_half(dims, seed=642)
     gpu = torch.cuda.get_device_name()
     for links in (stag.LINKS_UPLOADED, stag.LINKS_TEMPORAL):
         outs = []
-        for choice in (0, 1):
+        for choice in (0, 1, 2, 3):
             fresh_tuner.clear()
             key = "dslash_stage_tg" if links == stag.LINKS_TEMPORAL else "dslash_stage"
             fresh_tuner.insert(fresh_tuner.make_key(key, dims, 2, 12, 1, gpu), choice)
@@ -172,5 +175,6 @@ def test_half_operator_staged_links_identical(stag, fresh_tuner, dims):
             ctx.dslash_result(out)
             outs.append(out.cpu().numpy())
             ctx.close()
-        assert np.array_equal(outs[0], outs[1]), links
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o), links
         assert np.isfinite(outs[0]).all() and np.abs(outs[0]).max() > 0
