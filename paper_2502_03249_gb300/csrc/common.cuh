@@ -527,7 +527,7 @@ template <> struct LinkStage<LinkField<__half2, 12>> {
     static constexpr bool value = true;
     typedef LinkField<__half2, 12>::C C;
     // uint4 words of shared memory for a block of BS threads
-    static constexpr int words(int BS) { return 8 * C::NC * BS + (C::RB ? (8 * BS * C::RB + 15) / 16 : 0); }
+    __host__ __device__ static constexpr int words(int BS) { return 8 * C::NC * BS + (C::RB ? (8 * BS * C::RB + 15) / 16 : 0); }
     static __device__ __forceinline__ uint4* chunks(uint4* st, int BS, int k) { return st + (size_t)k * C::NC * BS + threadIdx.x; }
     static __device__ __forceinline__ void* rem(uint4* st, int BS, int k)
     {

@@ -150,15 +150,19 @@ def test_mixed_half_staged_links_identical(stag, fresh_tuner):
             assert got[:2] == ref[:2] and np.array_equal(got[2], ref[2]), (tg, hop, mp)
 
 
-@pytest.mark.parametrize("dims", [(10, 6, 4, 6), (6, 4, 2, 10), (16, 16, 16, 16)])
+@pytest.mark.parametrize("dims", [(10, 6, 4, 6), (6, 4, 2, 10), (16, 16, 16, 16), (32, 32, 32, 12)])
 def test_half_operator_staged_links_identical(stag, fresh_tuner, dims):
     """stag_dslash_repeat on half 12-real storage with the links, the
     neighbour spinors or both staged in shared memory equals the unstaged
     kernel bit for bit, as uploaded and in temporal gauge (identity time links
     skipped)."""
     import torch
-    U = li.random_links(dims, "haar", seed=641)
-    psi = li.gaussian_half(dims, seed=642)
+    if li.volume(dims) > 100000:
+        U = li.random_links_torch(dims, "smooth", 0.3, seed=641).cpu().numpy()
+        psi = li.gaussian_half_torch(dims, seed=642).cpu().numpy()
+    else:
+        U = li.random_links(dims, "haar", seed=641)
+        psi = li.gaussian_half(dims, seed=642)
     gpu = torch.cuda.get_device_name()
     for links in (stag.LINKS_UPLOADED, stag.LINKS_TEMPORAL):
         outs = []
