@@ -679,7 +679,6 @@ struct SpinorF16 {
 template <class S> struct SpinorStage { static constexpr bool value = false; };
 template <> struct SpinorStage<SpinorF32> {
     static constexpr bool value = true;
-    static constexpr bool TWO = true;   // a second (8-byte) word per slot
     static __device__ __forceinline__ void issue(const SpinorF32& in, int h, uint4* a, uint2* b)
     {
         cp_async16_ca(a, in.pa() + h);
@@ -701,7 +700,6 @@ template <> struct SpinorStage<SpinorF32> {
 };
 template <> struct SpinorStage<SpinorF16> {
     static constexpr bool value = true;
-    static constexpr bool TWO = false;
     static __device__ __forceinline__ void issue(const SpinorF16& in, int h, uint4* a, uint2*)
     {
         cp_async16_ca(a, in.p + h);

@@ -13,6 +13,7 @@
 // G = s u v^dagger is an outer product, so W = U G^dagger = s (U v) u^dagger
 // costs one matrix-vector product per link.
 #include <chrono>
+#include <cmath>
 #include <new>
 
 #include "cg_kernels.cuh"
@@ -31,17 +32,17 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
 {
     const long long idx = (long long)blockIdx.x * F_BS + threadIdx.x;
     if (idx >= 8LL * g.Vh) return;
-    const long long i = idx >> 2;
+    const int i = (int)(idx >> 2);   // lexicographic site (V < 2^31)
     const int mu = (int)(idx & 3);
-    // parity of lexicographic site i
-    const int x = (int)(i % g.L[0]);
-    long long r = i / g.L[0];
-    const int y = (int)(r % g.L[1]);
-    r /= g.L[1];
-    const int z = (int)(r % g.L[2]);
-    const int t = (int)(r / g.L[2]);
+    // coordinates and parity of site i from its half index (Lx even)
+    const int h = i >> 1;
+    const int rr = fast_div(h, g.dxh);
+    const int x = 2 * (h - rr * g.Lxh) + (i & 1);
+    const int zt = fast_div(rr, g.dy);
+    const int y = rr - zt * g.L[1];
+    const int t = fast_div(zt, g.dz);
+    const int z = zt - t * g.L[2];
     const int par = (x + y + z + t) & 1;
-    const int h = (int)(i >> 1);
     int hf;
     uint32_t sfb;
     fwd_nbr(g, par, h, mu, hf, sfb);
@@ -135,26 +136,33 @@ __global__ void __launch_bounds__(F_BS) k_force(Geom g, LF U, const double2* X, 
 // when asked for, is formed in IEEE double as in k_force (18 products of
 // doubles cost less than converting 18 double-float results).  kexp[0] and
 // kexp[1]: the exponents of X and Y.
+//
+// The thread's site comes from its half index h = i / 2 by the multiply-high
+// divisions of the geometry (x = 2 (h mod Lx/2) + (i mod 2), Lx even), and
+// |sg| = 2 |scale| = sgn 2^ks is split once on the host (sgn in [1, 2), ks its
+// exponent); the sign of sg (the parity, eta and boundary, and scale's) is a
+// sign bit applied exactly to u and to the G products.
 __global__ void __launch_bounds__(F_BS) k_force_df(Geom g, LinkFieldDF<18> U, const double2* X, const double2* Y,
-                                                   double2* P, double2* G, double scale, int accumulate,
-                                                   const int* kexp)
+                                                   double2* P, double2* G, double sg_abs, double sgn, int ks,
+                                                   uint32_t sbit_scale, int accumulate, const int* kexp)
 {
     const long long idx = (long long)blockIdx.x * F_BS + threadIdx.x;
     if (idx >= 8LL * g.Vh) return;
-    const long long i = idx >> 2;
+    const int i = (int)(idx >> 2);   // lexicographic site (V < 2^31)
     const int mu = (int)(idx & 3);
-    const int x = (int)(i % g.L[0]);
-    long long r = i / g.L[0];
-    const int y = (int)(r % g.L[1]);
-    r /= g.L[1];
-    const int z = (int)(r % g.L[2]);
-    const int t = (int)(r / g.L[2]);
+    const int h = i >> 1;
+    const int rr = fast_div(h, g.dxh);
+    const int x = 2 * (h - rr * g.Lxh) + (i & 1);
+    const int zt = fast_div(rr, g.dy);
+    const int y = rr - zt * g.L[1];
+    const int t = fast_div(zt, g.dz);
+    const int z = zt - t * g.L[2];
     const int par = (x + y + z + t) & 1;
-    const int h = (int)(i >> 1);
     int hf;
     uint32_t sfb;
     fwd_nbr(g, par, h, mu, hf, sfb);
-    const double sg = (par == 0 ? 2.0 : -2.0) * (sfb ? -1.0 : 1.0) * scale;
+    const uint32_t sbit = (par ? 0x80000000u : 0u) ^ sfb ^ sbit_scale;   // sign of sg
+    const double sg = flip(sg_abs, sbit);
     const double2* up = par == 0 ? X + (size_t)h * 3 : Y + (size_t)h * 3;
     const double2* vp = par == 0 ? Y + (size_t)hf * 3 : X + (size_t)hf * 3;
     const int ku = kexp[par], kv = kexp[1 - par];
@@ -182,8 +190,7 @@ __global__ void __launch_bounds__(F_BS) k_force_df(Geom g, LinkFieldDF<18> U, co
         }
     }
     if (!P) return;
-    const int ks = ilogb(sg);
-    const DF sgd = split_double_scaled(sg, ks);   // sg = sgd 2^ks, |sgd| in [1, 2)
+    const DF sgd = split_double(sgn);   // |sg| = sgd 2^ks, sgd in [1, 2)
     Cplx<DF> u[3], v[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -191,6 +198,8 @@ __global__ void __launch_bounds__(F_BS) k_force_df(Geom g, LinkFieldDF<18> U, co
         u[a] = {DF(0), DF(0)};
         df_mac(u[a].re, sgd, ur);
         df_mac(u[a].im, sgd, ui);
+        // the sign of sg: an exact negation of the products
+        u[a] = {flip(u[a].re, sbit), flip(u[a].im, sbit)};
         v[a] = {split_double_scaled(vq[a].x, kv), split_double_scaled(vq[a].y, kv)};
     }
     const Mat3<DF> Um = U.load(par, mu, h);
@@ -323,8 +332,13 @@ int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2
         STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lkdf));
         STAG_TRY(field_exponents(ctx, X, 1, (size_t)3 * g.Vh, SLOT_FORCE, ctx->stream));
         STAG_TRY(field_exponents(ctx, ctx->tmp_odd, 1, (size_t)3 * g.Vh, SLOT_FORCE + 1, ctx->stream));
+        // |sg| = 2 |scale| = sgn 2^ks with sgn in [1, 2) (exact scalings)
+        const double sg_abs = 2.0 * fabs(scale);
+        const int ks = ilogb(sg_abs);
+        const double sgn = ldexp(sg_abs, -ks);
         k_force_df<<<grid, F_BS, 0, ctx->stream>>>(g, LinkFieldDF<18>{(const float4*)lkdf, g.Vh}, X, ctx->tmp_odd, P,
-                                                   G, scale, accumulate, ctx->scale_k + SLOT_FORCE);
+                                                   G, sg_abs, sgn, ks, signbit(scale) ? 0x80000000u : 0u, accumulate,
+                                                   ctx->scale_k + SLOT_FORCE);
     } else {
         k_force<LinkField<double2, 18>><<<grid, F_BS, 0, ctx->stream>>>(g, U, X, ctx->tmp_odd, P, G, scale,
                                                                         accumulate);

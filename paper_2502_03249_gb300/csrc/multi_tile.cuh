@@ -171,6 +171,49 @@ __device__ __forceinline__ Mat3<typename LF::real> hop_matrix(const LF& U, int p
     return H;
 }
 
+// Phase 2 for one thread: acc[k] += the 8 hops applied to field f[k] at the
+// neighbours of s, for the k of mask (ALL: every k, no tests), the hop
+// matrices read from the tile in shared memory.
+template <class LF, class S, int NBT, bool ALL>
+__device__ __forceinline__ void tile_apply_hops(const SiteNbrs& s, const LF& U, const S* f, unsigned mask,
+                                                const uint4* sm, int TS, int sl, Vec3<typename LF::real>* acc)
+{
+    typedef typename LF::real real;
+#pragma unroll
+    for (int hop = 0; hop < 8; ++hop) {
+        const int nb = (hop & 1) ? s.bwd[hop >> 1] : s.fwd[hop >> 1];
+        // the neighbour spinors in batches of up to four loads in flight
+        constexpr int NL = NBT < 4 ? NBT : 4;
+        if (unit_hop(U, s, hop)) {
+            // identity time link of a temporal-gauge field: the signed spinor
+            // is added (what the product with the hop matrix +-1 gives)
+            const uint32_t sb = (hop & 1) ? s.sb[3] : s.sf[3];
+#pragma unroll
+            for (int kb = 0; kb < NBT; kb += NL) {
+                Vec3<real> v[NL];
+#pragma unroll
+                for (int k = 0; k < NL; ++k)
+                    if (ALL || (mask & (1u << (kb + k)))) v[k] = load_flipped(f[kb + k], nb, sb);
+#pragma unroll
+                for (int k = 0; k < NL; ++k)
+                    if (ALL || (mask & (1u << (kb + k)))) hop_add(acc[kb + k], v[k]);
+            }
+            continue;
+        }
+        const Mat3<real> H = HopStore<real>::get(sm, TS, hop, sl);
+#pragma unroll
+        for (int kb = 0; kb < NBT; kb += NL) {
+            Vec3<real> v[NL];
+#pragma unroll
+            for (int k = 0; k < NL; ++k)
+                if (ALL || (mask & (1u << (kb + k)))) v[k] = f[kb + k].load(nb);
+#pragma unroll
+            for (int k = 0; k < NL; ++k)
+                if (ALL || (mask & (1u << (kb + k)))) mv_acc(acc[kb + k], H, v[k]);
+        }
+    }
+}
+
 // Phase 1 and 2 for one thread: stage the tile's hop matrices, then
 // acc[k] = (D_{p,1-p} in_{k0+k})_h for the k of mask.  All threads of the
 // block call this (it contains a barrier); h >= Vh and mask = 0 only skip work.
@@ -195,39 +238,16 @@ __device__ __forceinline__ void tile_site_multi(const Geom& g, int p, int h, con
 #pragma unroll
         for (int a = 0; a < 3; ++a) acc[k].c[a].re = acc[k].c[a].im = real(0);
     if (!on || !mask) return;
+    // the thread's NBT fields, and the hop loop without per-system tests
+    // when all of them are active (the usual case)
+    S f[NBT];
 #pragma unroll
-    for (int hop = 0; hop < 8; ++hop) {
-        const int nb = (hop & 1) ? s.bwd[hop >> 1] : s.fwd[hop >> 1];
-        // the neighbour spinors in batches of up to four loads in flight
-        constexpr int NL = NBT < 4 ? NBT : 4;
-        if (unit_hop(U, s, hop)) {
-            // identity time link of a temporal-gauge field: the signed spinor
-            // is added (what the product with the hop matrix +-1 gives)
-            const uint32_t sb = (hop & 1) ? s.sb[3] : s.sf[3];
-#pragma unroll
-            for (int kb = 0; kb < NBT; kb += NL) {
-                Vec3<real> v[NL];
-#pragma unroll
-                for (int k = 0; k < NL; ++k)
-                    if (mask & (1u << (kb + k))) v[k] = load_flipped(in.at(k0 + kb + k, stride), nb, sb);
-#pragma unroll
-                for (int k = 0; k < NL; ++k)
-                    if (mask & (1u << (kb + k))) hop_add(acc[kb + k], v[k]);
-            }
-            continue;
-        }
-        const Mat3<real> H = HopStore<real>::get(sm, TS, hop, sl);
-#pragma unroll
-        for (int kb = 0; kb < NBT; kb += NL) {
-            Vec3<real> v[NL];
-#pragma unroll
-            for (int k = 0; k < NL; ++k)
-                if (mask & (1u << (kb + k))) v[k] = in.at(k0 + kb + k, stride).load(nb);
-#pragma unroll
-            for (int k = 0; k < NL; ++k)
-                if (mask & (1u << (kb + k))) mv_acc(acc[kb + k], H, v[k]);
-        }
+    for (int k = 0; k < NBT; ++k) f[k] = in.at(k0 + k, stride);
+    if (mask == (1u << NBT) - 1u) {
+        tile_apply_hops<LF, S, NBT, true>(s, U, f, mask, sm, TS, sl, acc);
+        return;
     }
+    tile_apply_hops<LF, S, NBT, false>(s, U, f, mask, sm, TS, sl, acc);
 }
 
 // Shared memory of a tile kernel (bytes).
