@@ -162,6 +162,10 @@ int multi_dslash_internal(stag_ctx ctx, int prec, int recon, int par_out, void* 
                           int nb, int* nb_used, int links = STAG_LINKS_UPLOADED);
 int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2* in, int nfield, int links,
                           int nb, int* nb_used, cudaStream_t s);
+// the context's double-float scratch fields: nfield inputs and nfield outputs
+// of SpinorDF storage (48 bytes per site each), kept until the next call that
+// uses them (the double-float operator entry points, the force)
+int dfx_fields(stag_ctx ctx, int nfield, float4** in, float4** out);
 // dslash.cu: the staging decision of the half 12-real operator for a link
 // field (ctx->half_stage), timed once on in/out (outputs overwritten).  Only
 // outside stream capture.

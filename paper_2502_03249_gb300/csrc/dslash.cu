@@ -95,7 +95,7 @@ int tune_half_stage(stag_ctx ctx, int links, void* out, const void* in)
 
 // Scratch of the double-float operator on canonical fields: nfield input and
 // nfield output fields of double-float pairs (48 bytes per site each).
-static int ensure_dfx_tmp(stag_ctx ctx, int nfield, float4** in, float4** out)
+int dfx_fields(stag_ctx ctx, int nfield, float4** in, float4** out)
 {
     const size_t per = lo_spinor_bytes(ctx->g, STAG_F64X);
     const size_t bytes = 2 * per * (size_t)nfield;
@@ -127,7 +127,7 @@ int dslash_f64x_canonical(stag_ctx ctx, int par_out, double2* out, const double2
     int tg = 0;
     STAG_TRY(op_links_for(ctx, links, STAG_F64X, 18, &lk, &tg));
     float4 *ti = nullptr, *to = nullptr;
-    STAG_TRY(ensure_dfx_tmp(ctx, nfield, &ti, &to));
+    STAG_TRY(dfx_fields(ctx, nfield, &ti, &to));
     const size_t elems = (size_t)3 * ctx->g.Vh;
     STAG_TRY(field_exponents(ctx, in, nfield, elems, SLOT_OPER, s));
     STAG_TRY(split_fields_scaled(ctx, in, ti, nfield, elems, SLOT_OPER, -DFX_TOP, s));

@@ -269,6 +269,106 @@ __global__ void __launch_bounds__(F_BS) k_force_df(Geom g, LinkFieldDF<18> U, co
     }
 }
 
+// P alone from X and Y already in double-float storage at one scale: X' =
+// 2^-kx X (largest component in [1, 2)) and Y' = D_oe X' from the
+// double-float operator, so neither field is joined to double, normalised
+// again or split per link.  The arithmetic is that of k_force_df with
+// ku = kv = kx (kexp[0]).
+__global__ void __launch_bounds__(F_BS) k_force_dfin(Geom g, LinkFieldDF<18> U, const float4* Xd, const float4* Yd,
+                                                     double2* P, double sgn, int ks, uint32_t sbit_scale,
+                                                     int accumulate, const int* kexp)
+{
+    const long long idx = (long long)blockIdx.x * F_BS + threadIdx.x;
+    if (idx >= 8LL * g.Vh) return;
+    const int i = (int)(idx >> 2);   // lexicographic site (V < 2^31)
+    const int mu = (int)(idx & 3);
+    const int h = i >> 1;
+    const int rr = fast_div(h, g.dxh);
+    const int x = 2 * (h - rr * g.Lxh) + (i & 1);
+    const int zt = fast_div(rr, g.dy);
+    const int y = rr - zt * g.L[1];
+    const int t = fast_div(zt, g.dz);
+    const int z = zt - t * g.L[2];
+    const int par = (x + y + z + t) & 1;
+    int hf;
+    uint32_t sfb;
+    fwd_nbr(g, par, h, mu, hf, sfb);
+    const uint32_t sbit = (par ? 0x80000000u : 0u) ^ sfb ^ sbit_scale;   // sign of sg
+    const float4* up = par == 0 ? Xd + (size_t)h * 3 : Yd + (size_t)h * 3;
+    const float4* vp = par == 0 ? Yd + (size_t)hf * 3 : Xd + (size_t)hf * 3;
+    const DF sgd = split_double(sgn);   // |sg| = sgd 2^ks
+    Cplx<DF> u[3], v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float4 q = __ldg(up + a), w = __ldg(vp + a);
+        u[a] = {DF(0), DF(0)};
+        df_mac(u[a].re, sgd, DF(q.x, q.y));
+        df_mac(u[a].im, sgd, DF(q.z, q.w));
+        u[a] = {flip(u[a].re, sbit), flip(u[a].im, sbit)};
+        v[a] = {DF(w.x, w.y), DF(w.z, w.w)};
+    }
+    const Mat3<DF> Um = U.load(par, mu, h);
+    Cplx<DF> wv[3];   // U v'
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        DF re(0), im(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            df_mac(re, Um.m[a * 3 + c].re, v[c].re);
+            df_mac(re, df_neg(Um.m[a * 3 + c].im), v[c].im);
+            df_mac(im, Um.m[a * 3 + c].re, v[c].im);
+            df_mac(im, Um.m[a * 3 + c].im, v[c].re);
+        }
+        wv[a] = {re, im};
+    }
+    DF d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        DF q(0);
+        df_mac(q, wv[a].im, u[a].re);
+        df_mac(q, df_neg(wv[a].re), u[a].im);
+        d[a] = q;
+    }
+    const DF tr = df_add(df_add(d[0], d[1]), d[2]);
+    const DF third = split_double(1.0 / 3.0);
+    DF trim(0);
+    df_mac(trim, tr, third);
+    auto offd = [&](int a, int b) {
+        DF re(0), im(0);
+        df_mac(re, wv[a].re, u[b].re);
+        df_mac(re, wv[a].im, u[b].im);
+        df_mac(re, df_neg(u[a].re), wv[b].re);
+        df_mac(re, df_neg(u[a].im), wv[b].im);
+        df_mac(im, wv[a].im, u[b].re);
+        df_mac(im, df_neg(wv[a].re), u[b].im);
+        df_mac(im, df_neg(u[a].im), wv[b].re);
+        df_mac(im, u[a].re, wv[b].im);
+        return Cplx<DF>{re, im};
+    };
+    const Cplx<DF> p01 = offd(0, 1), p02 = offd(0, 2), p12 = offd(1, 2);
+    const int k = 2 * kexp[0] + ks - 1;
+    auto out = [&](const DF& v_) { return df_to_double_scaled(v_, k); };
+    const double d0 = df_to_double_scaled(df_add(d[0], df_neg(trim)), k + 1),
+                 d1 = df_to_double_scaled(df_add(d[1], df_neg(trim)), k + 1),
+                 d2 = df_to_double_scaled(df_add(d[2], df_neg(trim)), k + 1);
+    const double r01 = out(p01.re), i01 = out(p01.im), r02 = out(p02.re), i02 = out(p02.im), r12 = out(p12.re),
+                 i12 = out(p12.im);
+    const double2 Pm[9] = {make_double2(0.0, d0),    make_double2(r01, i01),   make_double2(r02, i02),
+                           make_double2(-r01, i01),  make_double2(0.0, d1),    make_double2(r12, i12),
+                           make_double2(-r02, i02),  make_double2(-r12, i12),  make_double2(0.0, d2)};
+    double2* Pp = P + (size_t)idx * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        double2 o = Pm[e];
+        if (accumulate) {
+            const double2 q = Pp[e];
+            o.x += q.x;
+            o.y += q.y;
+        }
+        Pp[e] = o;
+    }
+}
+
 // out = c X (the gradient 2 dS X of S with respect to phi), canonical half field.
 __global__ void k_scale_copy(long long n, const double2* X, double2* out, double c)
 {
@@ -321,23 +421,45 @@ int force_from_X(stag_ctx ctx, double2* P, double2* G, const double2* X, double2
     STAG_TRY(ensure_links(ctx, STAG_F64, 18, &lk));
     const Geom g = ctx->g;
     const LinkField<double2, 18> U{(const double2*)lk, g.Vh};
+    const long long n = 8LL * g.Vh;
+    const unsigned grid = (unsigned)((n + F_BS - 1) / F_BS);
+    const bool df_ok = ctx->df_link_exp == 0 && scale != 0.0 && isfinite(scale);
+    // |sg| = 2 |scale| = sgn 2^ks with sgn in [1, 2) (exact scalings)
+    const double sg_abs = 2.0 * fabs(scale);
+    const int ks = df_ok ? ilogb(sg_abs) : 0;
+    const double sgn = df_ok ? ldexp(sg_abs, -ks) : 0.0;
+    const uint32_t sbit_scale = signbit(scale) ? 0x80000000u : 0u;
+    if (P && !G && df_ok) {
+        // P alone: X' = 2^-kx X split once into double-float storage, Y' =
+        // D_oe X' by the double-float operator, both read as they are
+        const void* lkdf = nullptr;
+        STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lkdf));
+        float4 *xd = nullptr, *yd = nullptr;
+        STAG_TRY(dfx_fields(ctx, 1, &xd, &yd));
+        const size_t elems = (size_t)3 * g.Vh;
+        STAG_TRY(field_exponents(ctx, X, 1, elems, SLOT_FORCE, ctx->stream));
+        STAG_TRY(split_fields_scaled(ctx, X, xd, 1, elems, SLOT_FORCE, 0, ctx->stream));
+        STAG_TRY(launch_dslash_internal(ctx, STAG_F64X, 18, 1, yd, xd, ctx->stream));
+        k_force_dfin<<<grid, F_BS, 0, ctx->stream>>>(g, LinkFieldDF<18>{(const float4*)lkdf, g.Vh}, xd, yd, P, sgn,
+                                                     ks, sbit_scale, accumulate, ctx->scale_k + SLOT_FORCE);
+        if (phi_grad) {
+            const long long m = 3LL * g.Vh;
+            k_scale_copy<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(m, X, phi_grad, 2.0 * scale);
+        }
+        STAG_CUDA_TRY(cudaGetLastError());
+        return STAG_OK;
+    }
     // Y = D_oe X into the context's odd temporary, with the double-float
     // operator (~1e-14 relative; the IEEE-double one is FP64-bound on GB300)
     STAG_TRY(launch_dslash(ctx, STAG_F64X, 18, 1, ctx->tmp_odd, X, ctx->stream));
-    const long long n = 8LL * g.Vh;
-    const unsigned grid = (unsigned)((n + F_BS - 1) / F_BS);
-    if (P && ctx->df_link_exp == 0 && scale != 0.0 && isfinite(scale)) {
+    if (P && df_ok) {
         // P in double-float arithmetic on the double-float links, X and Y normalised
         const void* lkdf = nullptr;
         STAG_TRY(ensure_links(ctx, STAG_F64X, 18, &lkdf));
         STAG_TRY(field_exponents(ctx, X, 1, (size_t)3 * g.Vh, SLOT_FORCE, ctx->stream));
         STAG_TRY(field_exponents(ctx, ctx->tmp_odd, 1, (size_t)3 * g.Vh, SLOT_FORCE + 1, ctx->stream));
-        // |sg| = 2 |scale| = sgn 2^ks with sgn in [1, 2) (exact scalings)
-        const double sg_abs = 2.0 * fabs(scale);
-        const int ks = ilogb(sg_abs);
-        const double sgn = ldexp(sg_abs, -ks);
         k_force_df<<<grid, F_BS, 0, ctx->stream>>>(g, LinkFieldDF<18>{(const float4*)lkdf, g.Vh}, X, ctx->tmp_odd, P,
-                                                   G, sg_abs, sgn, ks, signbit(scale) ? 0x80000000u : 0u, accumulate,
+                                                   G, sg_abs, sgn, ks, sbit_scale, accumulate,
                                                    ctx->scale_k + SLOT_FORCE);
     } else {
         k_force<LinkField<double2, 18>><<<grid, F_BS, 0, ctx->stream>>>(g, U, X, ctx->tmp_odd, P, G, scale,

@@ -203,6 +203,11 @@ def test_rational_force_is_weighted_sum(stag):
     Gref = sum(c * orc.force(dims, U, Xh[i])[1] for i, c in enumerate(coeffs))
     assert np.linalg.norm(host(P) - Pref) <= 1e-12 * np.linalg.norm(Pref)
     assert np.linalg.norm(host(G) - Gref) <= 1e-12 * np.linalg.norm(Gref)
+    # P alone (the kernel on the double-float fields of the operator pass,
+    # accumulated over the terms) against the same sum
+    P1 = torch.full_like(P, float("nan"))
+    ctx.fermion_force_multi(X, coeffs, P=P1)
+    assert np.linalg.norm(host(P1) - Pref) <= 1e-12 * np.linalg.norm(Pref)
     # finite differences of the rational action on the group (oracle solves)
     def S_of(Ux):
         tot = 0.0

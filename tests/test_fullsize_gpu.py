@@ -44,6 +44,11 @@ def test_force_64c16_every_link(stag, big):
     Po, Go = orc.force(DIMS, Uh, X.cpu().numpy())
     assert rel(P.cpu().numpy(), Po) <= 1e-12
     assert rel(G.cpu().numpy(), Go) <= 1e-12
+    # P alone, as the benchmark calls it (the kernel on the double-float
+    # fields of the operator pass), on every link
+    P1 = torch.full_like(U, float("nan"))
+    ctx.fermion_force(X, P=P1)
+    assert rel(P1.cpu().numpy(), Po) <= 1e-12
 
 
 @pytest.mark.parametrize("prec", [3, 0])
