@@ -690,8 +690,9 @@ def section_force(stag, torch, timer, hbm):
     res = {"workload": w["name"] + " (inputs from the torch generator)",
            "force_call_ms": ms_f, "links": nlinks, "algorithmic_bytes_per_link": bpl, "achieved_gbs": gbs,
            "frac_of_hbm": gbs / hbm, "action_solve_iters": st["iters"],
-           "force_note": "stag_fermion_force with P only: Y = D_oe X (double-float operator, normalised), the "
-                         "exponents of X and Y, and the force kernel (P in double-float arithmetic)"}
+           "force_note": "stag_fermion_force with P only: the exponent of X and its double-float split, "
+                         "Y' = D_oe X' by the double-float operator, and the force kernel on those fields "
+                         "(P in double-float arithmetic, accumulated in double)"}
     Ug = U.clone().requires_grad_(True)
 
     def fwd_bwd():
@@ -702,6 +703,17 @@ def section_force(stag, torch, timer, hbm):
     ms_ab, _ = timer(fwd_bwd, reps=1)
     res["autograd_forward_backward_ms"] = ms_ab
     res["autograd_note"] = "forward solves X; backward re-solves X (not stored) and applies the force kernel"
+
+    def fwd_bwd_half():
+        # the same with the solver options SU(3) links allow: half 12-real inner
+        # iteration in temporal gauge (double-float reliable updates, 1e-10)
+        S = stag.StaggeredAction(Ug, phi, ctx, mass, tol=TOL, inner_prec=stag.F16, inner_recon=12,
+                                 temporal_gauge=1)
+        S.backward()
+        return S
+
+    ms_ah, _ = timer(fwd_bwd_half, reps=1)
+    res["autograd_forward_backward_half12_temporal_gauge_ms"] = ms_ah
     ctx.close()
     del Ug, U, P
     torch.cuda.empty_cache()
