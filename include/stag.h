@@ -147,7 +147,11 @@ int stag_dslash_oe(stag_ctx ctx, double *out_odd, const double *in_even, int pre
  * stag_dslash_repeat then applies D_eo (Sec. 4.2, Eq. (staggered)) to it nrep
  * times into a context-owned output with no conversions, so that a caller's
  * CUDA events on the context's stream around it time the bare operator
- * kernel.  stag_dslash_result converts that output back into the canonical
+ * kernel.  For half 12-real storage the first repeat per link field (as
+ * uploaded, temporal gauge) lets the autotuner time the kernel's
+ * shared-memory staging variants (same results bit for bit) unless its cache
+ * has the decision, so that call is not capturable in a CUDA graph.
+ * stag_dslash_result converts that output back into the canonical
  * device half field out (complex128 [V/2][3]).  Asynchronous.  Errors:
  * STAG_EINVAL (repeat before prepare, other precision, result before repeat,
  * bad pointer), STAG_ENOGAUGE, STAG_EUNSUPPORTED. */
